@@ -1,0 +1,160 @@
+/*
+ * mpt.h -- C ABI of the GB300 multiple-precision Taylor integrator for the
+ * Lorenz system (Dimova et al., "OpenMP parallelization of multiple precision
+ * Taylor series method", arXiv 1908.09301).
+ *
+ * The library computes, on one GPU and entirely in its own CUDA kernels, the
+ * Taylor step of Sec. 2:
+ *   - Eq. (1)  dx/dt = -sigma x + sigma y, dy/dt = R x - y - x z, dz/dt = x y - b z;
+ *   - Eq. (3)  the recursion for the normalized Taylor coefficients
+ *              alpha_i, beta_i, gamma_i (i = 0..N), whose Cauchy sums
+ *              sum_{k=0}^{i} alpha_{i-k} gamma_k and sum_{k=0}^{i} alpha_{i-k} beta_k
+ *              are the reductions Sec. 2 and Sec. 4 parallelise;
+ *   - Eq. (2)  x_{n+1} = x_n + sum_{i=1}^{N} alpha_i tau^i (same for y, z),
+ *              evaluated by Horner's rule as the complexity remark of Sec. 2 says.
+ *
+ * Number format.  A number with L 32-bit limbs is (sign, exp, limb[L]) with
+ *   value = (-1)^sign * sum_{j<L} limb[j] * 2^(32*(exp-L+j)),
+ * limb[0] least significant, limb[L-1] != 0, sign in {0, 1}; zero is
+ * sign = 0, exp = 0, all limbs 0.  |exp| <= 2^30.  Arrays of numbers are SoA:
+ * signs[n], exps[n], limbs[n][L].
+ *
+ * Arithmetic.  trunc_L(v) keeps the top L limbs of |v| counted from its top
+ * non-zero limb on the absolute 2^32 grid and drops the rest (toward zero).
+ * Every bracket of Eq. (3) is formed exactly from the stored coefficients and
+ * parameters and then coefficient_{i+1} = trunc_L(bracket / (i+1)); every
+ * Horner step is h_i = trunc_L(h_{i+1} * tau + c_i) with an exact product and
+ * sum, starting from h_N = c_N.  Results do not depend on how the GPU splits
+ * the sums, so they are bit-identical across launch shapes.
+ *
+ * Errors.  Every int-returning call returns MPT_OK (0) or a negative code and
+ * never throws; mpt_last_error() gives a message for the calling thread.
+ * Device-side conditions (exponent range, a bounded wait that expired) are
+ * reported by the call that launched the work, which waits for it.
+ *
+ * Threads.  A context may be used by one host thread at a time.
+ */
+#ifndef MPT_H
+#define MPT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPT_OK 0
+#define MPT_EINVAL (-1)    /* bad argument: sizes, a malformed number string, a null pointer */
+#define MPT_ENOMEM (-2)    /* a host or device allocation failed */
+#define MPT_ERANGE (-3)    /* an exponent left |exp| <= 2^30, or the terms of one exact sum
+                              span more limbs than the accumulator holds */
+#define MPT_ETIMEDOUT (-4) /* a bounded device-side wait expired; the context stays usable */
+#define MPT_ECUDA (-5)     /* a CUDA runtime call failed (message in mpt_last_error) */
+
+typedef struct mpt_ctx mpt_ctx;
+
+/* Number of 32-bit limbs for K decimal digits: ceil(K * log2(10) / 32). */
+int mpt_limbs_for_digits(int K_digits);
+
+/*
+ * Create a context for the Taylor method of order N (Sec. 2, Eq. (2)) with
+ * L-limb numbers.  L_limbs == 0 takes L = mpt_limbs_for_digits(K_digits).
+ * tau, sigma, R, b are decimal ("0.01", "-1.5e-3") or rational ("8/3")
+ * strings; each becomes trunc_L of its exact value (Sec. 2 gives
+ * sigma = 10, R = 28, b = 8/3; Sec. 5 takes tau = 0.01).  cuda_stream is a
+ * cudaStream_t (0 = the legacy default stream) on which all work of this
+ * context is queued; it must belong to the current device.  The context owns
+ * all the device memory it needs.  Limits: 1 <= L <= 1024, 1 <= N <= 4096, and
+ * the per-CTA tables for (L, N) must fit in shared memory (else MPT_EINVAL).
+ * The state starts at (0, 0, 0).
+ */
+int mpt_init(mpt_ctx **ctx, int K_digits, int N_order, int L_limbs, const char *tau,
+             const char *sigma, const char *R, const char *b, uint64_t cuda_stream);
+
+/*
+ * trunc_L of the exact value of a decimal ("-15.8", "1e-20") or rational
+ * ("8/3", "-1.5/0.25") string, as one number in the interchange layout
+ * (host memory, L limbs).  Host only; no device is needed.  MPT_EINVAL for
+ * a malformed string or zero denominator, MPT_ERANGE for |exp| > 2^30.
+ */
+int mpt_parse_number(const char *str, int L, int32_t *sign, int32_t *exp, uint32_t *limbs);
+
+/* Release the context and its device memory (null is accepted). */
+void mpt_destroy(mpt_ctx *ctx);
+
+/* L and N of the context. */
+int mpt_get_dims(const mpt_ctx *ctx, int *L, int *N);
+
+/*
+ * Set the state (x_n, y_n, z_n) = (alpha_0, beta_0, gamma_0) of Sec. 2 from
+ * decimal or rational strings, each truncated to L limbs (Sec. 5's benchmark
+ * point is "-15.8", "-17.48", "35.64").
+ */
+int mpt_set_state(mpt_ctx *ctx, const char *x0, const char *y0, const char *z0);
+
+/*
+ * Set / read the state as 3 numbers (x, y, z) in the interchange layout:
+ * signs[3], exps[3], limbs[3][L], all HOST memory owned by the caller.
+ * set_state_raw rejects non-normalised numbers with MPT_EINVAL.  get_state
+ * waits for the context's queued work.
+ */
+int mpt_set_state_raw(mpt_ctx *ctx, const int32_t *signs, const int32_t *exps,
+                      const uint32_t *limbs);
+int mpt_get_state(mpt_ctx *ctx, int32_t *signs, int32_t *exps, uint32_t *limbs);
+
+/* The truncated parameters (sigma, R, b, tau) as 4 numbers, host memory. */
+int mpt_get_params(mpt_ctx *ctx, int32_t *signs, int32_t *exps, uint32_t *limbs);
+
+/* One Taylor step (Eq. (3) for i = 0..N-1, then Eq. (2) by Horner). */
+int mpt_step(mpt_ctx *ctx);
+
+/*
+ * nsteps Taylor steps in one device launch.  If record_every > 0 the state
+ * after every record_every-th step is written to rec_* (nsteps / record_every
+ * records of 3 numbers, layout [record][component] for signs and exps and
+ * [record][component][L] for limbs).  The rec_* pointers may be host or
+ * device memory (CUDA unified addressing tells them apart); they may be null
+ * when record_every <= 0.  The call returns when the work is done.
+ */
+int mpt_integrate(mpt_ctx *ctx, int64_t nsteps, int64_t record_every, int32_t *rec_signs,
+                  int32_t *rec_exps, uint32_t *rec_limbs);
+
+/*
+ * The Taylor coefficients of the most recent step: 3*(N+1) numbers,
+ * component-major (alpha_0..alpha_N, beta_0..beta_N, gamma_0..gamma_N;
+ * index 0 is the state the step started from), host memory.
+ */
+int mpt_get_coefficients(mpt_ctx *ctx, int32_t *signs, int32_t *exps, uint32_t *limbs);
+
+/*
+ * Launch shape.  ctas = 0 lets the library choose; otherwise the coefficient
+ * phase runs on exactly that many CTAs (1 .. number of SMs).  Results do not
+ * depend on it.
+ */
+int mpt_set_launch(mpt_ctx *ctx, int ctas);
+int mpt_get_launch(const mpt_ctx *ctx, int *ctas);
+
+/*
+ * INT32 multiply-add throughput probe (sets the roofline of the limb
+ * products).  Runs instruction-form `variant` (0 mad.lo.u32, 1 mad.hi.u32,
+ * 2 mad.wide.u32, 3 limb product with mad.lo.cc/madc.hi.cc/addc, 4 two
+ * mad.wide.u32 on 16-bit halves, 5 mad.wide.u32 plus a wide carry word,
+ * 6 mad.lo.cc+addc and mad.hi.cc+addc, 7 mad.lo+mad.hi, 8 mul.wide plus
+ * add.cc chains) on one 1024-thread CTA per SM, 8 independent chains per
+ * thread, `iters` rounds.  Outputs: mean loop cycles of a CTA, kernel time in
+ * ms, number of distinct SMs used, grid size.  Allocates its own scratch
+ * buffers.  Returns 0 or a cudaError_t value.  (Not part of the paper: a
+ * measurement aid.)
+ */
+int mpt_int_peak_run(int variant, int iters, double *mean_cycles, double *ms, int *distinct_sms,
+                     int *grid_out);
+
+/* Message for an error code; message of the calling thread's last error. */
+const char *mpt_strerror(int code);
+const char *mpt_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPT_H */

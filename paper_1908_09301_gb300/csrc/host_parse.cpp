@@ -1,0 +1,288 @@
+// host_parse.cpp -- exact parsing of decimal / rational strings into L-limb
+// numbers (trunc_L of the exact value), on the host.
+//
+// The paper's constants (sigma = 10, R = 28, b = 8/3 after Eq. (1); tau = 0.01
+// and x(0) = -15.8, y(0) = -17.48, z(0) = 35.64 in Sec. 5) are not all binary
+// fractions, so each one enters the method as trunc_L of its exact rational
+// value.  This file holds a small unsigned big integer with exactly the
+// operations that needs: decimal digits in, shifts, comparison, subtraction
+// and long division.
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "host_parse.h"
+
+namespace mpt_host {
+namespace {
+
+struct BigU {
+    std::vector<uint32_t> w;  // little-endian limbs, no leading zeros
+
+    void trim()
+    {
+        while (!w.empty() && w.back() == 0) w.pop_back();
+    }
+    bool zero() const { return w.empty(); }
+    int bits() const
+    {
+        if (w.empty()) return 0;
+        uint32_t t = w.back();
+        int b = 0;
+        while (t) {
+            b++;
+            t >>= 1;
+        }
+        return (int)(w.size() - 1) * 32 + b;
+    }
+    void mul_small(uint32_t m)
+    {
+        uint64_t c = 0;
+        for (auto &x : w) {
+            uint64_t t = (uint64_t)x * m + c;
+            x = (uint32_t)t;
+            c = t >> 32;
+        }
+        if (c) w.push_back((uint32_t)c);
+    }
+    void add_small(uint32_t a)
+    {
+        uint64_t c = a;
+        for (size_t i = 0; i < w.size() && c; i++) {
+            uint64_t t = (uint64_t)w[i] + c;
+            w[i] = (uint32_t)t;
+            c = t >> 32;
+        }
+        if (c) w.push_back((uint32_t)c);
+    }
+    void shl(int64_t s)  // s >= 0 bits
+    {
+        if (w.empty() || s == 0) return;
+        size_t limbs = (size_t)(s / 32);
+        int r = (int)(s % 32);
+        std::vector<uint32_t> o(w.size() + limbs + 1, 0);
+        for (size_t i = 0; i < w.size(); i++) {
+            uint64_t v = (uint64_t)w[i] << r;
+            o[i + limbs] |= (uint32_t)v;
+            o[i + limbs + 1] |= (uint32_t)(v >> 32);
+        }
+        w.swap(o);
+        trim();
+    }
+    int bit(int64_t i) const
+    {
+        size_t l = (size_t)(i / 32);
+        if (l >= w.size()) return 0;
+        return (w[l] >> (i % 32)) & 1;
+    }
+};
+
+int cmp(const BigU &a, const BigU &b)
+{
+    if (a.w.size() != b.w.size()) return a.w.size() < b.w.size() ? -1 : 1;
+    for (size_t i = a.w.size(); i-- > 0;)
+        if (a.w[i] != b.w[i]) return a.w[i] < b.w[i] ? -1 : 1;
+    return 0;
+}
+
+void sub_inplace(BigU &a, const BigU &b)  // a -= b, requires a >= b
+{
+    int64_t borrow = 0;
+    for (size_t i = 0; i < a.w.size(); i++) {
+        int64_t t = (int64_t)a.w[i] - (i < b.w.size() ? b.w[i] : 0) - borrow;
+        borrow = t < 0;
+        a.w[i] = (uint32_t)(t + (borrow ? ((int64_t)1 << 32) : 0));
+    }
+    a.trim();
+}
+
+// floor(a / b), b != 0: restoring binary long division
+BigU divide(const BigU &a, const BigU &b)
+{
+    BigU q, r;
+    int nb = a.bits();
+    q.w.assign((size_t)nb / 32 + 1, 0);
+    for (int i = nb - 1; i >= 0; i--) {
+        r.shl(1);
+        if (a.bit(i)) {
+            if (r.w.empty()) r.w.push_back(0);
+            r.w[0] |= 1;
+        }
+        if (cmp(r, b) >= 0) {
+            sub_inplace(r, b);
+            q.w[(size_t)i / 32] |= 1u << (i % 32);
+        }
+    }
+    q.trim();
+    return q;
+}
+
+BigU pow10(int e)
+{
+    BigU p;
+    p.w.push_back(1);
+    for (int i = 0; i < e; i++) p.mul_small(10);
+    return p;
+}
+
+struct Rat {
+    bool neg = false;
+    BigU num, den;
+};
+
+const int kMaxDecimalExponent = 100000;
+
+bool parse_decimal(const char *&s, Rat &out)
+{
+    while (*s == ' ' || *s == '\t') s++;
+    bool neg = false;
+    if (*s == '+' || *s == '-') {
+        neg = *s == '-';
+        s++;
+    }
+    BigU digits;
+    int ndig = 0, frac = 0;
+    bool seen_point = false;
+    for (;; s++) {
+        if (*s >= '0' && *s <= '9') {
+            digits.mul_small(10);
+            digits.add_small((uint32_t)(*s - '0'));
+            digits.trim();
+            ndig++;
+            if (seen_point) frac++;
+        } else if (*s == '.' && !seen_point) {
+            seen_point = true;
+        } else {
+            break;
+        }
+    }
+    if (ndig == 0) return false;
+    long long e = 0;
+    if (*s == 'e' || *s == 'E') {
+        s++;
+        bool eneg = false;
+        if (*s == '+' || *s == '-') {
+            eneg = *s == '-';
+            s++;
+        }
+        int ed = 0;
+        while (*s >= '0' && *s <= '9') {
+            e = e * 10 + (*s - '0');
+            if (e > kMaxDecimalExponent) return false;
+            s++;
+            ed++;
+        }
+        if (ed == 0) return false;
+        if (eneg) e = -e;
+    }
+    long long scale = e - frac;
+    if (scale > kMaxDecimalExponent || scale < -kMaxDecimalExponent) return false;
+    out.neg = neg;
+    out.num = digits;
+    out.den.w.assign(1, 1);
+    if (scale >= 0) {
+        BigU p = pow10((int)scale);
+        // num *= 10^scale
+        BigU r;
+        r.w.assign(out.num.w.size() + p.w.size() + 1, 0);
+        for (size_t i = 0; i < out.num.w.size(); i++) {
+            uint64_t c = 0;
+            for (size_t j = 0; j < p.w.size(); j++) {
+                uint64_t t = (uint64_t)out.num.w[i] * p.w[j] + r.w[i + j] + c;
+                r.w[i + j] = (uint32_t)t;
+                c = t >> 32;
+            }
+            r.w[i + p.w.size()] += (uint32_t)c;
+        }
+        r.trim();
+        out.num = r;
+    } else {
+        out.den = pow10((int)-scale);
+    }
+    while (*s == ' ' || *s == '\t') s++;
+    return true;
+}
+
+BigU mul(const BigU &a, const BigU &b)
+{
+    BigU r;
+    if (a.zero() || b.zero()) return r;
+    r.w.assign(a.w.size() + b.w.size(), 0);
+    for (size_t i = 0; i < a.w.size(); i++) {
+        uint64_t c = 0;
+        for (size_t j = 0; j < b.w.size(); j++) {
+            uint64_t t = (uint64_t)a.w[i] * b.w[j] + r.w[i + j] + c;
+            r.w[i + j] = (uint32_t)t;
+            c = t >> 32;
+        }
+        r.w[i + b.w.size()] = (uint32_t)c;
+    }
+    r.trim();
+    return r;
+}
+
+bool parse_rational(const char *s, Rat &out)
+{
+    if (!s) return false;
+    Rat p;
+    if (!parse_decimal(s, p)) return false;
+    if (*s == '/') {
+        s++;
+        Rat q;
+        if (!parse_decimal(s, q)) return false;
+        if (q.num.zero()) return false;
+        out.neg = p.neg != q.neg;
+        out.num = mul(p.num, q.den);
+        out.den = mul(p.den, q.num);
+    } else {
+        out = p;
+    }
+    if (*s != '\0') return false;
+    if (out.num.zero()) out.neg = false;
+    return true;
+}
+
+}  // namespace
+
+// trunc_L of an exact decimal or rational string.  Returns 0, or -1 for a
+// malformed string, -3 for an exponent outside |exp| <= 2^30.
+int parse_number(const char *str, int L, int32_t *sign, int32_t *exp, uint32_t *limbs)
+{
+    Rat r;
+    if (!parse_rational(str, r)) return -1;
+    std::memset(limbs, 0, sizeof(uint32_t) * (size_t)L);
+    if (r.num.zero()) {
+        *sign = 0;
+        *exp = 0;
+        return 0;
+    }
+    // e with 2^(32(e-1)) <= num/den < 2^(32e)
+    long long e = ((long long)r.num.bits() - (long long)r.den.bits()) / 32;
+    auto ge_pow = [&](long long k) {  // num/den >= 2^(32k) ?
+        BigU a = r.num, b = r.den;
+        if (k >= 0)
+            b.shl(32 * k);
+        else
+            a.shl(-32 * k);
+        return cmp(a, b) >= 0;
+    };
+    while (ge_pow(e)) e++;
+    while (!ge_pow(e - 1)) e--;
+    if (e > (1LL << 30) || e < -(1LL << 30)) return -3;
+    // M = floor(num * 2^(32(L-e)) / den)
+    BigU a = r.num, b = r.den;
+    long long sh = 32LL * (L - e);
+    if (sh >= 0)
+        a.shl(sh);
+    else
+        b.shl(-sh);
+    BigU M = divide(a, b);
+    if ((int)M.w.size() != L || M.w[(size_t)L - 1] == 0) return -1;  // cannot happen
+    for (int j = 0; j < L; j++) limbs[j] = M.w[(size_t)j];
+    *sign = r.neg ? 1 : 0;
+    *exp = (int32_t)e;
+    return 0;
+}
+
+}  // namespace mpt_host

@@ -1,0 +1,513 @@
+// mpt_host.cu -- the C ABI of libmpt (declared in include/mpt.h): contexts,
+// device buffers, parameter and state conversion, launches and error codes.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/mpt.h"
+#include "host_parse.h"
+#include "mpt_kernel.cuh"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(MPT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// restores the caller's current device on scope exit
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) return;
+        ok = (prev == dev) || cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct mpt_ctx {
+    int L = 0, Lp = 0, P = 0, N = 0, Wcap = 0, tb = 0;
+    int dev = 0, sms = 0;
+    cudaStream_t st = nullptr;
+    int ctas_req = 0;
+    size_t smem = 0;
+    int max_grid = 0;
+    // device buffers
+    uint32_t *coefL = nullptr;
+    int32_t *coefE = nullptr, *coefF = nullptr;
+    uint32_t *parL = nullptr;
+    int32_t *parE = nullptr, *parF = nullptr;
+    uint32_t *stL = nullptr, *stBackL = nullptr;
+    int32_t *stE = nullptr, *stF = nullptr, *stBackEF = nullptr;
+    long long *gwin = nullptr;
+    unsigned *bar = nullptr;
+    int *status = nullptr;
+    int32_t *recS = nullptr, *recE = nullptr;
+    uint32_t *recL = nullptr;
+    long long rec_cap = 0;
+    bool have_coefficients = false;
+    // parameters in the interchange layout (host)
+    int32_t par_s[4] = {0, 0, 0, 0}, par_e[4] = {0, 0, 0, 0};
+    std::vector<uint32_t> par_l;
+};
+
+namespace {
+
+int grid_for(const mpt_ctx *c)
+{
+    int g = c->ctas_req;
+    if (g <= 0) {
+        // enough CTAs that the per-index work outweighs a grid barrier
+        double work = (double)c->N * c->Lp * c->Lp;
+        g = (int)std::lround(work / 50000.0);
+    }
+    if (g < 1) g = 1;
+    if (g > c->sms) g = c->sms;
+    if (g > c->max_grid) g = c->max_grid;
+    return g;
+}
+
+// interchange (sign, exp, L limbs) -> device layout (flags, exp, Lp limbs)
+int to_device_layout(const mpt_ctx *c, const int32_t *s, const int32_t *e, const uint32_t *l, int n,
+                     std::vector<uint32_t> &dl, std::vector<int32_t> &de, std::vector<int32_t> &df)
+{
+    dl.assign((size_t)n * c->Lp, 0u);
+    de.assign(n, 0);
+    df.assign(n, 0);
+    for (int j = 0; j < n; j++) {
+        const uint32_t *lj = l + (size_t)j * c->L;
+        bool zero = true;
+        for (int x = 0; x < c->L; x++) zero = zero && lj[x] == 0;
+        if (zero) {
+            if (s[j] != 0 || e[j] != 0)
+                return fail(MPT_EINVAL, "number %d: zero must have sign 0 and exp 0", j);
+            continue;
+        }
+        if (s[j] != 0 && s[j] != 1) return fail(MPT_EINVAL, "number %d: sign must be 0 or 1", j);
+        if (lj[c->L - 1] == 0) return fail(MPT_EINVAL, "number %d: top limb is zero", j);
+        if (e[j] > (1 << 30) || e[j] < -(1 << 30))
+            return fail(MPT_ERANGE, "number %d: exponent %d out of range", j, e[j]);
+        std::memcpy(&dl[(size_t)j * c->Lp], lj, sizeof(uint32_t) * c->L);
+        de[j] = e[j];
+        df[j] = mpt::F_NZ | (s[j] ? mpt::F_NEG : 0);
+    }
+    return MPT_OK;
+}
+
+void from_device_layout(const mpt_ctx *c, const std::vector<uint32_t> &dl,
+                        const std::vector<int32_t> &de, const std::vector<int32_t> &df, int n,
+                        int32_t *s, int32_t *e, uint32_t *l)
+{
+    for (int j = 0; j < n; j++) {
+        s[j] = (df[j] & mpt::F_NEG) ? 1 : 0;
+        e[j] = de[j];
+        std::memcpy(l + (size_t)j * c->L, &dl[(size_t)j * c->Lp], sizeof(uint32_t) * c->L);
+    }
+}
+
+int upload_state(mpt_ctx *c, const int32_t *s, const int32_t *e, const uint32_t *l)
+{
+    std::vector<uint32_t> dl;
+    std::vector<int32_t> de, df;
+    int rc = to_device_layout(c, s, e, l, 3, dl, de, df);
+    if (rc) return rc;
+    DeviceGuard g(c->dev);
+    cudaError_t ce = cudaMemcpyAsync(c->stL, dl.data(), sizeof(uint32_t) * 3 * c->Lp,
+                                     cudaMemcpyHostToDevice, c->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(c->stE, de.data(), sizeof(int32_t) * 3, cudaMemcpyHostToDevice, c->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(c->stF, df.data(), sizeof(int32_t) * 3, cudaMemcpyHostToDevice, c->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "state upload");
+    return MPT_OK;
+}
+
+void free_all(mpt_ctx *c)
+{
+    void *ptrs[] = {c->coefL, c->coefE, c->coefF, c->parL, c->parE, c->parF, c->stL, c->stBackL,
+                    c->stE, c->stF, c->stBackEF, c->gwin, c->bar, c->status, c->recS, c->recE,
+                    c->recL};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+}
+
+template <class T>
+cudaError_t dalloc(T **p, size_t count)
+{
+    return cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpt_limbs_for_digits(int K)
+{
+    if (K < 1) return fail(MPT_EINVAL, "K_digits must be >= 1");
+    return (int)std::ceil((double)K * 3.321928094887362 / 32.0);
+}
+
+const char *mpt_strerror(int code)
+{
+    switch (code) {
+        case MPT_OK: return "ok";
+        case MPT_EINVAL: return "invalid argument";
+        case MPT_ENOMEM: return "out of memory";
+        case MPT_ERANGE: return "exponent or accumulator range exceeded";
+        case MPT_ETIMEDOUT: return "a bounded device wait expired";
+        case MPT_ECUDA: return "CUDA error";
+        default: return "unknown error";
+    }
+}
+
+const char *mpt_last_error(void) { return g_last_error.c_str(); }
+
+int mpt_parse_number(const char *str, int L, int32_t *sign, int32_t *exp, uint32_t *limbs)
+{
+    if (!str || !sign || !exp || !limbs) return fail(MPT_EINVAL, "null argument");
+    if (L < 1 || L > mpt::MAX_L) return fail(MPT_EINVAL, "L = %d outside 1..%d", L, mpt::MAX_L);
+    int rc = mpt_host::parse_number(str, L, sign, exp, limbs);
+    if (rc == -3) return fail(MPT_ERANGE, "exponent of \"%s\" out of range", str);
+    if (rc) return fail(MPT_EINVAL, "malformed number \"%s\"", str);
+    return MPT_OK;
+}
+
+int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *tau,
+             const char *sigma, const char *R, const char *b, uint64_t cuda_stream)
+{
+    if (!out) return fail(MPT_EINVAL, "ctx pointer is null");
+    *out = nullptr;
+    int L = L_limbs;
+    if (L == 0) {
+        L = mpt_limbs_for_digits(K_digits);
+        if (L < 0) return L;
+    }
+    if (L < 1 || L > mpt::MAX_L) return fail(MPT_EINVAL, "L = %d outside 1..%d", L, mpt::MAX_L);
+    if (N_order < 1 || N_order > mpt::MAX_N)
+        return fail(MPT_EINVAL, "N = %d outside 1..%d", N_order, mpt::MAX_N);
+    mpt_ctx *c = new (std::nothrow) mpt_ctx();
+    if (!c) return fail(MPT_ENOMEM, "host allocation");
+    c->L = L;
+    c->Lp = (L + mpt::W - 1) / mpt::W * mpt::W;
+    c->P = c->Lp / mpt::W;
+    c->N = N_order;
+    int spread = c->Lp > 64 ? c->Lp : 64;
+    c->Wcap = (2 * c->Lp + 2 + spread + 31) / 32 * 32;
+    c->st = (cudaStream_t)(uintptr_t)cuda_stream;
+    // parameters: sigma, R, b, tau
+    const char *strs[4] = {sigma, R, b, tau};
+    const char *names[4] = {"sigma", "R", "b", "tau"};
+    c->par_l.assign((size_t)4 * L, 0u);
+    for (int j = 0; j < 4; j++) {
+        if (!strs[j]) {
+            delete c;
+            return fail(MPT_EINVAL, "%s is null", names[j]);
+        }
+        int rc = mpt_host::parse_number(strs[j], L, &c->par_s[j], &c->par_e[j],
+                                        &c->par_l[(size_t)j * L]);
+        if (rc) {
+            delete c;
+            return fail(rc == -3 ? MPT_ERANGE : MPT_EINVAL, "cannot use %s = \"%s\"", names[j],
+                        strs[j]);
+        }
+    }
+    cudaError_t ce = cudaGetDevice(&c->dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev);
+    int smem_optin = 0;
+    if (ce == cudaSuccess)
+        ce = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, c->dev);
+    if (ce != cudaSuccess) {
+        delete c;
+        return cuda_fail(ce, "device query");
+    }
+    // staging batch: as many terms as fit next to the fixed shared-memory parts
+    int tb = 64;
+    while (tb > 8 && mpt::smem_bytes(L, c->Lp, c->N, c->Wcap, tb) > (size_t)smem_optin) tb /= 2;
+    c->tb = tb;
+    c->smem = mpt::smem_bytes(L, c->Lp, c->N, c->Wcap, tb);
+    if (c->smem > (size_t)smem_optin) {
+        delete c;
+        return fail(MPT_EINVAL, "L = %d, N = %d need %zu bytes of shared memory (device has %d)", L,
+                    N_order, c->smem, smem_optin);
+    }
+    c->max_grid = mpt::max_coresident_ctas(c->smem);
+    if (c->max_grid < 1) {
+        delete c;
+        return fail(MPT_ECUDA, "kernel does not fit on the device");
+    }
+    const size_t N1 = (size_t)c->N + 1;
+    ce = dalloc(&c->coefL, 3 * N1 * c->Lp);
+    if (ce == cudaSuccess) ce = dalloc(&c->coefE, 3 * N1);
+    if (ce == cudaSuccess) ce = dalloc(&c->coefF, 3 * N1);
+    if (ce == cudaSuccess) ce = dalloc(&c->parL, (size_t)4 * c->Lp);
+    if (ce == cudaSuccess) ce = dalloc(&c->parE, 4);
+    if (ce == cudaSuccess) ce = dalloc(&c->parF, 4);
+    if (ce == cudaSuccess) ce = dalloc(&c->stL, (size_t)3 * c->Lp);
+    if (ce == cudaSuccess) ce = dalloc(&c->stBackL, (size_t)3 * c->Lp);
+    if (ce == cudaSuccess) ce = dalloc(&c->stE, 3);
+    if (ce == cudaSuccess) ce = dalloc(&c->stF, 3);
+    if (ce == cudaSuccess) ce = dalloc(&c->stBackEF, 6);
+    if (ce == cudaSuccess) ce = dalloc(&c->gwin, (size_t)9 * c->Wcap);
+    if (ce == cudaSuccess) ce = dalloc(&c->bar, 2);
+    if (ce == cudaSuccess) ce = dalloc(&c->status, 1);
+    if (ce != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return fail(ce == cudaErrorMemoryAllocation ? MPT_ENOMEM : MPT_ECUDA, "device allocation: %s",
+                    cudaGetErrorString(ce));
+    }
+    std::vector<uint32_t> dl;
+    std::vector<int32_t> de, df;
+    int rc = to_device_layout(c, c->par_s, c->par_e, c->par_l.data(), 4, dl, de, df);
+    if (rc) {
+        free_all(c);
+        delete c;
+        return rc;
+    }
+    ce = cudaMemcpy(c->parL, dl.data(), sizeof(uint32_t) * 4 * c->Lp, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(c->parE, de.data(), sizeof(int32_t) * 4, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(c->parF, df.data(), sizeof(int32_t) * 4, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemset(c->gwin, 0, sizeof(long long) * 9 * c->Wcap);
+    if (ce == cudaSuccess) ce = cudaMemset(c->stL, 0, sizeof(uint32_t) * 3 * c->Lp);
+    if (ce == cudaSuccess) ce = cudaMemset(c->stE, 0, sizeof(int32_t) * 3);
+    if (ce == cudaSuccess) ce = cudaMemset(c->stF, 0, sizeof(int32_t) * 3);
+    if (ce == cudaSuccess) ce = cudaMemset(c->coefL, 0, sizeof(uint32_t) * 3 * N1 * c->Lp);
+    if (ce == cudaSuccess) ce = cudaMemset(c->coefE, 0, sizeof(int32_t) * 3 * N1);
+    if (ce == cudaSuccess) ce = cudaMemset(c->coefF, 0, sizeof(int32_t) * 3 * N1);
+    if (ce != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return cuda_fail(ce, "device initialisation");
+    }
+    *out = c;
+    return MPT_OK;
+}
+
+void mpt_destroy(mpt_ctx *c)
+{
+    if (!c) return;
+    {
+        DeviceGuard g(c->dev);
+        cudaStreamSynchronize(c->st);
+        free_all(c);
+    }
+    delete c;
+}
+
+int mpt_get_dims(const mpt_ctx *c, int *L, int *N)
+{
+    if (!c || !L || !N) return fail(MPT_EINVAL, "null argument");
+    *L = c->L;
+    *N = c->N;
+    return MPT_OK;
+}
+
+int mpt_set_state(mpt_ctx *c, const char *x0, const char *y0, const char *z0)
+{
+    if (!c || !x0 || !y0 || !z0) return fail(MPT_EINVAL, "null argument");
+    int32_t s[3], e[3];
+    std::vector<uint32_t> l((size_t)3 * c->L);
+    const char *strs[3] = {x0, y0, z0};
+    for (int j = 0; j < 3; j++) {
+        int rc = mpt_host::parse_number(strs[j], c->L, &s[j], &e[j], &l[(size_t)j * c->L]);
+        if (rc)
+            return fail(rc == -3 ? MPT_ERANGE : MPT_EINVAL, "cannot use state \"%s\"", strs[j]);
+    }
+    return upload_state(c, s, e, l.data());
+}
+
+int mpt_set_state_raw(mpt_ctx *c, const int32_t *s, const int32_t *e, const uint32_t *l)
+{
+    if (!c || !s || !e || !l) return fail(MPT_EINVAL, "null argument");
+    return upload_state(c, s, e, l);
+}
+
+int mpt_get_state(mpt_ctx *c, int32_t *s, int32_t *e, uint32_t *l)
+{
+    if (!c || !s || !e || !l) return fail(MPT_EINVAL, "null argument");
+    DeviceGuard g(c->dev);
+    std::vector<uint32_t> dl((size_t)3 * c->Lp);
+    std::vector<int32_t> de(3), df(3);
+    cudaError_t ce = cudaMemcpyAsync(dl.data(), c->stL, sizeof(uint32_t) * 3 * c->Lp,
+                                     cudaMemcpyDeviceToHost, c->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(de.data(), c->stE, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, c->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(df.data(), c->stF, sizeof(int32_t) * 3, cudaMemcpyDeviceToHost, c->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "state download");
+    from_device_layout(c, dl, de, df, 3, s, e, l);
+    return MPT_OK;
+}
+
+int mpt_get_params(mpt_ctx *c, int32_t *s, int32_t *e, uint32_t *l)
+{
+    if (!c || !s || !e || !l) return fail(MPT_EINVAL, "null argument");
+    for (int j = 0; j < 4; j++) {
+        s[j] = c->par_s[j];
+        e[j] = c->par_e[j];
+    }
+    std::memcpy(l, c->par_l.data(), sizeof(uint32_t) * 4 * c->L);
+    return MPT_OK;
+}
+
+int mpt_set_launch(mpt_ctx *c, int ctas)
+{
+    if (!c) return fail(MPT_EINVAL, "null context");
+    if (ctas < 0 || ctas > c->sms || ctas > c->max_grid)
+        return fail(MPT_EINVAL, "ctas = %d outside 0..%d", ctas,
+                    c->sms < c->max_grid ? c->sms : c->max_grid);
+    c->ctas_req = ctas;
+    return MPT_OK;
+}
+
+int mpt_get_launch(const mpt_ctx *c, int *ctas)
+{
+    if (!c || !ctas) return fail(MPT_EINVAL, "null argument");
+    *ctas = grid_for(c);
+    return MPT_OK;
+}
+
+int mpt_integrate(mpt_ctx *c, int64_t nsteps, int64_t record_every, int32_t *rs, int32_t *re,
+                  uint32_t *rl)
+{
+    if (!c) return fail(MPT_EINVAL, "null context");
+    if (nsteps < 0) return fail(MPT_EINVAL, "nsteps < 0");
+    long long nrec = record_every > 0 ? nsteps / record_every : 0;
+    if (nrec > 0 && (!rs || !re || !rl)) return fail(MPT_EINVAL, "record pointers are null");
+    if (nsteps == 0) return MPT_OK;
+    DeviceGuard g(c->dev);
+    if (!g.ok) return fail(MPT_ECUDA, "cannot select the context's device");
+    cudaError_t ce = cudaSuccess;
+    if (nrec > c->rec_cap) {
+        if (c->recS) cudaFree(c->recS);
+        if (c->recE) cudaFree(c->recE);
+        if (c->recL) cudaFree(c->recL);
+        c->recS = c->recE = nullptr;
+        c->recL = nullptr;
+        c->rec_cap = 0;
+        ce = dalloc(&c->recS, (size_t)nrec * 3);
+        if (ce == cudaSuccess) ce = dalloc(&c->recE, (size_t)nrec * 3);
+        if (ce == cudaSuccess) ce = dalloc(&c->recL, (size_t)nrec * 3 * c->L);
+        if (ce != cudaSuccess)
+            return fail(ce == cudaErrorMemoryAllocation ? MPT_ENOMEM : MPT_ECUDA,
+                        "record buffer: %s", cudaGetErrorString(ce));
+        c->rec_cap = nrec;
+    }
+    // keep the starting state so that a failed launch leaves it unchanged
+    ce = cudaMemcpyAsync(c->stBackL, c->stL, sizeof(uint32_t) * 3 * c->Lp, cudaMemcpyDeviceToDevice, c->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(c->stBackEF, c->stE, sizeof(int32_t) * 3, cudaMemcpyDeviceToDevice, c->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(c->stBackEF + 3, c->stF, sizeof(int32_t) * 3, cudaMemcpyDeviceToDevice, c->st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->bar, 0, sizeof(unsigned) * 2, c->st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->status, 0, sizeof(int), c->st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->gwin, 0, sizeof(long long) * 9 * c->Wcap, c->st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "launch preparation");
+    mpt::KArgs a;
+    a.L = c->L;
+    a.Lp = c->Lp;
+    a.P = c->P;
+    a.N = c->N;
+    a.Wcap = c->Wcap;
+    a.tb = c->tb;
+    a.coefL = c->coefL;
+    a.coefE = c->coefE;
+    a.coefF = c->coefF;
+    a.parL = c->parL;
+    a.parE = c->parE;
+    a.parF = c->parF;
+    a.stL = c->stL;
+    a.stE = c->stE;
+    a.stF = c->stF;
+    a.gwin = c->gwin;
+    a.bar = c->bar;
+    a.status = c->status;
+    a.recS = c->recS;
+    a.recE = c->recE;
+    a.recL = c->recL;
+    a.nsteps = nsteps;
+    a.record_every = nrec > 0 ? record_every : 0;
+    const int grid = grid_for(c);
+    ce = mpt::launch_integrate(a, grid, c->smem, c->st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "kernel launch");
+    int status = 0;
+    ce = cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "kernel execution");
+    c->have_coefficients = true;
+    if (status != 0) {
+        cudaMemcpyAsync(c->stL, c->stBackL, sizeof(uint32_t) * 3 * c->Lp, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(c->stE, c->stBackEF, sizeof(int32_t) * 3, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemcpyAsync(c->stF, c->stBackEF + 3, sizeof(int32_t) * 3, cudaMemcpyDeviceToDevice, c->st);
+        cudaStreamSynchronize(c->st);
+        c->have_coefficients = false;
+        if (status == mpt::DEV_ERANGE)
+            return fail(MPT_ERANGE, "exponent out of range, or an exact sum spans more than %d limbs",
+                        c->Wcap);
+        if (status == mpt::DEV_TIMEOUT) return fail(MPT_ETIMEDOUT, "a grid barrier wait expired");
+        return fail(MPT_ECUDA, "device invariant failed (status %d)", status);
+    }
+    if (nrec > 0) {
+        ce = cudaMemcpyAsync(rs, c->recS, sizeof(int32_t) * nrec * 3, cudaMemcpyDefault, c->st);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(re, c->recE, sizeof(int32_t) * nrec * 3, cudaMemcpyDefault, c->st);
+        if (ce == cudaSuccess)
+            ce = cudaMemcpyAsync(rl, c->recL, sizeof(uint32_t) * nrec * 3 * c->L, cudaMemcpyDefault,
+                                 c->st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "record copy");
+    }
+    return MPT_OK;
+}
+
+int mpt_step(mpt_ctx *c) { return mpt_integrate(c, 1, 0, nullptr, nullptr, nullptr); }
+
+int mpt_get_coefficients(mpt_ctx *c, int32_t *s, int32_t *e, uint32_t *l)
+{
+    if (!c || !s || !e || !l) return fail(MPT_EINVAL, "null argument");
+    if (!c->have_coefficients) return fail(MPT_EINVAL, "no step has completed yet");
+    DeviceGuard g(c->dev);
+    const size_t n = (size_t)3 * (c->N + 1);
+    std::vector<uint32_t> dl(n * c->Lp);
+    std::vector<int32_t> de(n), df(n);
+    cudaError_t ce = cudaMemcpyAsync(dl.data(), c->coefL, sizeof(uint32_t) * n * c->Lp,
+                                     cudaMemcpyDeviceToHost, c->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(de.data(), c->coefE, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(df.data(), c->coefF, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, c->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "coefficient download");
+    from_device_layout(c, dl, de, df, (int)n, s, e, l);
+    return MPT_OK;
+}
+
+}  // extern "C"

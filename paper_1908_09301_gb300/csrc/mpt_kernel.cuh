@@ -1,0 +1,52 @@
+// mpt_kernel.cuh -- shared declarations between the host side of libmpt and
+// the Taylor-step kernel.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpt {
+
+constexpr int W = 8;         // columns per limb-product block (register tile)
+constexpr int NT = 256;      // threads per CTA
+constexpr int MAX_L = 1024;  // limbs per number
+constexpr int MAX_N = 4096;  // Taylor order (exponent tables live in shared memory)
+
+// status word values written by the device (0 = fine)
+constexpr int DEV_ERANGE = 1;    // exponent range or accumulator window exceeded
+constexpr int DEV_TIMEOUT = 2;   // a bounded wait expired
+constexpr int DEV_INTERNAL = 3;  // an internal invariant failed (carry did not settle)
+
+// flag bits of a stored number
+constexpr int F_NEG = 1;
+constexpr int F_NZ = 2;
+
+struct KArgs {
+    int L, Lp, P, N, Wcap;  // limbs, padded limbs (multiple of W), Lp / W, order, window
+    int tb;                 // terms per staging batch
+    uint32_t *coefL;        // [3][N+1][Lp]   coefficients of the current step
+    int32_t *coefE;         // [3][N+1]
+    int32_t *coefF;         // [3][N+1]
+    const uint32_t *parL;   // [4][Lp]        sigma, R, b, tau
+    const int32_t *parE;    // [4]
+    const int32_t *parF;    // [4]
+    uint32_t *stL;          // [3][Lp]        state (x, y, z)
+    int32_t *stE;           // [3]
+    int32_t *stF;           // [3]
+    long long *gwin;        // [3 sets][3 targets][Wcap] cross-CTA accumulators
+    unsigned *bar;          // [2] grid barrier: arrival count, generation
+    int *status;            // [1]
+    int32_t *recS;          // [nrec][3]      records in the interchange layout
+    int32_t *recE;          // [nrec][3]
+    uint32_t *recL;         // [nrec][3][L]
+    long long nsteps;
+    long long record_every;
+};
+
+// dynamic shared memory bytes for a configuration
+size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb);
+// launch nsteps steps on `grid` CTAs (cooperative when grid > 1)
+cudaError_t launch_integrate(const KArgs &a, int grid, size_t smem, cudaStream_t st);
+// largest co-resident grid for this smem size (0 on error)
+int max_coresident_ctas(size_t smem);
+
+}  // namespace mpt

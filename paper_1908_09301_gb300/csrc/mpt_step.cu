@@ -1,0 +1,964 @@
+// mpt_step.cu -- the multiple-precision Taylor step for the Lorenz system on
+// sm_103a: Eq. (3)'s coefficient recursion with its Cauchy sums, the
+// division by (i+1), and Eq. (2) evaluated by Horner's rule (Sec. 2 of
+// Dimova et al., arXiv 1908.09301).
+//
+// Layout and method (one persistent launch runs nsteps steps):
+//  * Numbers are L 32-bit limbs (padded with zero limbs to Lp, a multiple of
+//    W), an exponent in limbs and a flag word (sign, non-zero).  The
+//    coefficients of the running step live in global memory (they stay in
+//    L2); every CTA keeps the exponent and flag tables in shared memory.
+//  * Coefficient index m (Eq. (3) with i = m) is a set of "terms": the
+//    products of Eq. (3)'s brackets (sigma*beta_m, sigma*alpha_m, R*alpha_m,
+//    b*gamma_m and the 2(m+1) Cauchy products alpha_{m-k}gamma_k,
+//    alpha_{m-k}beta_k) plus the lone -beta_m.  Each term is an exact L x L
+//    limb product added into one of three exact accumulators (X, Y, Z for
+//    alpha, beta, gamma): int64 columns on the absolute 2^32 grid, with the
+//    window placed from the terms' exponents.  The Cauchy-sum reduction the
+//    paper parallelises over k with OpenMP (Sec. 3-4) is split here over
+//    CTAs (contiguous term ranges), threads (column pairs of a product) and
+//    registers (8-column Comba tiles with mad.lo.cc / madc.hi.cc / addc).
+//    Integer addition is associative, so partial sums of any split add up to
+//    the same exact value.
+//  * After all CTAs have added their partial windows into global memory, a
+//    grid barrier, then every CTA closes the three brackets redundantly:
+//    carry-normalise the window (warp-level carry resolution), take sign and
+//    magnitude, and divide by (m+1) with a warp-parallel long division (the
+//    remainder passes from chunk to chunk as an affine map mod (m+1), composed
+//    with a shuffle scan), truncating to L limbs.
+//  * Horner: h_N = c_N, h_i = trunc_L(tau*h_{i+1} + c_i): the same exact
+//    accumulator with a division by one, one CTA per component.
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mpt_kernel.cuh"
+
+namespace mpt {
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr long long SPIN_LIMIT = 40LL * 1000 * 1000;  // bounded waits (about a few seconds)
+
+__device__ __forceinline__ int phys(int x) { return x + (x >> 3); }
+
+// one 32x32 limb product added into a 96-bit column (c0, c1, c2)
+__device__ __forceinline__ void mac_cc(uint32_t a, uint32_t b, uint32_t &c0, uint32_t &c1,
+                                       uint32_t &c2)
+{
+    asm volatile(
+        "mad.lo.cc.u32 %0, %3, %4, %0;\n\t"
+        "madc.hi.cc.u32 %1, %3, %4, %1;\n\t"
+        "addc.u32 %2, %2, 0;"
+        : "+r"(c0), "+r"(c1), "+r"(c2)
+        : "r"(a), "r"(b));
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ int ld_volatile_int(const int *p)
+{
+    return *(volatile const int *)p;
+}
+
+__device__ __forceinline__ void set_status(int *status, int code)
+{
+    atomicCAS(status, 0, code);
+}
+
+// ------------------------------------------------------------------ smem
+
+struct Smem {
+    long long *win;   // [3][Wcap]
+    uint32_t *dig;    // [3][Wcap]
+    int *expT;        // [3][N+1]
+    int *flgT;        // [3][N+1]
+    uint32_t *newc;   // [3][Lp]
+    uint32_t *slots;  // [tb][AV + CV]
+    int *tinfo;       // [tb][2]
+    int *misc;        // [128]
+    int AV, CV, M;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline void vec_sizes(int Lp, int &AV, int &CV, int &M)
+{
+    M = Lp + W;
+    AV = Lp + Lp / 8 + 1;
+    CV = M + M / 8 + 1;
+}
+
+// misc slots
+enum {
+    MS_BASE = 0,    // [3] long long window base (lowest limb position) per target: ints 0..5
+    MS_WIDTH = 8,   // [3] window width (0 = no non-zero term)
+    MS_PNZ = 12,    // [4] non-zero limb count of each parameter
+    MS_RED = 16,    // [8 warps][6] long long reduction scratch -> ints 16..111
+    MS_HE = 112,    // [3] Horner: exponent of h per local component
+    MS_HF = 116,    // [3] Horner: flags of h
+    MS_ERR = 120,   // status snapshot shared by the CTA
+};
+
+// The status word as one value for the whole CTA, so that every thread takes
+// the same branch after it (a per-thread read could differ while another CTA
+// is writing it).
+__device__ __forceinline__ bool cta_ok(const Smem &S, const KArgs &a)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) S.misc[MS_ERR] = *(volatile const int *)a.status;
+    __syncthreads();
+    return S.misc[MS_ERR] == 0;
+}
+
+__device__ Smem carve(unsigned char *base, const KArgs &a)
+{
+    Smem S;
+    vec_sizes(a.Lp, S.AV, S.CV, S.M);
+    size_t o = 0;
+    S.win = (long long *)(base + o);
+    o = align16(o + sizeof(long long) * 3 * a.Wcap);
+    S.dig = (uint32_t *)(base + o);
+    o = align16(o + sizeof(uint32_t) * 3 * a.Wcap);
+    S.expT = (int *)(base + o);
+    o = align16(o + sizeof(int) * 3 * (a.N + 1));
+    S.flgT = (int *)(base + o);
+    o = align16(o + sizeof(int) * 3 * (a.N + 1));
+    S.newc = (uint32_t *)(base + o);
+    o = align16(o + sizeof(uint32_t) * 3 * a.Lp);
+    S.slots = (uint32_t *)(base + o);
+    o = align16(o + sizeof(uint32_t) * (size_t)a.tb * (S.AV + S.CV));
+    S.tinfo = (int *)(base + o);
+    o = align16(o + sizeof(int) * 2 * a.tb);
+    S.misc = (int *)(base + o);
+    return S;
+}
+
+// ------------------------------------------------------------------ block reductions
+
+__device__ __forceinline__ long long warp_min_ll(long long v)
+{
+    for (int o = 16; o; o >>= 1) {
+        long long w = __shfl_xor_sync(FULL, v, o);
+        v = w < v ? w : v;
+    }
+    return v;
+}
+__device__ __forceinline__ long long warp_max_ll(long long v)
+{
+    for (int o = 16; o; o >>= 1) {
+        long long w = __shfl_xor_sync(FULL, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
+}
+
+// ------------------------------------------------------------------ grid barrier
+
+// Sense-free generation barrier over all CTAs of a cooperative launch.  The
+// wait is bounded: on expiry the status word is set and every CTA unwinds.
+__device__ bool grid_barrier(const Smem &S, const KArgs &a)
+{
+    __syncthreads();
+    if (gridDim.x > 1) {
+        if (threadIdx.x == 0) {
+            unsigned gen = ld_acquire(&a.bar[1]);
+            __threadfence();
+            unsigned arrived = atomicAdd(&a.bar[0], 1u);
+            if (arrived == gridDim.x - 1) {
+                atomicExch(&a.bar[0], 0u);
+                __threadfence();
+                atomicAdd(&a.bar[1], 1u);
+            } else {
+                long long it = 0;
+                while (ld_acquire(&a.bar[1]) == gen) {
+                    if (++it > SPIN_LIMIT) {
+                        set_status(a.status, DEV_TIMEOUT);
+                        break;
+                    }
+                    if ((it & 255) == 0 && ld_volatile_int(a.status) != 0) break;
+                    __nanosleep(32);
+                }
+            }
+        }
+    }
+    return cta_ok(S, a);
+}
+
+// ------------------------------------------------------------------ terms of Eq. (3)
+
+// source of an operand: >= 0 coefficient (comp * (N+1) + index); < 0 parameter -1-p
+enum { P_SIGMA = 0, P_R = 1, P_B = 2, P_TAU = 3 };
+enum { T_X = 0, T_Y = 1, T_Z = 2 };
+
+struct Term {
+    int target;  // 0 X (alpha), 1 Y (beta), 2 Z (gamma)
+    int neg;     // the bracket subtracts this term
+    int add;     // lone number (no product): c = bsrc
+    int asrc, bsrc;
+};
+
+// Terms of the brackets of Eq. (3) at i = m (T = 2m + 7 of them):
+//   X: +sigma beta_m, -sigma alpha_m
+//   Y: +R alpha_m, -beta_m, -sum_{k=0}^{m} alpha_{m-k} gamma_k
+//   Z: -b gamma_m, +sum_{k=0}^{m} alpha_{m-k} beta_k
+__device__ __forceinline__ Term term_of(int m, int t, int N1)
+{
+    Term r;
+    r.add = 0;
+    if (t == 0) { r.target = T_X; r.neg = 0; r.asrc = -1 - P_SIGMA; r.bsrc = 1 * N1 + m; }
+    else if (t == 1) { r.target = T_X; r.neg = 1; r.asrc = -1 - P_SIGMA; r.bsrc = 0 * N1 + m; }
+    else if (t == 2) { r.target = T_Y; r.neg = 0; r.asrc = -1 - P_R; r.bsrc = 0 * N1 + m; }
+    else if (t == 3) { r.target = T_Y; r.neg = 1; r.add = 1; r.asrc = 0; r.bsrc = 1 * N1 + m; }
+    else if (t == 4) { r.target = T_Z; r.neg = 1; r.asrc = -1 - P_B; r.bsrc = 2 * N1 + m; }
+    else if (t <= 5 + m) {
+        int k = t - 5;
+        r.target = T_Y; r.neg = 1; r.asrc = 0 * N1 + (m - k); r.bsrc = 2 * N1 + k;
+    } else {
+        int k = t - 6 - m;
+        r.target = T_Z; r.neg = 0; r.asrc = 0 * N1 + (m - k); r.bsrc = 1 * N1 + k;
+    }
+    return r;
+}
+
+struct Meta {
+    int e, f;
+};
+
+__device__ __forceinline__ Meta meta_of(const Smem &S, const KArgs &a, int src)
+{
+    Meta r;
+    if (src >= 0) {
+        r.e = S.expT[src];
+        r.f = S.flgT[src];
+    } else {
+        r.e = __ldg(&a.parE[-1 - src]);
+        r.f = __ldg(&a.parF[-1 - src]);
+    }
+    return r;
+}
+
+// limb x of an operand: parameter, the newest coefficient (index m, kept in
+// shared memory by every CTA) or an older coefficient from global memory
+__device__ __forceinline__ uint32_t fetch_limb(const Smem &S, const KArgs &a, int src, int m, int x)
+{
+    if (src < 0) return __ldg(&a.parL[(size_t)(-1 - src) * a.Lp + x]);
+    const int N1 = a.N + 1;
+    int comp = src / N1, idx = src - comp * N1;
+    if (idx == m) return S.newc[comp * a.Lp + x];
+    return __ldcg(&a.coefL[(size_t)src * a.Lp + x]);
+}
+
+// ------------------------------------------------------------------ the limb-product tile
+
+// Columns of the exact product A*B (Lp x Lp limbs): column c = sum_i a_i b_{c-i}.
+// A thread owns the column pair block1 = [qW, qW+W) and block2 = [qW+Lp, qW+Lp+W);
+// together they hold exactly W*Lp products, so every pair costs the same.  It
+// walks s = 0 .. Lp+W-1: block1 for s < (q+1)W (i = s), block2 after it
+// (i = s - W).  The window of W b-limbs slides down one limb per step through
+// a cyclic copy C of B padded with W zeros (C[x] = b_x for x < Lp, 0 for
+// Lp <= x < Lp+W), which makes the hand-over from block1 to block2 seamless;
+// the block1 sums are saved at the hand-over (a predicated copy, so the warp
+// never diverges) and block2 = final - saved.
+template <bool SPARSE>
+__device__ void mac_pair(const uint32_t *A, const uint32_t *C, int q, int P, int Lp, int M,
+                         long long *win, int off, bool neg)
+{
+    uint32_t a0[W], a1[W], a2[W], s0[W], s1[W], s2[W], bw[W];
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        a0[k] = a1[k] = a2[k] = 0u;
+        s0[k] = s1[k] = s2[k] = 0u;
+        bw[k] = C[phys(q * W + k)];
+    }
+    for (int j = 0; j <= P; j++) {
+        const bool snap = (j == q + 1);
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            s0[k] = snap ? a0[k] : s0[k];
+            s1[k] = snap ? a1[k] : s1[k];
+            s2[k] = snap ? a2[k] : s2[k];
+        }
+        const int ib = (j <= q) ? j * W : (j - 1) * W;
+        const uint32_t *Ap = A + phys(ib);
+        int xg = (q - j - 1) * W;
+        if (xg < 0) xg += M;
+        const uint32_t *Cp = C + phys(xg);
+#pragma unroll
+        for (int u = 0; u < W; u++) {
+            const uint32_t av = Ap[u];
+            if (!SPARSE || av != 0u) {
+#pragma unroll
+                for (int k = 0; k < W; k++) mac_cc(av, bw[k], a0[k], a1[k], a2[k]);
+            }
+#pragma unroll
+            for (int k = W - 1; k > 0; k--) bw[k] = bw[k - 1];
+            bw[0] = Cp[W - 1 - u];
+        }
+    }
+    // block1 = saved sums at columns qW + t, block2 = final - saved at qW + Lp + t
+    long long *w1 = win + off + q * W;
+    long long *w2 = w1 + Lp;
+#pragma unroll
+    for (int t = 0; t < W + 2; t++) {
+        long long v1 = 0, v2 = 0;
+        if (t < W) {
+            v1 += s0[t];
+            v2 += (long long)a0[t] - s0[t];
+        }
+        if (t >= 1 && t - 1 < W) {
+            v1 += s1[t - 1];
+            v2 += (long long)a1[t - 1] - s1[t - 1];
+        }
+        if (t >= 2 && t - 2 < W) {
+            v1 += s2[t - 2];
+            v2 += (long long)a2[t - 2] - s2[t - 2];
+        }
+        if (neg) {
+            v1 = -v1;
+            v2 = -v2;
+        }
+        if (v1) atomicAdd((unsigned long long *)&w1[t], (unsigned long long)v1);
+        if (v2) atomicAdd((unsigned long long *)&w2[t], (unsigned long long)v2);
+    }
+}
+
+// a lone number +-c: limbs [qW, qW+W) of c (staged in A layout) into the window
+__device__ void add_unit(const uint32_t *A, int q, long long *win, int off, bool neg)
+{
+#pragma unroll
+    for (int k = 0; k < W; k++) {
+        long long v = A[phys(q * W + k)];
+        if (v) atomicAdd((unsigned long long *)&win[off + q * W + k],
+                         (unsigned long long)(neg ? -v : v));
+    }
+}
+
+// ------------------------------------------------------------------ close: normalise, divide
+
+struct Norm {
+    int neg;
+    int top;  // index of the top non-zero digit, -1 for zero
+};
+
+// Exact value of Wn int64 columns (sum col[c] 2^(32c)) as sign and magnitude
+// digits.  One warp; lane l owns columns [lK, lK+K).  Local carries first,
+// then the carries that cross lanes ride up one lane per round until none is
+// left (any carry is absorbed or passed on, so 32 rounds always suffice).
+__device__ Norm warp_normalize(const long long *col, bool from_global, uint32_t *dig, int Wn,
+                               int *status)
+{
+    const int lane = threadIdx.x & 31;
+    const int K = (Wn + 31) >> 5;
+    const int c0 = lane * K;
+    const int c1 = min(c0 + K, Wn);
+    long long carry = 0;
+    for (int c = c0; c < c1; c++) {
+        long long v = (from_global ? __ldcg(&col[c]) : col[c]) + carry;
+        dig[c] = (uint32_t)v;
+        carry = v >> 32;
+    }
+    long long top = 0;
+    bool settled = false;
+    for (int round = 0; round < 40; round++) {
+        top += __shfl_sync(FULL, carry, 31);
+        long long cin = __shfl_up_sync(FULL, carry, 1);
+        if (lane == 0) cin = 0;
+        if (!__any_sync(FULL, cin != 0)) {
+            settled = true;
+            break;
+        }
+        long long c = cin;
+        for (int cc = c0; cc < c1 && c != 0; cc++) {
+            long long v = (long long)dig[cc] + c;
+            dig[cc] = (uint32_t)v;
+            c = v >> 32;
+        }
+        carry = c;
+    }
+    if (!settled && lane == 0) set_status(status, DEV_INTERNAL);
+    Norm r;
+    r.neg = top < 0;
+    if (r.neg) {
+        // |V| = 2^(32 Wn) - D: digits below the lowest non-zero one stay 0,
+        // that one becomes 2^32 - d, the ones above are complemented
+        int zl = 0x7fffffff;
+        for (int c = c1 - 1; c >= c0; c--)
+            if (dig[c]) zl = c;
+        int z = zl;
+        for (int o = 16; o; o >>= 1) z = min(z, __shfl_xor_sync(FULL, z, o));
+        for (int c = c0; c < c1; c++) {
+            if (c > z) dig[c] = ~dig[c];
+            else if (c == z) dig[c] = 0u - dig[c];
+        }
+    }
+    int tl = -1;
+    for (int c = c0; c < c1; c++)
+        if (dig[c]) tl = c;
+    for (int o = 16; o; o >>= 1) tl = max(tl, __shfl_xor_sync(FULL, tl, o));
+    r.top = tl;
+    __syncwarp();
+    return r;
+}
+
+// (hi * 2^32 + lo) div/mod d for r = hi < d < 2^16, in two 16-bit halves
+__device__ __forceinline__ uint32_t divstep(uint32_t &r, uint32_t x, uint32_t d)
+{
+    uint32_t n1 = (r << 16) | (x >> 16);
+    uint32_t q1 = n1 / d;
+    uint32_t r1 = n1 - q1 * d;
+    uint32_t n0 = (r1 << 16) | (x & 0xffffu);
+    uint32_t q0 = n0 / d;
+    r = n0 - q0 * d;
+    return (q1 << 16) | q0;
+}
+
+// trunc_L(|E| / d) for |E| = sum_c dig[c] 2^(32(base+c)) with top digit t:
+// writes L limbs to out (lanes write their own chunks) and returns the exponent.
+// Only limbs of |E| at or above the quotient's lowest kept position matter
+// (floor(|E| / (d 2^(32 s))) = floor(floor(|E| / 2^(32 s)) / d)); below the
+// window's lowest limb they are zero.
+__device__ long long warp_divide(const uint32_t *dig, int t, long long base, uint32_t d, int L,
+                                 uint32_t *out)
+{
+    const int lane = threadIdx.x & 31;
+    const long long T = base + t + 1;
+    const long long eq = (dig[t] >= d) ? T : T - 1;
+    const long long s = eq - L;
+    const int nX = (int)(T - s);
+    const int KX = (nX + 31) >> 5;
+    const int jhi = min(nX - lane * KX, nX);
+    const int jlo = max(jhi - KX, 0);
+    auto X = [&](int j) -> uint32_t {
+        long long idx = s + j - base;
+        return idx >= 0 ? dig[idx] : 0u;
+    };
+    if (d == 1u) {
+        for (int j = jhi - 1; j >= jlo; j--)
+            if (j < L) out[j] = X(j);
+        __syncwarp();
+        return eq;
+    }
+    // this lane's chunk as an affine map r -> (Pm r + V) mod d
+    uint32_t V = 0, Pm = 1;
+    uint32_t t32 = 0;
+    {
+        uint32_t rr = 1;  // 2^32 mod d
+        (void)divstep(rr, 0u, d);
+        t32 = rr;
+    }
+    for (int j = jhi - 1; j >= jlo; j--) {
+        (void)divstep(V, X(j), d);
+        Pm = (Pm * t32) % d;
+    }
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t Po = __shfl_up_sync(FULL, Pm, o);
+        uint32_t Vo = __shfl_up_sync(FULL, V, o);
+        if (lane >= o) {
+            V = (Pm * Vo + V) % d;
+            Pm = (Pm * Po) % d;
+        }
+    }
+    uint32_t r = __shfl_up_sync(FULL, V, 1);
+    if (lane == 0) r = 0;
+    for (int j = jhi - 1; j >= jlo; j--) {
+        uint32_t qd = divstep(r, X(j), d);
+        if (j < L) out[j] = qd;
+    }
+    __syncwarp();
+    return eq;
+}
+
+// ------------------------------------------------------------------ phases
+
+__device__ void init_slots(const Smem &S, const KArgs &a)
+{
+    // C-layout padding (x in [Lp, M)) stays zero for the whole launch
+    for (int e = threadIdx.x; e < a.tb * S.M; e += NT) {
+        int slot = e / S.M, x = e - slot * S.M;
+        uint32_t *Cv = S.slots + (size_t)slot * (S.AV + S.CV) + S.AV;
+        if (x >= a.Lp) Cv[phys(x)] = 0u;
+    }
+    for (int e = threadIdx.x; e < 3 * a.Wcap; e += NT) S.win[e] = 0;
+}
+
+// block-wide min (lo) / max (hi) for three targets; returns in S.misc
+__device__ void reduce_windows(const Smem &S, const KArgs &a, long long lo[3], long long hi[3])
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    long long *red = (long long *)(S.misc + MS_RED);  // [8][6] long long = 96 ints
+    for (int tg = 0; tg < 3; tg++) {
+        long long l = warp_min_ll(lo[tg]), h = warp_max_ll(hi[tg]);
+        if (lane == 0) {
+            red[warp * 6 + tg] = l;
+            red[warp * 6 + 3 + tg] = h;
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 3) {
+        int tg = threadIdx.x;
+        long long l = red[tg], h = red[3 + tg];
+        for (int w = 1; w < NT / 32; w++) {
+            l = min(l, red[w * 6 + tg]);
+            h = max(h, red[w * 6 + 3 + tg]);
+        }
+        int width = 0;
+        if (h > l) {
+            if (h - l > a.Wcap) {
+                set_status(a.status, DEV_ERANGE);
+            } else {
+                width = (int)(h - l);
+            }
+        }
+        ((long long *)(S.misc + MS_BASE))[tg] = l;
+        S.misc[MS_WIDTH + tg] = width;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ long long win_base(const Smem &S, int tg)
+{
+    return ((const long long *)(S.misc + MS_BASE))[tg];
+}
+
+// window placement for coefficient index m: lowest limb position over the
+// non-zero terms of each bracket and the highest position the exact sum can
+// reach (product: 2Lp columns plus two carry limbs of the 96-bit column sums
+// and of the sum's growth; lone number: Lp limbs plus two).
+__device__ void place_windows(const Smem &S, const KArgs &a, int m)
+{
+    const int T = 2 * m + 7;
+    const int N1 = a.N + 1;
+    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
+    long long hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
+    for (int t = threadIdx.x; t < T; t += NT) {
+        Term tm = term_of(m, t, N1);
+        Meta mb = meta_of(S, a, tm.bsrc);
+        if (!(mb.f & F_NZ)) continue;
+        long long lp, top;
+        if (tm.add) {
+            lp = (long long)mb.e - a.L;
+            top = lp + a.Lp + 2;
+        } else {
+            Meta ma = meta_of(S, a, tm.asrc);
+            if (!(ma.f & F_NZ)) continue;
+            lp = (long long)ma.e - a.L + (long long)mb.e - a.L;
+            top = lp + 2 * a.Lp + 2;
+        }
+        lo[tm.target] = min(lo[tm.target], lp);
+        hi[tm.target] = max(hi[tm.target], top);
+    }
+    reduce_windows(S, a, lo, hi);
+}
+
+// stage terms [t0, t0 + nt) of index m into slots; record offset and flags
+__device__ void stage_terms(const Smem &S, const KArgs &a, int m, int t0, int nt)
+{
+    const int N1 = a.N + 1;
+    const int Lp = a.Lp;
+    for (int e = threadIdx.x; e < nt * 2 * Lp; e += NT) {
+        int slot = e / (2 * Lp);
+        int r = e - slot * 2 * Lp;
+        int which = r >= Lp;  // 0: A operand, 1: B operand
+        int x = r - which * Lp;
+        Term tm = term_of(m, t0 + slot, N1);
+        uint32_t *base = S.slots + (size_t)slot * (S.AV + S.CV);
+        if (tm.add) {
+            if (which == 0) base[phys(x)] = fetch_limb(S, a, tm.bsrc, m, x);
+        } else if (which == 0) {
+            base[phys(x)] = fetch_limb(S, a, tm.asrc, m, x);
+        } else {
+            base[S.AV + phys(x)] = fetch_limb(S, a, tm.bsrc, m, x);
+        }
+    }
+    for (int slot = threadIdx.x; slot < nt; slot += NT) {
+        Term tm = term_of(m, t0 + slot, N1);
+        Meta mb = meta_of(S, a, tm.bsrc);
+        int flags = 0, off = 0;
+        bool skip = !(mb.f & F_NZ);
+        long long lp = 0;
+        int neg = tm.neg ^ (mb.f & F_NEG);
+        if (tm.add) {
+            lp = (long long)mb.e - a.L;
+            flags |= 2;
+        } else {
+            Meta ma = meta_of(S, a, tm.asrc);
+            skip = skip || !(ma.f & F_NZ);
+            neg ^= (ma.f & F_NEG);
+            lp = (long long)ma.e - a.L + (long long)mb.e - a.L;
+            if (tm.asrc < 0 && S.misc[MS_PNZ + (-1 - tm.asrc)] * 8 <= Lp) flags |= 8;  // sparse
+        }
+        if (skip) flags |= 4;
+        if (!skip) off = (int)(lp - win_base(S, tm.target));
+        flags |= neg ? 1 : 0;
+        flags |= tm.target << 4;
+        S.tinfo[2 * slot] = off;
+        S.tinfo[2 * slot + 1] = flags;
+    }
+}
+
+__device__ void run_unit(const Smem &S, const KArgs &a, int slot, int q)
+{
+    const int off = S.tinfo[2 * slot];
+    const int flags = S.tinfo[2 * slot + 1];
+    if (flags & 4) return;
+    const int tg = (flags >> 4) & 3;
+    const bool neg = flags & 1;
+    const uint32_t *A = S.slots + (size_t)slot * (S.AV + S.CV);
+    long long *win = S.win + (size_t)tg * a.Wcap;
+    if (flags & 2) {
+        add_unit(A, q, win, off, neg);
+    } else if (flags & 8) {
+        mac_pair<true>(A, A + S.AV, q, a.P, a.Lp, S.M, win, off, neg);
+    } else {
+        mac_pair<false>(A, A + S.AV, q, a.P, a.Lp, S.M, win, off, neg);
+    }
+}
+
+// this CTA's share of the products of index m, added into the shared windows
+// and then into the global accumulators
+__device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
+{
+    const int G = gridDim.x, g = blockIdx.x;
+    place_windows(S, a, m);
+    if (!cta_ok(S, a)) return;
+    if (G > 1) {
+        // clear the accumulator set that the next index will use (last read
+        // by the close two indices back, which every CTA finished before the
+        // previous barrier); sets rotate over the running index of the launch
+        long long *nxt = a.gwin + (size_t)((set + 1) % 3) * 3 * a.Wcap;
+        for (int e = g * NT + threadIdx.x; e < 3 * a.Wcap; e += G * NT) nxt[e] = 0;
+    }
+    const long long T = 2 * m + 7;
+    const long long U = T * a.P;
+    const long long u0 = U * g / G, u1 = U * (g + 1) / G;
+    if (u0 < u1) {
+        const int tA = (int)(u0 / a.P), tB = (int)((u1 - 1) / a.P);
+        for (int tb0 = tA; tb0 <= tB; tb0 += a.tb) {
+            const int nt = min(a.tb, tB - tb0 + 1);
+            stage_terms(S, a, m, tb0, nt);
+            __syncthreads();
+            const long long ua = max(u0, (long long)tb0 * a.P);
+            const long long ub = min(u1, (long long)(tb0 + nt) * a.P);
+            for (long long u = ua + threadIdx.x; u < ub; u += NT) {
+                const int t = (int)(u / a.P);
+                run_unit(S, a, t - tb0, (int)(u - (long long)t * a.P));
+            }
+            __syncthreads();
+        }
+    }
+    if (G > 1) {
+        long long *dst = a.gwin + (size_t)set * 3 * a.Wcap;
+        for (int tg = 0; tg < 3; tg++) {
+            const int wd = S.misc[MS_WIDTH + tg];
+            for (int c = threadIdx.x; c < wd; c += NT) {
+                long long v = S.win[tg * a.Wcap + c];
+                if (v) {
+                    atomicAdd((unsigned long long *)&dst[tg * a.Wcap + c], (unsigned long long)v);
+                    S.win[tg * a.Wcap + c] = 0;
+                }
+            }
+        }
+    }
+}
+
+// the three brackets of index m -> coefficients m+1 (every CTA, redundantly)
+__device__ void close_phase(const Smem &S, const KArgs &a, int m, int set)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G = gridDim.x;
+    const int N1 = a.N + 1;
+    if (warp < 3) {
+        const int tg = warp;  // 0 alpha, 1 beta, 2 gamma
+        const int wd = S.misc[MS_WIDTH + tg];
+        uint32_t *out = S.newc + tg * a.Lp;
+        int e = 0, f = 0;
+        if (wd > 0) {
+            const long long *src = (G > 1) ? a.gwin + ((size_t)set * 3 + tg) * a.Wcap
+                                            : S.win + (size_t)tg * a.Wcap;
+            uint32_t *dig = S.dig + (size_t)tg * a.Wcap;
+            Norm nr = warp_normalize(src, G > 1, dig, wd, a.status);
+            if (G == 1)
+                for (int c = lane; c < wd; c += 32) S.win[tg * a.Wcap + c] = 0;
+            if (nr.top >= 0) {
+                long long eq = warp_divide(dig, nr.top, win_base(S, tg), (uint32_t)(m + 1), a.L, out);
+                if (eq > (1LL << 30) || eq < -(1LL << 30)) {
+                    if (lane == 0) set_status(a.status, DEV_ERANGE);
+                    eq = 0;
+                }
+                e = (int)eq;
+                f = F_NZ | (nr.neg ? F_NEG : 0);
+            }
+        }
+        if (!(f & F_NZ))
+            for (int x = lane; x < a.L; x += 32) out[x] = 0u;
+        for (int x = a.L + lane; x < a.Lp; x += 32) out[x] = 0u;
+        __syncwarp();
+        if (lane == 0) {
+            S.expT[tg * N1 + m + 1] = e;
+            S.flgT[tg * N1 + m + 1] = f;
+        }
+        if (blockIdx.x == 0) {
+            uint32_t *g = a.coefL + ((size_t)tg * N1 + m + 1) * a.Lp;
+            for (int x = lane; x < a.Lp; x += 32) g[x] = out[x];
+            if (lane == 0) {
+                a.coefE[tg * N1 + m + 1] = e;
+                a.coefF[tg * N1 + m + 1] = f;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Horner for the components this CTA owns: h_N = c_N,
+// h_i = trunc_L(tau*h_{i+1} + c_i), i = N-1 .. 0.  Slot layout:
+// slot 2j: tau (A layout) and h_j (C layout); slot 2j+1: c_i (A layout).
+__device__ void horner_phase(const Smem &S, const KArgs &a, int step)
+{
+    const int G = gridDim.x, g = blockIdx.x;
+    int c_first, nc;
+    if (G >= 3) {
+        if (g >= 3) return;
+        c_first = g;
+        nc = 1;
+    } else {
+        if (g != 0) return;
+        c_first = 0;
+        nc = 3;
+    }
+    const int N1 = a.N + 1, Lp = a.Lp, N = a.N;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int SL = S.AV + S.CV;
+    // h meta per local component in misc: e at 32+j, f at 36+j
+    int *hE = S.misc + MS_HE, *hF = S.misc + MS_HF;
+    // stage tau and h = c_N, c_{N-1}
+    for (int j = 0; j < nc; j++) {
+        const int comp = c_first + j;
+        uint32_t *s0 = S.slots + (size_t)(2 * j) * SL;
+        uint32_t *s1 = S.slots + (size_t)(2 * j + 1) * SL;
+        for (int x = threadIdx.x; x < Lp; x += NT) {
+            s0[phys(x)] = __ldg(&a.parL[(size_t)P_TAU * Lp + x]);
+            s0[S.AV + phys(x)] = S.newc[comp * Lp + x];  // coefficient N
+            s1[phys(x)] = __ldcg(&a.coefL[((size_t)comp * N1 + N - 1) * Lp + x]);
+        }
+        if (threadIdx.x == 0) {
+            hE[j] = S.expT[comp * N1 + N];
+            hF[j] = S.flgT[comp * N1 + N];
+        }
+    }
+    const int tauE = __ldg(&a.parE[P_TAU]), tauF = __ldg(&a.parF[P_TAU]);
+    __syncthreads();
+    for (int i = N - 1; i >= 0; i--) {
+        // prefetch c_{i-1} into registers while the products of step i run
+        uint32_t pre[3][4];
+        if (i > 0) {
+            for (int j = 0; j < nc; j++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    int x = threadIdx.x + r * NT;
+                    pre[j][r] = x < Lp
+                        ? __ldcg(&a.coefL[((size_t)(c_first + j) * N1 + i - 1) * Lp + x]) : 0u;
+                }
+        }
+        // window placement and term info
+        if (threadIdx.x < nc) {
+            const int j = threadIdx.x, comp = c_first + j;
+            const int ce = S.expT[comp * N1 + i], cf = S.flgT[comp * N1 + i];
+            long long lo = LLONG_MAX, hi = LLONG_MIN;
+            int off0 = 0, off1 = 0, fl0 = 4, fl1 = 4 | 2;
+            long long lp0 = 0, lp1 = 0;
+            if ((hF[j] & F_NZ) && (tauF & F_NZ)) {
+                lp0 = (long long)hE[j] - a.L + (long long)tauE - a.L;
+                lo = min(lo, lp0);
+                hi = max(hi, lp0 + 2 * Lp + 2);
+                fl0 = ((hF[j] ^ tauF) & F_NEG) ? 1 : 0;
+            }
+            if (cf & F_NZ) {
+                lp1 = (long long)ce - a.L;
+                lo = min(lo, lp1);
+                hi = max(hi, lp1 + Lp + 2);
+                fl1 = 2 | ((cf & F_NEG) ? 1 : 0);
+            }
+            int width = 0;
+            if (hi > lo) {
+                if (hi - lo > a.Wcap) set_status(a.status, DEV_ERANGE);
+                else width = (int)(hi - lo);
+            }
+            if (!(fl0 & 4)) off0 = (int)(lp0 - lo);
+            if (!(fl1 & 4)) off1 = (int)(lp1 - lo);
+            S.tinfo[2 * (2 * j)] = off0;
+            S.tinfo[2 * (2 * j) + 1] = fl0 | (j << 4);
+            S.tinfo[2 * (2 * j + 1)] = off1;
+            S.tinfo[2 * (2 * j + 1) + 1] = fl1 | (j << 4);
+            ((long long *)(S.misc + MS_BASE))[j] = lo;
+            S.misc[MS_WIDTH + j] = width;
+        }
+        if (!cta_ok(S, a)) return;
+        const int units = 2 * nc * a.P;
+        for (int u = threadIdx.x; u < units; u += NT) {
+            const int slot = u / a.P;
+            run_unit(S, a, slot, u - slot * a.P);
+        }
+        __syncthreads();
+        // close: h_i for each component (division by one = truncation)
+        if (warp < nc) {
+            const int j = warp;
+            const int wd = S.misc[MS_WIDTH + j];
+            uint32_t *hC = S.slots + (size_t)(2 * j) * SL + S.AV;
+            uint32_t *hp = S.newc + (size_t)(c_first + j) * Lp;  // plain copy of h
+            int e = 0, f = 0;
+            if (wd > 0) {
+                uint32_t *dig = S.dig + (size_t)j * a.Wcap;
+                Norm nr = warp_normalize(S.win + (size_t)j * a.Wcap, false, dig, wd, a.status);
+                for (int c = lane; c < wd; c += 32) S.win[j * a.Wcap + c] = 0;
+                if (nr.top >= 0) {
+                    long long eq = warp_divide(dig, nr.top, win_base(S, j), 1u, a.L, hp);
+                    if (eq > (1LL << 30) || eq < -(1LL << 30)) {
+                        if (lane == 0) set_status(a.status, DEV_ERANGE);
+                        eq = 0;
+                    }
+                    e = (int)eq;
+                    f = F_NZ | (nr.neg ? F_NEG : 0);
+                }
+            }
+            if (!(f & F_NZ))
+                for (int x = lane; x < a.L; x += 32) hp[x] = 0u;
+            __syncwarp();
+            for (int x = lane; x < Lp; x += 32) hC[phys(x)] = x < a.L ? hp[x] : 0u;
+            if (lane == 0) {
+                hE[j] = e;
+                hF[j] = f;
+            }
+        }
+        // c_{i-1} into the lone-number slots
+        if (i > 0) {
+            for (int j = 0; j < nc; j++)
+#pragma unroll
+                for (int r = 0; r < 4; r++) {
+                    int x = threadIdx.x + r * NT;
+                    if (x < Lp) S.slots[(size_t)(2 * j + 1) * SL + phys(x)] = pre[j][r];
+                }
+        }
+        __syncthreads();
+    }
+    // the new state and, when due, a record
+    const long long rec = (a.record_every > 0 && ((step + 1) % a.record_every) == 0)
+                              ? (step + 1) / a.record_every - 1 : -1;
+    for (int j = 0; j < nc; j++) {
+        const int comp = c_first + j;
+        const uint32_t *hp = S.newc + (size_t)comp * Lp;
+        for (int x = threadIdx.x; x < Lp; x += NT) a.stL[comp * Lp + x] = hp[x];
+        if (rec >= 0)
+            for (int x = threadIdx.x; x < a.L; x += NT)
+                a.recL[((size_t)rec * 3 + comp) * a.L + x] = hp[x];
+        if (threadIdx.x == 0) {
+            a.stE[comp] = hE[j];
+            a.stF[comp] = hF[j];
+            if (rec >= 0) {
+                a.recS[rec * 3 + comp] = (hF[j] & F_NEG) ? 1 : 0;
+                a.recE[rec * 3 + comp] = hE[j];
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(NT, 1) taylor_kernel(KArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem S = carve(smem_raw, a);
+    const int N1 = a.N + 1;
+    if (threadIdx.x < 4) {
+        int nz = 0;
+        for (int x = 0; x < a.Lp; x++) nz += __ldg(&a.parL[(size_t)threadIdx.x * a.Lp + x]) != 0u;
+        S.misc[MS_PNZ + threadIdx.x] = nz;
+    }
+    init_slots(S, a);
+    __syncthreads();
+    for (long long step = 0; step < a.nsteps; step++) {
+        // alpha_0, beta_0, gamma_0 = the state (Sec. 2)
+        for (int e = threadIdx.x; e < 3 * a.Lp; e += NT) {
+            uint32_t v = __ldcg(&a.stL[e]);
+            S.newc[e] = v;
+            if (blockIdx.x == 0) {
+                int comp = e / a.Lp, x = e - comp * a.Lp;
+                a.coefL[(size_t)comp * N1 * a.Lp + x] = v;
+            }
+        }
+        if (threadIdx.x < 3) {
+            int e = __ldcg(&a.stE[threadIdx.x]), f = __ldcg(&a.stF[threadIdx.x]);
+            S.expT[threadIdx.x * N1] = e;
+            S.flgT[threadIdx.x * N1] = f;
+            if (blockIdx.x == 0) {
+                a.coefE[threadIdx.x * N1] = e;
+                a.coefF[threadIdx.x * N1] = f;
+            }
+        }
+        __syncthreads();
+        bool ok = true;
+        for (int m = 0; m < a.N && ok; m++) {
+            const int set = (int)((step * a.N + m) % 3);
+            term_phase(S, a, m, set);
+            ok = grid_barrier(S, a);
+            if (!ok) break;
+            close_phase(S, a, m, set);
+            ok = cta_ok(S, a);
+        }
+        if (!ok) break;
+        if (!grid_barrier(S, a)) break;
+        horner_phase(S, a, (int)step);
+        if (!grid_barrier(S, a)) break;
+    }
+}
+
+}  // namespace
+
+size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb)
+{
+    (void)L;
+    int AV, CV, M;
+    vec_sizes(Lp, AV, CV, M);
+    size_t o = 0;
+    o = align16(o + sizeof(long long) * 3 * Wcap);
+    o = align16(o + sizeof(uint32_t) * 3 * Wcap);
+    o = align16(o + sizeof(int) * 3 * (N + 1));
+    o = align16(o + sizeof(int) * 3 * (N + 1));
+    o = align16(o + sizeof(uint32_t) * 3 * Lp);
+    o = align16(o + sizeof(uint32_t) * (size_t)tb * (AV + CV));
+    o = align16(o + sizeof(int) * 2 * tb);
+    o = align16(o + sizeof(int) * 128);
+    return o;
+}
+
+int max_coresident_ctas(size_t smem)
+{
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    if (cudaFuncSetAttribute(taylor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, taylor_kernel, NT, smem) != cudaSuccess)
+        return 0;
+    return per * sms;
+}
+
+cudaError_t launch_integrate(const KArgs &a, int grid, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(taylor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    KArgs copy = a;
+    if (grid <= 1) {
+        taylor_kernel<<<1, NT, smem, st>>>(copy);
+        return cudaGetLastError();
+    }
+    void *args[] = {&copy};
+    return cudaLaunchCooperativeKernel((const void *)taylor_kernel, dim3(grid), dim3(NT), args,
+                                       smem, st);
+}
+
+}  // namespace mpt

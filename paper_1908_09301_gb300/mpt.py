@@ -1,0 +1,222 @@
+"""ctypes binding of libmpt (the C ABI in ``include/mpt.h``).
+
+Argument marshalling only: every step of the Taylor method runs in the CUDA
+kernels of ``libmpt.so``.  There is no CPU fallback -- if the library cannot
+be loaded the import of :func:`lib` raises.
+
+Numbers cross the boundary in the interchange layout of ``include/mpt.h``:
+``signs[n]`` (int32, 0/1), ``exps[n]`` (int32, limb exponent) and
+``limbs[n, L]`` (uint32, least significant first).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpt.so")
+
+MPT_OK, MPT_EINVAL, MPT_ENOMEM, MPT_ERANGE, MPT_ETIMEDOUT, MPT_ECUDA = 0, -1, -2, -3, -4, -5
+
+_lock = threading.Lock()
+_lib = None
+
+i32p = ctypes.POINTER(ctypes.c_int32)
+u32p = ctypes.POINTER(ctypes.c_uint32)
+vp = ctypes.c_void_p
+
+# name -> (restype, argtypes); every symbol include/mpt.h declares
+SIGNATURES = {
+    "mpt_limbs_for_digits": (ctypes.c_int, [ctypes.c_int]),
+    "mpt_init": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p,
+                                ctypes.c_uint64]),
+    "mpt_destroy": (None, [vp]),
+    "mpt_parse_number": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int, vp, vp, vp]),
+    "mpt_get_dims": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int)]),
+    "mpt_set_state": (ctypes.c_int, [vp, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p]),
+    "mpt_set_state_raw": (ctypes.c_int, [vp, vp, vp, vp]),
+    "mpt_get_state": (ctypes.c_int, [vp, vp, vp, vp]),
+    "mpt_get_params": (ctypes.c_int, [vp, vp, vp, vp]),
+    "mpt_step": (ctypes.c_int, [vp]),
+    "mpt_integrate": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int64, vp, vp, vp]),
+    "mpt_get_coefficients": (ctypes.c_int, [vp, vp, vp, vp]),
+    "mpt_set_launch": (ctypes.c_int, [vp, ctypes.c_int]),
+    "mpt_get_launch": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
+    "mpt_int_peak_run": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int)]),
+    "mpt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "mpt_last_error": (ctypes.c_char_p, []),
+}
+
+
+class MPTError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"mpt error {code}: {msg}")
+        self.code = code
+
+
+def lib(build_if_missing: bool = True) -> ctypes.CDLL:
+    """The loaded libmpt.so (built in-tree by ``build.py`` when absent)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if build_if_missing:
+                from . import build as _build
+                _build.build()
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libmpt.so not found at {LIB_PATH}: run the build first")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != MPT_OK:
+        msg = lib().mpt_last_error().decode(errors="replace")
+        raise MPTError(rc, msg)
+
+
+def limbs_for_digits(K: int) -> int:
+    rc = lib().mpt_limbs_for_digits(int(K))
+    if rc < 0:
+        _check(rc)
+    return rc
+
+
+def parse_number(text: str, L: int):
+    """trunc_L of a decimal or rational string: (sign, exp, limbs[L]) (host only)."""
+    s = np.zeros(1, np.int32)
+    e = np.zeros(1, np.int32)
+    l = np.zeros(L, np.uint32)
+    _check(lib().mpt_parse_number(str(text).encode(), int(L), _ptr(s), _ptr(e), _ptr(l)))
+    return int(s[0]), int(e[0]), [int(x) for x in l]
+
+
+def _ptr(a):
+    """Pointer of a numpy array or a torch tensor (host or device)."""
+    if isinstance(a, np.ndarray):
+        assert a.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(a.ctypes.data)
+    if hasattr(a, "data_ptr"):
+        assert a.is_contiguous()
+        return ctypes.c_void_p(a.data_ptr())
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _current_stream() -> int:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return int(torch.cuda.current_stream().cuda_stream)
+    except ImportError:  # pragma: no cover
+        pass
+    return 0
+
+
+class Context:
+    """One integrator context (``mpt_init`` .. ``mpt_destroy``)."""
+
+    def __init__(self, N: int, L: int = 0, K: int = 0, tau: str = "0.01", sigma: str = "10",
+                 R: str = "28", b: str = "8/3", stream: int | None = None):
+        self._h = vp()
+        if stream is None:
+            stream = _current_stream()
+        _check(lib().mpt_init(ctypes.byref(self._h), int(K), int(N), int(L), str(tau).encode(),
+                              str(sigma).encode(), str(R).encode(), str(b).encode(),
+                              ctypes.c_uint64(int(stream))))
+        l, n = ctypes.c_int(), ctypes.c_int()
+        _check(lib().mpt_get_dims(self._h, ctypes.byref(l), ctypes.byref(n)))
+        self.L, self.N = l.value, n.value
+
+    def close(self):
+        if self._h:
+            lib().mpt_destroy(self._h)
+            self._h = vp()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # pragma: no cover
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # -- numbers
+    def _empty(self, n: int):
+        return (np.zeros(n, np.int32), np.zeros(n, np.int32), np.zeros((n, self.L), np.uint32))
+
+    def set_state(self, x0: str, y0: str, z0: str):
+        _check(lib().mpt_set_state(self._h, str(x0).encode(), str(y0).encode(), str(z0).encode()))
+
+    def set_state_raw(self, signs, exps, limbs):
+        s = np.ascontiguousarray(signs, np.int32)
+        e = np.ascontiguousarray(exps, np.int32)
+        l = np.ascontiguousarray(limbs, np.uint32).reshape(3, self.L)
+        _check(lib().mpt_set_state_raw(self._h, _ptr(s), _ptr(e), _ptr(l)))
+
+    def get_state(self):
+        s, e, l = self._empty(3)
+        _check(lib().mpt_get_state(self._h, _ptr(s), _ptr(e), _ptr(l)))
+        return s, e, l
+
+    def params(self):
+        s, e, l = self._empty(4)
+        _check(lib().mpt_get_params(self._h, _ptr(s), _ptr(e), _ptr(l)))
+        return s, e, l
+
+    def coefficients(self):
+        s, e, l = self._empty(3 * (self.N + 1))
+        _check(lib().mpt_get_coefficients(self._h, _ptr(s), _ptr(e), _ptr(l)))
+        return s, e, l
+
+    # -- stepping
+    def step(self):
+        _check(lib().mpt_step(self._h))
+
+    def integrate(self, nsteps: int, record_every: int = 0, out=None):
+        """nsteps steps in one launch.  With record_every > 0 the records go to
+        ``out`` = (signs, exps, limbs) (numpy arrays or torch tensors, host or
+        device) or to new numpy arrays, which are returned."""
+        nrec = nsteps // record_every if record_every > 0 else 0
+        if nrec == 0:
+            _check(lib().mpt_integrate(self._h, int(nsteps), 0, None, None, None))
+            return None
+        if out is None:
+            out = (np.zeros((nrec, 3), np.int32), np.zeros((nrec, 3), np.int32),
+                   np.zeros((nrec, 3, self.L), np.uint32))
+        _check(lib().mpt_integrate(self._h, int(nsteps), int(record_every), _ptr(out[0]),
+                                   _ptr(out[1]), _ptr(out[2])))
+        return out
+
+    def set_launch(self, ctas: int):
+        _check(lib().mpt_set_launch(self._h, int(ctas)))
+
+    def launch(self) -> int:
+        c = ctypes.c_int()
+        _check(lib().mpt_get_launch(self._h, ctypes.byref(c)))
+        return c.value
+
+
+def int_peak(variant: int, iters: int = 20000):
+    """INT32 multiply-add probe: (results per SM per clock, ms, sms, grid)."""
+    cyc, ms = ctypes.c_double(), ctypes.c_double()
+    ds, g = ctypes.c_int(), ctypes.c_int()
+    rc = lib().mpt_int_peak_run(int(variant), int(iters), ctypes.byref(cyc), ctypes.byref(ms),
+                                ctypes.byref(ds), ctypes.byref(g))
+    if rc != 0:
+        raise MPTError(MPT_ECUDA, f"int peak probe failed with CUDA error {rc}")
+    per_clk = iters * 8 * 1024 / cyc.value
+    return per_clk, ms.value, ds.value, g.value

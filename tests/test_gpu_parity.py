@@ -1,0 +1,190 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer work, so the bar is bit-exact: signs, exponents and every limb of
+every coefficient and every recorded state.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mpt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_09301_gb300 import mpt as M
+    M.lib()
+    return M
+
+
+def gpu_ctx(mpt, L, N, par=(O.SIGMA, O.R, O.B, O.TAU), x0=O.X0, ctas=0):
+    c = mpt.Context(N=N, L=L, sigma=par[0], R=par[1], b=par[2], tau=par[3])
+    c.set_state(*x0)
+    if ctas:
+        c.set_launch(ctas)
+    return c
+
+
+def oracle_run(L, N, par=(O.SIGMA, O.R, O.B, O.TAU), x0=O.X0, nsteps=1, record_every=0):
+    p = O.params(L, *par)
+    s = O.state(L, x0)
+    return O.integrate(L, N, nsteps, p, s, record_every, nthreads=O.default_threads())
+
+
+def oracle_coefficients(L, N, par=(O.SIGMA, O.R, O.B, O.TAU), x0=O.X0):
+    return O.coefficients(L, N, O.params(L, *par), O.state(L, x0), nthreads=O.default_threads())
+
+
+def same(gpu, orc):
+    s, e, l = gpu
+    return (np.array_equal(s.reshape(-1), orc.sign) and np.array_equal(e.reshape(-1), orc.exp)
+            and np.array_equal(l.reshape(len(orc), -1), orc.limbs))
+
+
+def first_mismatch(gpu, orc):
+    s, e, l = gpu
+    l = l.reshape(len(orc), -1)
+    for j in range(len(orc)):
+        if s.reshape(-1)[j] != orc.sign[j] or e.reshape(-1)[j] != orc.exp[j] or \
+                not np.array_equal(l[j], orc.limbs[j]):
+            return j, (int(s.reshape(-1)[j]), int(e.reshape(-1)[j])), (int(orc.sign[j]), int(orc.exp[j]))
+    return None
+
+
+def test_parameters_match_oracle(mpt):
+    c = gpu_ctx(mpt, 11, 5)
+    assert same(c.params(), O.params(11))
+    c.close()
+
+
+@pytest.mark.parametrize("L,N", [(1, 5), (2, 7), (3, 20), (11, 60), (13, 25), (21, 40), (53, 30),
+                                 (8, 9), (9, 64)])
+def test_one_step_coefficients(mpt, L, N):
+    """Eq. (3) coefficients alpha_0..alpha_N etc. and the Horner state, bit for bit."""
+    c = gpu_ctx(mpt, L, N)
+    c.step()
+    want = oracle_coefficients(L, N)
+    got = c.coefficients()
+    assert same(got, want), first_mismatch(got, want)
+    fin, _ = oracle_run(L, N)
+    assert same(c.get_state(), fin)
+    c.close()
+
+
+@pytest.mark.parametrize("ctas", [1, 2, 3, 5, 17])
+def test_launch_shape_invariance(mpt, ctas):
+    """The exact sums make the result independent of how the GPU splits them."""
+    L, N = 21, 90
+    c = gpu_ctx(mpt, L, N, ctas=ctas)
+    c.integrate(3)
+    fin, _ = oracle_run(L, N, nsteps=3)
+    assert same(c.get_state(), fin)
+    prev, _ = oracle_run(L, N, nsteps=2)
+    want = O.coefficients(L, N, O.params(L), prev)
+    assert same(c.coefficients(), want)
+    c.close()
+
+
+def test_k100_n60_full_run(mpt):
+    """100 digits, N = 60, 1000 steps of tau = 0.01 (t in [0, 10]), every 100th state."""
+    L, N, steps, every = 11, 60, 1000, 100
+    c = gpu_ctx(mpt, L, N)
+    rec = c.integrate(steps, every)
+    _, orec = oracle_run(L, N, nsteps=steps, record_every=every)
+    assert same(rec, orec), first_mismatch(rec, orec)
+    c.close()
+
+
+EDGE = [
+    # name, L, N, params, x0
+    ("origin", 4, 12, (O.SIGMA, O.R, O.B, O.TAU), ("0", "0", "0")),
+    ("x_y_zero", 5, 20, (O.SIGMA, O.R, O.B, O.TAU), ("0", "0", "35.64")),
+    ("fixed_point_b3", 6, 15, (O.SIGMA, O.R, "3", O.TAU), ("9", "9", "27")),
+    ("mirrored", 7, 30, (O.SIGMA, O.R, O.B, O.TAU), ("15.8", "17.48", "35.64")),
+    ("tiny_x", 4, 25, ("10.5", "28", "3", "1/64"), ("-1e-30", "17.48", "-35.64")),
+    ("odd_params", 5, 20, ("-2", "0.5", "8/3", "0.01"), ("4.294967296", "-4.294967295", "1e-3")),
+    ("rational_state", 3, 33, (O.SIGMA, O.R, O.B, O.TAU), ("1/3", "-2/7", "5/11")),
+    ("n_equals_1", 9, 1, (O.SIGMA, O.R, O.B, O.TAU), O.X0),
+    ("l_equals_1", 1, 40, (O.SIGMA, O.R, O.B, O.TAU), O.X0),
+]
+
+
+@pytest.mark.parametrize("name,L,N,par,x0", EDGE, ids=[e[0] for e in EDGE])
+def test_edge_cases(mpt, name, L, N, par, x0):
+    c = gpu_ctx(mpt, L, N, par, x0)
+    rec = c.integrate(6, 1)
+    _, orec = oracle_run(L, N, par, x0, nsteps=6, record_every=1)
+    assert same(rec, orec), first_mismatch(rec, orec)
+    c.close()
+
+
+def test_symmetry_bit_exact(mpt):
+    """(x, y, z) -> (-x, -y, z) maps GPU runs onto each other exactly."""
+    L, N = 11, 60
+    a = gpu_ctx(mpt, L, N, x0=("-15.8", "-17.48", "35.64"))
+    b = gpu_ctx(mpt, L, N, x0=("15.8", "17.48", "35.64"))
+    a.integrate(20)
+    b.integrate(20)
+    sa, ea, la = a.get_state()
+    sb, eb, lb = b.get_state()
+    assert np.array_equal(la, lb) and np.array_equal(ea, eb)
+    assert sa[2] == sb[2] and sa[0] == 1 - sb[0] and sa[1] == 1 - sb[1]
+
+
+def test_spread_beyond_accumulator_is_erange(mpt):
+    """Terms 500+ limbs apart cannot share one exact window: MPT_ERANGE, and the
+    state is left as it was."""
+    c = gpu_ctx(mpt, 2, 5, x0=("1e-5000", "17.48", "35.64"))
+    before = c.get_state()
+    with pytest.raises(mpt.MPTError) as ei:
+        c.step()
+    assert ei.value.code == mpt.MPT_ERANGE
+    after = c.get_state()
+    assert all(np.array_equal(x, y) for x, y in zip(before, after))
+    c.close()
+
+
+def test_state_roundtrip_and_raw(mpt):
+    L = 7
+    c = gpu_ctx(mpt, L, 10)
+    s, e, l = c.get_state()
+    assert same((s, e, l), O.state(L))
+    st = O.state(L, ("1/7", "-3", "2e-9"))
+    c.set_state_raw(st.sign, st.exp, st.limbs)
+    assert same(c.get_state(), st)
+    bad = st.limbs.copy()
+    bad[0, L - 1] = 0  # not normalised
+    with pytest.raises(mpt.MPTError):
+        c.set_state_raw(st.sign, st.exp, bad)
+    c.close()
+
+
+def test_k500_n300_steps(mpt):
+    """500 digits (53 limbs), N = 300: five steps, every state."""
+    L, N = 53, 300
+    c = gpu_ctx(mpt, L, N)
+    rec = c.integrate(5, 1)
+    _, orec = oracle_run(L, N, nsteps=5, record_every=1)
+    assert same(rec, orec), first_mismatch(rec, orec)
+    want = O.coefficients(L, N, O.params(L), oracle_run(L, N, nsteps=4)[0],
+                          nthreads=O.default_threads())
+    assert same(c.coefficients(), want)
+    c.close()
+
+
+def test_k2000_n1000_step(mpt):
+    """Paper-scale step (2000 digits = 208 limbs, N = 1000) in the benchmark's
+    launch shape: every coefficient and the new state, bit for bit."""
+    L, N = 208, 1000
+    c = gpu_ctx(mpt, L, N)
+    c.step()
+    want = oracle_coefficients(L, N)
+    got = c.coefficients()
+    assert same(got, want), first_mismatch(got, want)
+    fin, _ = oracle_run(L, N)
+    assert same(c.get_state(), fin)
+    c.close()
