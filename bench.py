@@ -1,0 +1,321 @@
+#!/usr/bin/env python
+"""Benchmark of the multiple-precision Taylor step for the Lorenz system.
+
+One bench step = one Taylor step (Eq. (3)'s N coefficients with their exact
+Cauchy sums, the divisions by i+1, and Eq. (2) by Horner) of the paper-scale
+workload: 2000 decimal digits (208 limbs), order N = 1000, tau = 0.01, from
+Sec. 5's point (-15.8, -17.48, 35.64).  The state is synthetic only in the
+sense that it is the paper's benchmark point; nothing is read from disk.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+
+Prints one JSON line.  ``value`` = Taylor steps/s of the whole job (all
+ranks), device-timed with CUDA events per launch, L2 flushed between timed
+steps.  ``e2e`` = the same metric through the C ABI with the state coming
+from and going back to host memory every step.  ``roofline`` compares the
+limb-product rate with the INT32 multiply-add roofline (bound "alu").
+``cpu_baseline`` times the CPU oracle on a bounded sample on the host's cores.
+Multi-GPU (torchrun): independent replicas, one per rank, no collective on the
+data path ("replicas only": a single trajectory does not shard).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1908_09301_gb300 import workloads as WL  # noqa: E402
+
+METRIC = "Taylor steps/sec and INT32 limb-MAC fraction of peak at K digits, N order (bit-exact)"
+UNIT = "steps/s"
+# 32-bit integer multiply-add results per SM per clock on this architecture
+# (measured by the library's probe: mad.lo.u32 retires 64 per SM per clock);
+# one exact limb product needs a low and a high half, so the limb-product
+# roofline is half of it.
+IMAD_PER_SM_CLK = 64
+PROFILE = os.path.join(ROOT, "profiles", "taylor_kernel_k2000_n1000.md")
+KERNEL_SOURCES = ["paper_1908_09301_gb300/csrc/mpt_step.cu",
+                  "paper_1908_09301_gb300/csrc/mpt_kernel.cuh"]
+
+
+def kernel_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources (else None)."""
+    if not os.path.exists(PROFILE):
+        return None
+    vals = {}
+    for line in open(PROFILE):
+        line = line.strip().lstrip("-* ")
+        if ":" in line:
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    try:
+        if vals.get("kernel_source_hash") != kernel_hash():
+            return None
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p))
+        except ValueError:
+            return {}
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.path = os.path.join("/tmp", f"mpt_clocks_{os.getpid()}.csv")
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(device_index)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def cpu_oracle_rate(wl, nsteps: int):
+    """Oracle (plain C, OpenMP over all host cores with the paper's container
+    reduction) on nsteps full Taylor steps of the workload."""
+    from oracle import oracle as O
+    O.build()
+    threads = O.default_threads()
+    p, s = O.params(wl.L), O.state(wl.L, wl.x0)
+    t0 = time.perf_counter()
+    O.integrate(wl.L, wl.N, nsteps, p, s, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return nsteps / dt, threads, dt
+
+
+def reference_arm(args, wl):
+    """The reference arm of this repository is the CPU oracle itself."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    O.build()
+    threads = O.default_threads()
+    p, s = O.params(wl.L), O.state(wl.L, wl.x0)
+    O.integrate(wl.L, wl.N, args.warmup, p, s, nthreads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        s, _ = O.integrate(wl.L, wl.N, 1, p, s, nthreads=threads)
+        times.append(time.perf_counter() - t0)
+    ms = 1000.0 * sum(times) / len(times)
+    value = 1000.0 / ms
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (Sec. 5 initial point)",
+        "config": config_of(wl, None),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{args.steps} full Taylor steps of {wl.name}"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_of(wl, ctas):
+    return {"workload": wl.name, "K_digits": wl.K, "L_limbs": wl.L, "N_order": wl.N,
+            "tau": wl.tau, "x0": list(wl.x0), "ctas": ctas,
+            "l2": "flushed between timed steps (256 MiB memset)",
+            "parallelism": "replicas"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default=WL.HEADLINE, choices=sorted(WL.WORKLOADS))
+    ap.add_argument("--ctas", type=int, default=0, help="CTAs of the launch (0 = library choice)")
+    ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    wl = WL.WORKLOADS[args.workload]
+    if args.impl == "reference":
+        return reference_arm(args, wl)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1908_09301_gb300 import mpt
+
+    stream = torch.cuda.current_stream()
+    ctx = mpt.Context(N=wl.N, L=wl.L, tau=wl.tau, stream=stream.cuda_stream)
+    ctx.set_state(*wl.x0)
+    if args.ctas:
+        ctx.set_launch(args.ctas)
+    ctas = ctx.launch()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+
+    # live INT32 probe (mad.lo.u32, and the limb-product form the kernel uses)
+    probe = {}
+    for v, name in ((0, "mad.lo.u32"), (3, "limb product mad.lo.cc/madc.hi.cc/addc")):
+        per_clk, _, sms, _ = mpt.int_peak(v, 4000)
+        probe[name] = round(per_clk, 2)
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+
+    for _ in range(args.warmup):
+        ctx.launch_async(1)
+        ctx.wait()
+
+    # device-timed region: one launch per Taylor step, L2 flushed in between
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    for i in range(args.steps):
+        flush.zero_()
+        starts[i].record(stream)
+        ctx.launch_async(1)
+        ends[i].record(stream)
+        ctx.wait()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    if dist is not None:
+        dist.barrier()
+    ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_per_step = sum(ms_steps) / len(ms_steps)
+    if dist is not None:
+        t = torch.tensor([ms_per_step], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_per_step = float(t.item())
+    value = world * 1000.0 / ms_per_step
+
+    # end to end through the C ABI: host state in, one step, host state out
+    s0, e0, l0 = ctx.get_state()
+    hs, he, hl = s0.copy(), e0.copy(), l0.copy()
+    h2d = hs.nbytes + he.nbytes + hl.nbytes
+    for _ in range(2):
+        ctx.set_state_raw(hs, he, hl)
+        ctx.step()
+        hs, he, hl = ctx.get_state()
+    if dist is not None:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_state_raw(hs, he, hl)
+        ctx.step()
+        hs, he, hl = ctx.get_state()
+    e2e_s = time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = world * args.steps / e2e_s
+
+    work = wl.work_per_step()
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * IMAD_PER_SM_CLK / 2 * sm_max * 1e6
+    achieved = work / (ms_per_step / 1000.0)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (Sec. 5 initial point, exact decimal inputs)",
+        "config": config_of(wl, ctas),
+        "gpu_launches": args.steps,
+        "limb_macs_per_step": work,
+        "limb_macs_per_s": achieved * world,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                     "unit": "limb-MAC/s", "frac": achieved / peak,
+                     "traffic": profiled_traffic(),
+                     "peak_source": (f"derived: {sms} SMs x {IMAD_PER_SM_CLK} INT32 multiply-adds "
+                                     f"per SM per clock / 2 per limb product x {sm_max:.0f} MHz"),
+                     "probe_per_sm_per_clk": probe},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(h2d)},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, threads, dt = cpu_oracle_rate(wl, args.cpu_steps)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": f"{args.cpu_steps} full Taylor steps of {wl.name} "
+                                          f"({dt:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

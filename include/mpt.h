@@ -120,6 +120,15 @@ int mpt_integrate(mpt_ctx *ctx, int64_t nsteps, int64_t record_every, int32_t *r
                   int32_t *rec_exps, uint32_t *rec_limbs);
 
 /*
+ * Queue nsteps steps on the context's stream and return at once (no records).
+ * Finish with mpt_wait, which reports device-side errors; until then the
+ * context accepts no other launch, and the calls that read or set the state
+ * wait first.  On an error the state is put back to where the launch began.
+ */
+int mpt_launch(mpt_ctx *ctx, int64_t nsteps);
+int mpt_wait(mpt_ctx *ctx);
+
+/*
  * The Taylor coefficients of the most recent step: 3*(N+1) numbers,
  * component-major (alpha_0..alpha_N, beta_0..beta_N, gamma_0..gamma_N;
  * index 0 is the state the step started from), host memory.
@@ -135,19 +144,51 @@ int mpt_set_launch(mpt_ctx *ctx, int ctas);
 int mpt_get_launch(const mpt_ctx *ctx, int *ctas);
 
 /*
+ * Kernel organisation (results are identical): 1 = lock-step (every CTA
+ * takes a share of each index's products, grid barrier, every CTA closes the
+ * brackets); 2 = pipelined (a CTA cluster closes the brackets and runs
+ * Horner while the other CTAs compute the next index's inner Cauchy sums);
+ * 0 = the library's choice (pipelined for large L x N).  mpt_get_kernel
+ * reports the organisation the next launch uses.
+ */
+int mpt_set_kernel(mpt_ctx *ctx, int kind);
+int mpt_get_kernel(const mpt_ctx *ctx, int *kind);
+
+/*
+ * Bound of every device-side wait (grid barrier, hand-over flags), in polls;
+ * 0 restores the default (tens of millions, seconds).  When a wait runs out
+ * the launch stops, the call returns MPT_ETIMEDOUT and the state is put back
+ * to where the launch began; the context stays usable.  A small bound is the
+ * way to exercise that path on purpose.  (Not part of the paper.)
+ */
+int mpt_set_wait_limit(mpt_ctx *ctx, int64_t polls);
+
+/*
+ * Per-phase cycle profile (a device-side stats block; not part of the
+ * paper).  With profiling on, every launch accumulates SM clock cycles per
+ * phase for the first and the last CTA; mpt_get_profile copies up to n
+ * counters (layout: [cta][slot], 16 slots per CTA: 0 window placement,
+ * 1 operand staging, 2 limb products, 3 accumulator flush, 4 grid barrier,
+ * 5 close (normalise + divide), 6 Horner, 7 Horner products, 8 Horner
+ * close, 9 whole launch) of the last launch.  Off by default.
+ */
+int mpt_set_profiling(mpt_ctx *ctx, int on);
+int mpt_get_profile(mpt_ctx *ctx, int64_t *cycles, int n);
+
+/*
  * INT32 multiply-add throughput probe (sets the roofline of the limb
  * products).  Runs instruction-form `variant` (0 mad.lo.u32, 1 mad.hi.u32,
  * 2 mad.wide.u32, 3 limb product with mad.lo.cc/madc.hi.cc/addc, 4 two
  * mad.wide.u32 on 16-bit halves, 5 mad.wide.u32 plus a wide carry word,
  * 6 mad.lo.cc+addc and mad.hi.cc+addc, 7 mad.lo+mad.hi, 8 mul.wide plus
- * add.cc chains) on one 1024-thread CTA per SM, 8 independent chains per
- * thread, `iters` rounds.  Outputs: mean loop cycles of a CTA, kernel time in
- * ms, number of distinct SMs used, grid size.  Allocates its own scratch
- * buffers.  Returns 0 or a cudaError_t value.  (Not part of the paper: a
- * measurement aid.)
+ * add.cc chains) on one CTA of `threads` threads (multiple of 32, <= 1024)
+ * per SM, 8 independent chains per thread, `iters` rounds.  Outputs: mean
+ * loop cycles of a CTA, kernel time in ms, number of distinct SMs used, grid
+ * size.  Allocates its own scratch buffers.  Returns 0 or a cudaError_t
+ * value.  (Not part of the paper: a measurement aid.)
  */
-int mpt_int_peak_run(int variant, int iters, double *mean_cycles, double *ms, int *distinct_sms,
-                     int *grid_out);
+int mpt_int_peak_run(int variant, int threads, int iters, double *mean_cycles, double *ms,
+                     int *distinct_sms, int *grid_out);
 
 /* Message for an error code; message of the calling thread's last error. */
 const char *mpt_strerror(int code);

@@ -82,7 +82,7 @@ __device__ __forceinline__ void mac_lohi(uint32_t a, uint32_t b, uint32_t &l0, u
 }
 
 template <int V>
-__global__ void __launch_bounds__(1024, 1) peak_kernel(int iters, uint32_t seed, uint64_t *sink,
+__global__ void __launch_bounds__(1024) peak_kernel(int iters, uint32_t seed, uint64_t *sink,
                                                        long long *cycles, int *smid)
 {
     uint32_t a = seed ^ (threadIdx.x * 2654435761u);
@@ -137,24 +137,28 @@ __global__ void __launch_bounds__(1024, 1) peak_kernel(int iters, uint32_t seed,
     }
 }
 
-constexpr int THREADS = 1024;
+constexpr int MAX_THREADS = 1024;
+int g_threads = MAX_THREADS;
 
 template <int V>
 void launch(int grid, int iters, uint64_t *sink, long long *cycles, int *smid, cudaStream_t st)
 {
-    peak_kernel<V><<<grid, THREADS, 0, st>>>(iters, 12345u, sink, cycles, smid);
+    peak_kernel<V><<<grid, g_threads, 0, st>>>(iters, 12345u, sink, cycles, smid);
 }
 
 }  // namespace
 
-// Runs variant `variant` on one CTA of 1024 threads per SM (grid = SM count)
-// for `iters` rounds of 8 chains per thread.  Writes the mean loop cycles of a
-// CTA to *mean_cycles, the kernel's wall time to *ms, and the number of
-// distinct SMs the CTAs ran on to *distinct_sms.  Allocates and frees its own
-// small buffers.  Returns 0, or the CUDA error code.
-extern "C" int mpt_int_peak_run(int variant, int iters, double *mean_cycles, double *ms,
-                                int *distinct_sms, int *grid_out)
+// Runs variant `variant` on one CTA of `threads` threads (a multiple of 32,
+// at most 1024) per SM (grid = SM count) for `iters` rounds of 8 chains per
+// thread.  Writes the mean loop cycles of a CTA to *mean_cycles, the kernel's
+// wall time to *ms, and the number of distinct SMs the CTAs ran on to
+// *distinct_sms.  Allocates and frees its own small buffers.  Returns 0, or
+// the CUDA error code.
+extern "C" int mpt_int_peak_run(int variant, int threads, int iters, double *mean_cycles,
+                                double *ms, int *distinct_sms, int *grid_out)
 {
+    if (threads < 32 || threads > MAX_THREADS || threads % 32) return (int)cudaErrorInvalidValue;
+    g_threads = threads;
     int dev = 0, grid = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&grid, cudaDevAttrMultiProcessorCount, dev);
@@ -163,7 +167,7 @@ extern "C" int mpt_int_peak_run(int variant, int iters, double *mean_cycles, dou
     uint64_t *sink = nullptr;
     long long *cycles = nullptr;
     int *smid = nullptr;
-    e = cudaMalloc(&sink, (size_t)grid * THREADS * sizeof(uint64_t));
+    e = cudaMalloc(&sink, (size_t)grid * MAX_THREADS * sizeof(uint64_t));
     if (e == cudaSuccess) e = cudaMalloc(&cycles, (size_t)grid * sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc(&smid, (size_t)grid * sizeof(int));
     cudaEvent_t a = nullptr, b = nullptr;

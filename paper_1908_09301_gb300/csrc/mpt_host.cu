@@ -72,12 +72,47 @@ struct mpt_ctx {
     uint32_t *recL = nullptr;
     long long rec_cap = 0;
     bool have_coefficients = false;
+    bool pending = false;  // steps queued by mpt_launch, not yet waited for
+    long long *prof = nullptr;  // per-phase cycle counters when profiling is on
+    long long spin_limit = mpt::DEFAULT_SPIN_LIMIT;
+    // pipelined kernel (closer cluster + workers)
+    int kind_req = 0;           // 0 auto, 1 lockstep, 2 pipelined
+    int pipe_C = 8;             // CTAs in the closer cluster (fixed by the kernel)
+    int pipe_max_grid = 0;      // co-resident CTAs in whole clusters
+    int pipe_tb = 0;
+    size_t pipe_smem = 0;
+    unsigned *pub = nullptr, *done = nullptr;
+    long long *gin = nullptr;
     // parameters in the interchange layout (host)
     int32_t par_s[4] = {0, 0, 0, 0}, par_e[4] = {0, 0, 0, 0};
     std::vector<uint32_t> par_l;
 };
 
 namespace {
+
+// which kernel runs a launch: the pipelined one for large L x N, when the
+// device fits a closer cluster and at least one worker cluster
+int kind_for(const mpt_ctx *c)
+{
+    if (c->kind_req == 1) return 1;
+    bool pipe_ok = c->pipe_max_grid >= 2 * c->pipe_C && c->N >= 3;
+    if (c->kind_req == 2) return pipe_ok ? 2 : 1;
+    double work = (double)c->N * c->Lp * c->Lp;
+    return (pipe_ok && work >= 5e5) ? 2 : 1;
+}
+
+int pipe_grid_for(const mpt_ctx *c)
+{
+    int g = c->pipe_max_grid;
+    int lim = (c->sms / c->pipe_C) * c->pipe_C;
+    if (g > lim) g = lim;
+    if (c->ctas_req > 0) {
+        int r = c->ctas_req / c->pipe_C * c->pipe_C;
+        if (r < 2 * c->pipe_C) r = 2 * c->pipe_C;
+        if (r < g) g = r;
+    }
+    return g;
+}
 
 int grid_for(const mpt_ctx *c)
 {
@@ -92,6 +127,7 @@ int grid_for(const mpt_ctx *c)
     if (g > c->max_grid) g = c->max_grid;
     return g;
 }
+
 
 // interchange (sign, exp, L limbs) -> device layout (flags, exp, Lp limbs)
 int to_device_layout(const mpt_ctx *c, const int32_t *s, const int32_t *e, const uint32_t *l, int n,
@@ -131,8 +167,14 @@ void from_device_layout(const mpt_ctx *c, const std::vector<uint32_t> &dl,
     }
 }
 
+int wait_steps(mpt_ctx *c);
+
 int upload_state(mpt_ctx *c, const int32_t *s, const int32_t *e, const uint32_t *l)
 {
+    if (c->pending) {
+        int rc = wait_steps(c);
+        if (rc) return rc;
+    }
     std::vector<uint32_t> dl;
     std::vector<int32_t> de, df;
     int rc = to_device_layout(c, s, e, l, 3, dl, de, df);
@@ -153,7 +195,7 @@ void free_all(mpt_ctx *c)
 {
     void *ptrs[] = {c->coefL, c->coefE, c->coefF, c->parL, c->parE, c->parF, c->stL, c->stBackL,
                     c->stE, c->stF, c->stBackEF, c->gwin, c->bar, c->status, c->recS, c->recE,
-                    c->recL};
+                    c->recL, c->prof, c->pub, c->done, c->gin};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -262,6 +304,18 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
         delete c;
         return fail(MPT_ECUDA, "kernel does not fit on the device");
     }
+    {
+        int ptb = 32;
+        while (ptb > 8 && mpt::pipe_smem_bytes(c->Lp, c->N, c->Wcap, ptb) > (size_t)smem_optin) ptb /= 2;
+        c->pipe_tb = ptb;
+        c->pipe_smem = mpt::pipe_smem_bytes(c->Lp, c->N, c->Wcap, ptb);
+        c->pipe_max_grid = 0;
+        if (c->pipe_smem <= (size_t)smem_optin) {
+            int ncl = mpt::pipe_max_clusters(c->pipe_C, c->pipe_smem);
+            (void)cudaGetLastError();
+            c->pipe_max_grid = ncl * c->pipe_C;
+        }
+    }
     const size_t N1 = (size_t)c->N + 1;
     ce = dalloc(&c->coefL, 3 * N1 * c->Lp);
     if (ce == cudaSuccess) ce = dalloc(&c->coefE, 3 * N1);
@@ -277,6 +331,9 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
     if (ce == cudaSuccess) ce = dalloc(&c->gwin, (size_t)9 * c->Wcap);
     if (ce == cudaSuccess) ce = dalloc(&c->bar, 2);
     if (ce == cudaSuccess) ce = dalloc(&c->status, 1);
+    if (ce == cudaSuccess) ce = dalloc(&c->pub, 1);
+    if (ce == cudaSuccess) ce = dalloc(&c->done, mpt::PIPE_SETS);
+    if (ce == cudaSuccess) ce = dalloc(&c->gin, (size_t)mpt::PIPE_SETS * 2 * c->Wcap);
     if (ce != cudaSuccess) {
         free_all(c);
         delete c;
@@ -295,6 +352,8 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
     if (ce == cudaSuccess) ce = cudaMemcpy(c->parE, de.data(), sizeof(int32_t) * 4, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemcpy(c->parF, df.data(), sizeof(int32_t) * 4, cudaMemcpyHostToDevice);
     if (ce == cudaSuccess) ce = cudaMemset(c->gwin, 0, sizeof(long long) * 9 * c->Wcap);
+    if (ce == cudaSuccess) ce = cudaMemset(c->status, 0, sizeof(int));
+    if (ce == cudaSuccess) ce = cudaMemset(c->bar, 0, sizeof(unsigned) * 2);
     if (ce == cudaSuccess) ce = cudaMemset(c->stL, 0, sizeof(uint32_t) * 3 * c->Lp);
     if (ce == cudaSuccess) ce = cudaMemset(c->stE, 0, sizeof(int32_t) * 3);
     if (ce == cudaSuccess) ce = cudaMemset(c->stF, 0, sizeof(int32_t) * 3);
@@ -353,6 +412,10 @@ int mpt_get_state(mpt_ctx *c, int32_t *s, int32_t *e, uint32_t *l)
 {
     if (!c || !s || !e || !l) return fail(MPT_EINVAL, "null argument");
     DeviceGuard g(c->dev);
+    if (c->pending) {
+        int rc = wait_steps(c);
+        if (rc) return rc;
+    }
     std::vector<uint32_t> dl((size_t)3 * c->Lp);
     std::vector<int32_t> de(3), df(3);
     cudaError_t ce = cudaMemcpyAsync(dl.data(), c->stL, sizeof(uint32_t) * 3 * c->Lp,
@@ -381,9 +444,8 @@ int mpt_get_params(mpt_ctx *c, int32_t *s, int32_t *e, uint32_t *l)
 int mpt_set_launch(mpt_ctx *c, int ctas)
 {
     if (!c) return fail(MPT_EINVAL, "null context");
-    if (ctas < 0 || ctas > c->sms || ctas > c->max_grid)
-        return fail(MPT_EINVAL, "ctas = %d outside 0..%d", ctas,
-                    c->sms < c->max_grid ? c->sms : c->max_grid);
+    if (ctas < 0 || ctas > c->sms)
+        return fail(MPT_EINVAL, "ctas = %d outside 0..%d", ctas, c->sms);
     c->ctas_req = ctas;
     return MPT_OK;
 }
@@ -391,22 +453,36 @@ int mpt_set_launch(mpt_ctx *c, int ctas)
 int mpt_get_launch(const mpt_ctx *c, int *ctas)
 {
     if (!c || !ctas) return fail(MPT_EINVAL, "null argument");
-    *ctas = grid_for(c);
+    *ctas = kind_for(c) == 2 ? pipe_grid_for(c) : grid_for(c);
     return MPT_OK;
 }
 
-int mpt_integrate(mpt_ctx *c, int64_t nsteps, int64_t record_every, int32_t *rs, int32_t *re,
-                  uint32_t *rl)
+int mpt_set_kernel(mpt_ctx *c, int kind)
 {
     if (!c) return fail(MPT_EINVAL, "null context");
-    if (nsteps < 0) return fail(MPT_EINVAL, "nsteps < 0");
-    long long nrec = record_every > 0 ? nsteps / record_every : 0;
-    if (nrec > 0 && (!rs || !re || !rl)) return fail(MPT_EINVAL, "record pointers are null");
-    if (nsteps == 0) return MPT_OK;
-    DeviceGuard g(c->dev);
-    if (!g.ok) return fail(MPT_ECUDA, "cannot select the context's device");
+    if (kind < 0 || kind > 2) return fail(MPT_EINVAL, "kernel kind %d outside 0..2", kind);
+    c->kind_req = kind;
+    return MPT_OK;
+}
+
+int mpt_get_kernel(const mpt_ctx *c, int *kind)
+{
+    if (!c || !kind) return fail(MPT_EINVAL, "null argument");
+    *kind = kind_for(c);
+    return MPT_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// queue nsteps steps on the context's stream; records go to the device buffers
+int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_every)
+{
     cudaError_t ce = cudaSuccess;
     if (nrec > c->rec_cap) {
+        ce = cudaStreamSynchronize(c->st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "stream synchronisation");
         if (c->recS) cudaFree(c->recS);
         if (c->recE) cudaFree(c->recE);
         if (c->recL) cudaFree(c->recL);
@@ -428,7 +504,6 @@ int mpt_integrate(mpt_ctx *c, int64_t nsteps, int64_t record_every, int32_t *rs,
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(c->stBackEF + 3, c->stF, sizeof(int32_t) * 3, cudaMemcpyDeviceToDevice, c->st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->bar, 0, sizeof(unsigned) * 2, c->st);
-    if (ce == cudaSuccess) ce = cudaMemsetAsync(c->status, 0, sizeof(int), c->st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->gwin, 0, sizeof(long long) * 9 * c->Wcap, c->st);
     if (ce != cudaSuccess) return cuda_fail(ce, "launch preparation");
     mpt::KArgs a;
@@ -455,18 +530,47 @@ int mpt_integrate(mpt_ctx *c, int64_t nsteps, int64_t record_every, int32_t *rs,
     a.recL = c->recL;
     a.nsteps = nsteps;
     a.record_every = nrec > 0 ? record_every : 0;
-    const int grid = grid_for(c);
-    ce = mpt::launch_integrate(a, grid, c->smem, c->st);
+    a.prof = c->prof;
+    a.spin_limit = c->spin_limit;
+    if (c->prof) {
+        ce = cudaMemsetAsync(c->prof, 0, sizeof(long long) * 2 * mpt::PROF_SLOTS, c->st);
+        if (ce != cudaSuccess) return cuda_fail(ce, "profile reset");
+    }
+    if (kind_for(c) == 2) {
+        mpt::PArgs pa;
+        pa.pub = c->pub;
+        pa.done = c->done;
+        pa.gin = c->gin;
+        pa.C = c->pipe_C;
+        a.tb = c->pipe_tb;
+        ce = cudaMemsetAsync(c->pub, 0, sizeof(unsigned), c->st);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(c->done, 0, sizeof(unsigned) * mpt::PIPE_SETS, c->st);
+        if (ce == cudaSuccess)
+            ce = cudaMemsetAsync(c->gin, 0, sizeof(long long) * mpt::PIPE_SETS * 2 * c->Wcap, c->st);
+        if (ce == cudaSuccess) ce = mpt::launch_pipe(a, pa, pipe_grid_for(c), c->pipe_smem, c->st);
+    } else {
+        ce = mpt::launch_integrate(a, grid_for(c), c->smem, c->st);
+    }
     if (ce != cudaSuccess) return cuda_fail(ce, "kernel launch");
+    c->pending = true;
+    return MPT_OK;
+}
+
+// wait for queued steps; on a device-side error put the starting state back
+int wait_steps(mpt_ctx *c)
+{
     int status = 0;
-    ce = cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+    cudaError_t ce = cudaMemcpyAsync(&status, c->status, sizeof(int), cudaMemcpyDeviceToHost, c->st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
     if (ce != cudaSuccess) return cuda_fail(ce, "kernel execution");
+    if (!c->pending) return MPT_OK;
+    c->pending = false;
     c->have_coefficients = true;
     if (status != 0) {
         cudaMemcpyAsync(c->stL, c->stBackL, sizeof(uint32_t) * 3 * c->Lp, cudaMemcpyDeviceToDevice, c->st);
         cudaMemcpyAsync(c->stE, c->stBackEF, sizeof(int32_t) * 3, cudaMemcpyDeviceToDevice, c->st);
         cudaMemcpyAsync(c->stF, c->stBackEF + 3, sizeof(int32_t) * 3, cudaMemcpyDeviceToDevice, c->st);
+        cudaMemsetAsync(c->status, 0, sizeof(int), c->st);
         cudaStreamSynchronize(c->st);
         c->have_coefficients = false;
         if (status == mpt::DEV_ERANGE)
@@ -475,8 +579,33 @@ int mpt_integrate(mpt_ctx *c, int64_t nsteps, int64_t record_every, int32_t *rs,
         if (status == mpt::DEV_TIMEOUT) return fail(MPT_ETIMEDOUT, "a grid barrier wait expired");
         return fail(MPT_ECUDA, "device invariant failed (status %d)", status);
     }
+    return MPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpt_integrate(mpt_ctx *c, int64_t nsteps, int64_t record_every, int32_t *rs, int32_t *re,
+                  uint32_t *rl)
+{
+    if (!c) return fail(MPT_EINVAL, "null context");
+    if (nsteps < 0) return fail(MPT_EINVAL, "nsteps < 0");
+    long long nrec = record_every > 0 ? nsteps / record_every : 0;
+    if (nrec > 0 && (!rs || !re || !rl)) return fail(MPT_EINVAL, "record pointers are null");
+    if (nsteps == 0) return MPT_OK;
+    DeviceGuard g(c->dev);
+    if (!g.ok) return fail(MPT_ECUDA, "cannot select the context's device");
+    if (c->pending) {
+        int rc = wait_steps(c);
+        if (rc) return rc;
+    }
+    int rc = launch_steps(c, nsteps, nrec, record_every);
+    if (rc) return rc;
+    rc = wait_steps(c);
+    if (rc) return rc;
     if (nrec > 0) {
-        ce = cudaMemcpyAsync(rs, c->recS, sizeof(int32_t) * nrec * 3, cudaMemcpyDefault, c->st);
+        cudaError_t ce = cudaMemcpyAsync(rs, c->recS, sizeof(int32_t) * nrec * 3, cudaMemcpyDefault, c->st);
         if (ce == cudaSuccess)
             ce = cudaMemcpyAsync(re, c->recE, sizeof(int32_t) * nrec * 3, cudaMemcpyDefault, c->st);
         if (ce == cudaSuccess)
@@ -488,13 +617,72 @@ int mpt_integrate(mpt_ctx *c, int64_t nsteps, int64_t record_every, int32_t *rs,
     return MPT_OK;
 }
 
+int mpt_set_wait_limit(mpt_ctx *c, int64_t polls)
+{
+    if (!c) return fail(MPT_EINVAL, "null context");
+    if (polls < 0) return fail(MPT_EINVAL, "polls < 0");
+    c->spin_limit = polls == 0 ? mpt::DEFAULT_SPIN_LIMIT : polls;
+    return MPT_OK;
+}
+
+int mpt_set_profiling(mpt_ctx *c, int on)
+{
+    if (!c) return fail(MPT_EINVAL, "null context");
+    DeviceGuard g(c->dev);
+    if (on && !c->prof) {
+        cudaError_t ce = dalloc(&c->prof, 2 * mpt::PROF_SLOTS);
+        if (ce == cudaSuccess) ce = cudaMemset(c->prof, 0, sizeof(long long) * 2 * mpt::PROF_SLOTS);
+        if (ce != cudaSuccess) return cuda_fail(ce, "profile buffer");
+    } else if (!on && c->prof) {
+        cudaStreamSynchronize(c->st);
+        cudaFree(c->prof);
+        c->prof = nullptr;
+    }
+    return MPT_OK;
+}
+
+int mpt_get_profile(mpt_ctx *c, int64_t *cycles, int n)
+{
+    if (!c || !cycles) return fail(MPT_EINVAL, "null argument");
+    if (!c->prof) return fail(MPT_EINVAL, "profiling is off");
+    DeviceGuard g(c->dev);
+    long long h[2 * mpt::PROF_SLOTS];
+    cudaError_t ce = cudaMemcpyAsync(h, c->prof, sizeof h, cudaMemcpyDeviceToHost, c->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "profile download");
+    for (int i = 0; i < n && i < 2 * mpt::PROF_SLOTS; i++) cycles[i] = h[i];
+    return MPT_OK;
+}
+
+int mpt_launch(mpt_ctx *c, int64_t nsteps)
+{
+    if (!c) return fail(MPT_EINVAL, "null context");
+    if (nsteps < 0) return fail(MPT_EINVAL, "nsteps < 0");
+    if (nsteps == 0) return MPT_OK;
+    if (c->pending) return fail(MPT_EINVAL, "steps already queued: call mpt_wait first");
+    DeviceGuard g(c->dev);
+    if (!g.ok) return fail(MPT_ECUDA, "cannot select the context's device");
+    return launch_steps(c, nsteps, 0, 0);
+}
+
+int mpt_wait(mpt_ctx *c)
+{
+    if (!c) return fail(MPT_EINVAL, "null context");
+    DeviceGuard g(c->dev);
+    return wait_steps(c);
+}
+
 int mpt_step(mpt_ctx *c) { return mpt_integrate(c, 1, 0, nullptr, nullptr, nullptr); }
 
 int mpt_get_coefficients(mpt_ctx *c, int32_t *s, int32_t *e, uint32_t *l)
 {
     if (!c || !s || !e || !l) return fail(MPT_EINVAL, "null argument");
-    if (!c->have_coefficients) return fail(MPT_EINVAL, "no step has completed yet");
     DeviceGuard g(c->dev);
+    if (c->pending) {
+        int rc = wait_steps(c);
+        if (rc) return rc;
+    }
+    if (!c->have_coefficients) return fail(MPT_EINVAL, "no step has completed yet");
     const size_t n = (size_t)3 * (c->N + 1);
     std::vector<uint32_t> dl(n * c->Lp);
     std::vector<int32_t> de(n), df(n);

@@ -40,7 +40,46 @@ struct KArgs {
     uint32_t *recL;         // [nrec][3][L]
     long long nsteps;
     long long record_every;
+    long long *prof;        // [2][PROF_SLOTS] per-phase SM cycles of CTAs 0 and G-1, or null
+    long long spin_limit;   // polls before a device-side wait gives up
 };
+
+constexpr long long DEFAULT_SPIN_LIMIT = 20LL * 1000 * 1000;
+
+// phases of the per-phase cycle profile
+enum ProfSlot {
+    PR_PLACE = 0,   // window placement for an index
+    PR_STAGE,       // operand staging
+    PR_MAC,         // limb products
+    PR_FLUSH,       // shared -> global accumulator flush
+    PR_BARRIER,     // grid barrier wait
+    PR_CLOSE,       // normalise + divide
+    PR_HORNER,      // Horner chains (all of it)
+    PR_HMAC,        // Horner products
+    PR_HCLOSE,      // Horner normalise + truncate
+    PR_TOTAL,       // whole launch
+    PR_X1,          // finer marks of the pipelined closer
+    PR_X2,
+    PR_X3,
+    PR_X4,
+    PR_X5,
+    PR_X6,
+    PROF_SLOTS = 16
+};
+
+// pipelined kernel: closer cluster + workers
+constexpr int PIPE_SETS = 8;  // rotating global accumulator sets / completion counters
+
+struct PArgs {
+    unsigned *pub;   // [1] published coefficients of the launch (monotone)
+    unsigned *done;  // [PIPE_SETS] workers finished with an index (monotone)
+    long long *gin;  // [PIPE_SETS][2][Wcap] inner Cauchy sums (targets beta, gamma)
+    int C;           // CTAs of the closer cluster
+};
+
+size_t pipe_smem_bytes(int Lp, int N, int Wcap, int tb);
+int pipe_max_clusters(int C, size_t smem);
+cudaError_t launch_pipe(const KArgs &a, const PArgs &pa, int grid, size_t smem, cudaStream_t st);
 
 // dynamic shared memory bytes for a configuration
 size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb);

@@ -37,7 +37,6 @@ namespace mpt {
 namespace {
 
 constexpr unsigned FULL = 0xffffffffu;
-constexpr long long SPIN_LIMIT = 40LL * 1000 * 1000;  // bounded waits (about a few seconds)
 
 __device__ __forceinline__ int phys(int x) { return x + (x >> 3); }
 
@@ -69,6 +68,28 @@ __device__ __forceinline__ void set_status(int *status, int code)
 {
     atomicCAS(status, 0, code);
 }
+
+// per-phase cycle counters (thread 0 of the first and the last CTA)
+struct Prof {
+    long long *p;
+    long long t;
+    __device__ Prof(const KArgs &a)
+    {
+        p = nullptr;
+        t = 0;
+        if (a.prof && threadIdx.x == 0 && (blockIdx.x == 0 || blockIdx.x == gridDim.x - 1))
+            p = a.prof + (blockIdx.x == 0 ? 0 : PROF_SLOTS);
+        if (p) t = clock64();
+    }
+    __device__ __forceinline__ void mark(int slot)
+    {
+        if (p) {
+            long long n = clock64();
+            p[slot] += n - t;
+            t = n;
+        }
+    }
+};
 
 // ------------------------------------------------------------------ smem
 
@@ -163,6 +184,7 @@ __device__ __forceinline__ long long warp_max_ll(long long v)
 // wait is bounded: on expiry the status word is set and every CTA unwinds.
 __device__ bool grid_barrier(const Smem &S, const KArgs &a)
 {
+    Prof pr(a);
     __syncthreads();
     if (gridDim.x > 1) {
         if (threadIdx.x == 0) {
@@ -176,7 +198,7 @@ __device__ bool grid_barrier(const Smem &S, const KArgs &a)
             } else {
                 long long it = 0;
                 while (ld_acquire(&a.bar[1]) == gen) {
-                    if (++it > SPIN_LIMIT) {
+                    if (++it > a.spin_limit) {
                         set_status(a.status, DEV_TIMEOUT);
                         break;
                     }
@@ -186,7 +208,9 @@ __device__ bool grid_barrier(const Smem &S, const KArgs &a)
             }
         }
     }
-    return cta_ok(S, a);
+    bool ok = cta_ok(S, a);
+    pr.mark(PR_BARRIER);
+    return ok;
 }
 
 // ------------------------------------------------------------------ terms of Eq. (3)
@@ -624,8 +648,10 @@ __device__ void run_unit(const Smem &S, const KArgs &a, int slot, int q)
 __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
 {
     const int G = gridDim.x, g = blockIdx.x;
+    Prof pr(a);
     place_windows(S, a, m);
     if (!cta_ok(S, a)) return;
+    pr.mark(PR_PLACE);
     if (G > 1) {
         // clear the accumulator set that the next index will use (last read
         // by the close two indices back, which every CTA finished before the
@@ -642,6 +668,7 @@ __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
             const int nt = min(a.tb, tB - tb0 + 1);
             stage_terms(S, a, m, tb0, nt);
             __syncthreads();
+            pr.mark(PR_STAGE);
             const long long ua = max(u0, (long long)tb0 * a.P);
             const long long ub = min(u1, (long long)(tb0 + nt) * a.P);
             for (long long u = ua + threadIdx.x; u < ub; u += NT) {
@@ -649,6 +676,7 @@ __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
                 run_unit(S, a, t - tb0, (int)(u - (long long)t * a.P));
             }
             __syncthreads();
+            pr.mark(PR_MAC);
         }
     }
     if (G > 1) {
@@ -663,6 +691,8 @@ __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
                 }
             }
         }
+        __syncthreads();
+        pr.mark(PR_FLUSH);
     }
 }
 
@@ -672,6 +702,7 @@ __device__ void close_phase(const Smem &S, const KArgs &a, int m, int set)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x;
     const int N1 = a.N + 1;
+    Prof pr(a);
     if (warp < 3) {
         const int tg = warp;  // 0 alpha, 1 beta, 2 gamma
         const int wd = S.misc[MS_WIDTH + tg];
@@ -712,6 +743,7 @@ __device__ void close_phase(const Smem &S, const KArgs &a, int m, int set)
         }
     }
     __syncthreads();
+    pr.mark(PR_CLOSE);
 }
 
 // Horner for the components this CTA owns: h_N = c_N,
@@ -752,6 +784,7 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
     }
     const int tauE = __ldg(&a.parE[P_TAU]), tauF = __ldg(&a.parF[P_TAU]);
     __syncthreads();
+    Prof pr(a);
     for (int i = N - 1; i >= 0; i--) {
         // prefetch c_{i-1} into registers while the products of step i run
         uint32_t pre[3][4];
@@ -804,6 +837,7 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
             run_unit(S, a, slot, u - slot * a.P);
         }
         __syncthreads();
+        pr.mark(PR_HMAC);
         // close: h_i for each component (division by one = truncation)
         if (warp < nc) {
             const int j = warp;
@@ -844,6 +878,7 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
                 }
         }
         __syncthreads();
+        pr.mark(PR_HCLOSE);
     }
     // the new state and, when due, a record
     const long long rec = (a.record_every > 0 && ((step + 1) % a.record_every) == 0)
@@ -871,6 +906,7 @@ __global__ void __launch_bounds__(NT, 1) taylor_kernel(KArgs a)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem S = carve(smem_raw, a);
     const int N1 = a.N + 1;
+    Prof tot(a);
     if (threadIdx.x < 4) {
         int nz = 0;
         for (int x = 0; x < a.Lp; x++) nz += __ldg(&a.parL[(size_t)threadIdx.x * a.Lp + x]) != 0u;
@@ -909,9 +945,16 @@ __global__ void __launch_bounds__(NT, 1) taylor_kernel(KArgs a)
         }
         if (!ok) break;
         if (!grid_barrier(S, a)) break;
-        horner_phase(S, a, (int)step);
+        {
+            Prof ph(a);
+            horner_phase(S, a, (int)step);
+            __syncthreads();
+            ph.mark(PR_HORNER);
+        }
         if (!grid_barrier(S, a)) break;
     }
+    __syncthreads();
+    tot.mark(PR_TOTAL);
 }
 
 }  // namespace

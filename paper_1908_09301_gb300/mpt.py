@@ -44,9 +44,17 @@ SIGNATURES = {
     "mpt_step": (ctypes.c_int, [vp]),
     "mpt_integrate": (ctypes.c_int, [vp, ctypes.c_int64, ctypes.c_int64, vp, vp, vp]),
     "mpt_get_coefficients": (ctypes.c_int, [vp, vp, vp, vp]),
+    "mpt_launch": (ctypes.c_int, [vp, ctypes.c_int64]),
+    "mpt_set_profiling": (ctypes.c_int, [vp, ctypes.c_int]),
+    "mpt_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_int64]),
+    "mpt_get_profile": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+    "mpt_wait": (ctypes.c_int, [vp]),
     "mpt_set_launch": (ctypes.c_int, [vp, ctypes.c_int]),
     "mpt_get_launch": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
-    "mpt_int_peak_run": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+    "mpt_set_kernel": (ctypes.c_int, [vp, ctypes.c_int]),
+    "mpt_get_kernel": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
+    "mpt_int_peak_run": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
     "mpt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -201,8 +209,45 @@ class Context:
                                    _ptr(out[1]), _ptr(out[2])))
         return out
 
+    def launch_async(self, nsteps: int = 1):
+        """Queue nsteps steps on the context's stream (``mpt_launch``)."""
+        _check(lib().mpt_launch(self._h, int(nsteps)))
+
+    def wait(self):
+        """Finish queued steps and report device-side errors (``mpt_wait``)."""
+        _check(lib().mpt_wait(self._h))
+
+    PROFILE_SLOTS = ["place", "stage", "mac", "flush", "barrier", "close", "horner", "horner_mac",
+                     "horner_close", "total", "x1", "x2", "x3", "x4", "x5", "x6"]
+
+    def set_wait_limit(self, polls: int = 0):
+        """Bound of device-side waits in polls (0 = default) (``mpt_set_wait_limit``)."""
+        _check(lib().mpt_set_wait_limit(self._h, int(polls)))
+
+    def set_profiling(self, on: bool = True):
+        _check(lib().mpt_set_profiling(self._h, int(bool(on))))
+
+    def profile(self):
+        """Per-phase SM cycles of the last launch: {cta: {phase: cycles}} for
+        the first and the last CTA."""
+        buf = np.zeros(32, np.int64)
+        _check(lib().mpt_get_profile(self._h, _ptr(buf), 32))
+        out = {}
+        for k, cta in enumerate(("first", "last")):
+            out[cta] = {n: int(buf[16 * k + j]) for j, n in enumerate(self.PROFILE_SLOTS)}
+        return out
+
     def set_launch(self, ctas: int):
         _check(lib().mpt_set_launch(self._h, int(ctas)))
+
+    def set_kernel(self, kind: int):
+        """0 = library choice, 1 = lock-step, 2 = pipelined (``mpt_set_kernel``)."""
+        _check(lib().mpt_set_kernel(self._h, int(kind)))
+
+    def kernel(self) -> int:
+        k = ctypes.c_int()
+        _check(lib().mpt_get_kernel(self._h, ctypes.byref(k)))
+        return k.value
 
     def launch(self) -> int:
         c = ctypes.c_int()
@@ -210,13 +255,13 @@ class Context:
         return c.value
 
 
-def int_peak(variant: int, iters: int = 20000):
+def int_peak(variant: int, iters: int = 20000, threads: int = 1024):
     """INT32 multiply-add probe: (results per SM per clock, ms, sms, grid)."""
     cyc, ms = ctypes.c_double(), ctypes.c_double()
     ds, g = ctypes.c_int(), ctypes.c_int()
-    rc = lib().mpt_int_peak_run(int(variant), int(iters), ctypes.byref(cyc), ctypes.byref(ms),
-                                ctypes.byref(ds), ctypes.byref(g))
+    rc = lib().mpt_int_peak_run(int(variant), int(threads), int(iters), ctypes.byref(cyc),
+                                ctypes.byref(ms), ctypes.byref(ds), ctypes.byref(g))
     if rc != 0:
         raise MPTError(MPT_ECUDA, f"int peak probe failed with CUDA error {rc}")
-    per_clk = iters * 8 * 1024 / cyc.value
+    per_clk = iters * 8 * threads / cyc.value
     return per_clk, ms.value, ds.value, g.value

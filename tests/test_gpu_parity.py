@@ -21,12 +21,17 @@ def mpt():
     return M
 
 
-def gpu_ctx(mpt, L, N, par=(O.SIGMA, O.R, O.B, O.TAU), x0=O.X0, ctas=0):
+def gpu_ctx(mpt, L, N, par=(O.SIGMA, O.R, O.B, O.TAU), x0=O.X0, ctas=0, kind=0):
     c = mpt.Context(N=N, L=L, sigma=par[0], R=par[1], b=par[2], tau=par[3])
     c.set_state(*x0)
     if ctas:
         c.set_launch(ctas)
+    if kind:
+        c.set_kernel(kind)
     return c
+
+
+KINDS = [1, 2]  # lock-step, pipelined
 
 
 def oracle_run(L, N, par=(O.SIGMA, O.R, O.B, O.TAU), x0=O.X0, nsteps=1, record_every=0):
@@ -61,11 +66,12 @@ def test_parameters_match_oracle(mpt):
     c.close()
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("L,N", [(1, 5), (2, 7), (3, 20), (11, 60), (13, 25), (21, 40), (53, 30),
                                  (8, 9), (9, 64)])
-def test_one_step_coefficients(mpt, L, N):
+def test_one_step_coefficients(mpt, L, N, kind):
     """Eq. (3) coefficients alpha_0..alpha_N etc. and the Horner state, bit for bit."""
-    c = gpu_ctx(mpt, L, N)
+    c = gpu_ctx(mpt, L, N, kind=kind)
     c.step()
     want = oracle_coefficients(L, N)
     got = c.coefficients()
@@ -75,11 +81,12 @@ def test_one_step_coefficients(mpt, L, N):
     c.close()
 
 
-@pytest.mark.parametrize("ctas", [1, 2, 3, 5, 17])
-def test_launch_shape_invariance(mpt, ctas):
+@pytest.mark.parametrize("kind,ctas", [(1, 1), (1, 2), (1, 3), (1, 5), (1, 17), (2, 16), (2, 24),
+                                       (2, 64), (2, 0)])
+def test_launch_shape_invariance(mpt, kind, ctas):
     """The exact sums make the result independent of how the GPU splits them."""
     L, N = 21, 90
-    c = gpu_ctx(mpt, L, N, ctas=ctas)
+    c = gpu_ctx(mpt, L, N, ctas=ctas, kind=kind)
     c.integrate(3)
     fin, _ = oracle_run(L, N, nsteps=3)
     assert same(c.get_state(), fin)
@@ -89,10 +96,11 @@ def test_launch_shape_invariance(mpt, ctas):
     c.close()
 
 
-def test_k100_n60_full_run(mpt):
+@pytest.mark.parametrize("kind", KINDS)
+def test_k100_n60_full_run(mpt, kind):
     """100 digits, N = 60, 1000 steps of tau = 0.01 (t in [0, 10]), every 100th state."""
     L, N, steps, every = 11, 60, 1000, 100
-    c = gpu_ctx(mpt, L, N)
+    c = gpu_ctx(mpt, L, N, kind=kind)
     rec = c.integrate(steps, every)
     _, orec = oracle_run(L, N, nsteps=steps, record_every=every)
     assert same(rec, orec), first_mismatch(rec, orec)
@@ -113,9 +121,10 @@ EDGE = [
 ]
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("name,L,N,par,x0", EDGE, ids=[e[0] for e in EDGE])
-def test_edge_cases(mpt, name, L, N, par, x0):
-    c = gpu_ctx(mpt, L, N, par, x0)
+def test_edge_cases(mpt, name, L, N, par, x0, kind):
+    c = gpu_ctx(mpt, L, N, par, x0, kind=kind)
     rec = c.integrate(6, 1)
     _, orec = oracle_run(L, N, par, x0, nsteps=6, record_every=1)
     assert same(rec, orec), first_mismatch(rec, orec)
@@ -135,10 +144,11 @@ def test_symmetry_bit_exact(mpt):
     assert sa[2] == sb[2] and sa[0] == 1 - sb[0] and sa[1] == 1 - sb[1]
 
 
-def test_spread_beyond_accumulator_is_erange(mpt):
+@pytest.mark.parametrize("kind", KINDS)
+def test_spread_beyond_accumulator_is_erange(mpt, kind):
     """Terms 500+ limbs apart cannot share one exact window: MPT_ERANGE, and the
     state is left as it was."""
-    c = gpu_ctx(mpt, 2, 5, x0=("1e-5000", "17.48", "35.64"))
+    c = gpu_ctx(mpt, 2, 5, x0=("1e-5000", "17.48", "35.64"), kind=kind)
     before = c.get_state()
     with pytest.raises(mpt.MPTError) as ei:
         c.step()
@@ -163,10 +173,11 @@ def test_state_roundtrip_and_raw(mpt):
     c.close()
 
 
-def test_k500_n300_steps(mpt):
+@pytest.mark.parametrize("kind", KINDS)
+def test_k500_n300_steps(mpt, kind):
     """500 digits (53 limbs), N = 300: five steps, every state."""
     L, N = 53, 300
-    c = gpu_ctx(mpt, L, N)
+    c = gpu_ctx(mpt, L, N, kind=kind)
     rec = c.integrate(5, 1)
     _, orec = oracle_run(L, N, nsteps=5, record_every=1)
     assert same(rec, orec), first_mismatch(rec, orec)
@@ -186,5 +197,25 @@ def test_k2000_n1000_step(mpt):
     got = c.coefficients()
     assert same(got, want), first_mismatch(got, want)
     fin, _ = oracle_run(L, N)
+    assert same(c.get_state(), fin)
+    c.close()
+
+
+@pytest.mark.parametrize("kind,ctas", [(1, 5), (2, 0)])
+def test_expired_wait_reports_timeout_and_recovers(mpt, kind, ctas):
+    """A device-side wait that runs out (its flag is not set within one poll)
+    ends the launch with MPT_ETIMEDOUT; the state is put back and the next
+    launch with the normal bound is bit-exact again."""
+    L, N = 21, 90
+    c = gpu_ctx(mpt, L, N, ctas=ctas, kind=kind)
+    before = c.get_state()
+    c.set_wait_limit(1)
+    with pytest.raises(mpt.MPTError) as ei:
+        c.integrate(3)
+    assert ei.value.code == mpt.MPT_ETIMEDOUT
+    assert all(np.array_equal(x, y) for x, y in zip(before, c.get_state()))
+    c.set_wait_limit(0)
+    c.integrate(2)
+    fin, _ = oracle_run(L, N, nsteps=2)
     assert same(c.get_state(), fin)
     c.close()
