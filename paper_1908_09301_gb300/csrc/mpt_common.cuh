@@ -98,12 +98,19 @@ __host__ __device__ __forceinline__ uint32_t mod_inv(uint32_t n, const Divisor &
 // registers slide down one limb per step through a cyclic copy C of B padded
 // with W zeros (C[x] = b_x for x < Lp, 0 below M = Lp + W), so the hand-over
 // from block1 to block2 needs no reload.  A unit covers steps [s0, s1)
-// (multiples of W); the block1 sums are saved by a predicated copy at the
-// hand-over, so a warp never diverges.  Results are added (negated when `neg`)
-// into an int64 column window `win` (skewed layout) at column offset `off`.
+// (multiples of W).  The block1 sums are saved at the hand-over; the copy is
+// predicated per lane and only issued in chunks where some lane among the
+// ones running together hands over (a vote over the active lanes: a lane that
+// needs the copy always takes it, the others copy nothing), so lanes of one
+// warp never diverge and callers may run units in loops of unequal length.
+//
+// Output: v1[t] (t < W+2) is the block1 contribution to column qW + t,
+// v2[t] the block2 contribution to column qW + Lp + t, as signed int64
+// digits of the exact 96-bit column sums.
 template <bool SPARSE>
-__device__ __forceinline__ void mac_unit(const uint32_t *A, const uint32_t *C, int q, int s0,
-                                         int s1, int Lp, int M, long long *win, int off, bool neg)
+__device__ __forceinline__ void mac_unit_vals(const uint32_t *A, const uint32_t *C, int q, int s0,
+                                              int s1, int Lp, int M, long long v1[W + 2],
+                                              long long v2[W + 2])
 {
     uint32_t a0[W], a1[W], a2[W], k0[W], k1[W], k2[W], bw[W];
     {
@@ -120,27 +127,34 @@ __device__ __forceinline__ void mac_unit(const uint32_t *A, const uint32_t *C, i
     const int jt = q + 1;  // chunk at which block2 starts
     for (int j = s0 / W; j < s1 / W; j++) {
         const bool snap = (j == jt);
+        if (__any_sync(__activemask(), snap)) {
 #pragma unroll
-        for (int k = 0; k < W; k++) {
-            k0[k] = snap ? a0[k] : k0[k];
-            k1[k] = snap ? a1[k] : k1[k];
-            k2[k] = snap ? a2[k] : k2[k];
+            for (int k = 0; k < W; k++) {
+                k0[k] = snap ? a0[k] : k0[k];
+                k1[k] = snap ? a1[k] : k1[k];
+                k2[k] = snap ? a2[k] : k2[k];
+            }
         }
         const int ib = (j < jt) ? j * W : (j - 1) * W;
         const uint32_t *Ap = A + phys(ib);
         int xg = (q - j - 1) * W;
         if (xg < 0) xg += M;
         const uint32_t *Cp = C + phys(xg);
+        uint32_t av[W], bn[W];
 #pragma unroll
         for (int u = 0; u < W; u++) {
-            const uint32_t av = Ap[u];
-            if (!SPARSE || av != 0u) {
+            av[u] = Ap[u];
+            bn[u] = Cp[W - 1 - u];
+        }
 #pragma unroll
-                for (int k = 0; k < W; k++) mac_cc(av, bw[k], a0[k], a1[k], a2[k]);
+        for (int u = 0; u < W; u++) {
+            if (!SPARSE || av[u] != 0u) {
+#pragma unroll
+                for (int k = W - 1; k >= 0; k--) mac_cc(av[u], bw[k], a0[k], a1[k], a2[k]);
             }
 #pragma unroll
             for (int k = W - 1; k > 0; k--) bw[k] = bw[k - 1];
-            bw[0] = Cp[W - 1 - u];
+            bw[0] = bn[u];
         }
     }
     // block1 = saved sums (or all of it when the hand-over lies beyond s1)
@@ -152,28 +166,41 @@ __device__ __forceinline__ void mac_unit(const uint32_t *A, const uint32_t *C, i
             k2[k] = a2[k];
         }
     }
+#pragma unroll
+    for (int t = 0; t < W + 2; t++) {
+        long long x1 = 0, x2 = 0;
+        if (t < W) {
+            x1 += k0[t];
+            x2 += (long long)a0[t] - k0[t];
+        }
+        if (t >= 1 && t - 1 < W) {
+            x1 += k1[t - 1];
+            x2 += (long long)a1[t - 1] - k1[t - 1];
+        }
+        if (t >= 2 && t - 2 < W) {
+            x1 += k2[t - 2];
+            x2 += (long long)a2[t - 2] - k2[t - 2];
+        }
+        v1[t] = x1;
+        v2[t] = x2;
+    }
+}
+
+// the unit's contributions added (negated when `neg`) into an int64 column
+// window `win` (skewed layout) at column offset `off`
+template <bool SPARSE>
+__device__ __forceinline__ void mac_unit(const uint32_t *A, const uint32_t *C, int q, int s0,
+                                         int s1, int Lp, int M, long long *win, int off, bool neg)
+{
+    long long v1[W + 2], v2[W + 2];
+    mac_unit_vals<SPARSE>(A, C, q, s0, s1, Lp, M, v1, v2);
     const int c1 = off + q * W, c2 = c1 + Lp;
 #pragma unroll
     for (int t = 0; t < W + 2; t++) {
-        long long v1 = 0, v2 = 0;
-        if (t < W) {
-            v1 += k0[t];
-            v2 += (long long)a0[t] - k0[t];
-        }
-        if (t >= 1 && t - 1 < W) {
-            v1 += k1[t - 1];
-            v2 += (long long)a1[t - 1] - k1[t - 1];
-        }
-        if (t >= 2 && t - 2 < W) {
-            v1 += k2[t - 2];
-            v2 += (long long)a2[t - 2] - k2[t - 2];
-        }
-        if (neg) {
-            v1 = -v1;
-            v2 = -v2;
-        }
-        if (v1) atomicAdd((unsigned long long *)&win[wphys(c1 + t)], (unsigned long long)v1);
-        if (v2) atomicAdd((unsigned long long *)&win[wphys(c2 + t)], (unsigned long long)v2);
+        long long x1 = neg ? -v1[t] : v1[t];
+        long long x2 = neg ? -v2[t] : v2[t];
+        if (x1) atomicAdd((unsigned long long *)&win[wphys(c1 + t)], (unsigned long long)x1);
+        if (x2) atomicAdd((unsigned long long *)&win[wphys(c2 + t)], (unsigned long long)x2);
     }
 }
 
@@ -227,10 +254,18 @@ __device__ Norm warp_normalize(const long long *col, uint32_t *dig, int Wn, int 
     const int c0 = lane * K;
     const int c1 = min(c0 + K, Wn);
     long long carry = 0;
-    for (int c = c0; c < c1; c++) {
-        long long v = col[wphys(c)] + carry;
-        dig[c] = (uint32_t)v;
-        carry = v >> 32;
+    for (int c = c0; c < c1; c += 8) {
+        long long v[8];
+#pragma unroll
+        for (int k = 0; k < 8; k++) v[k] = (c + k < c1) ? col[wphys(c + k)] : 0;
+#pragma unroll
+        for (int k = 0; k < 8; k++) {
+            if (c + k < c1) {
+                long long t = v[k] + carry;
+                dig[c + k] = (uint32_t)t;
+                carry = t >> 32;
+            }
+        }
     }
     long long top = 0;
     bool settled = false;

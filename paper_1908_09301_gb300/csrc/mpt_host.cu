@@ -80,6 +80,7 @@ struct mpt_ctx {
     int pipe_C = 8;             // CTAs in the closer cluster (fixed by the kernel)
     int pipe_max_grid = 0;      // co-resident CTAs in whole clusters
     int pipe_tb = 0;
+    int pipe_umax = 0;
     size_t pipe_smem = 0;
     unsigned *pub = nullptr, *done = nullptr;
     long long *gin = nullptr;
@@ -305,10 +306,19 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
         return fail(MPT_ECUDA, "kernel does not fit on the device");
     }
     {
-        int ptb = 32;
-        while (ptb > 8 && mpt::pipe_smem_bytes(c->Lp, c->N, c->Wcap, ptb) > (size_t)smem_optin) ptb /= 2;
+        // worker staging: operand slots for up to 32 products and as many
+        // unit results as fit next to them (at least one product's units)
+        int ptb = 32, umax = 4096;
+        const int min_umax = 4 * c->P;
+        while (umax > min_umax &&
+               mpt::pipe_smem_bytes(c->Lp, c->N, c->Wcap, ptb, umax) > (size_t)smem_optin)
+            umax -= 64;
+        while (ptb > 8 && mpt::pipe_smem_bytes(c->Lp, c->N, c->Wcap, ptb, umax) > (size_t)smem_optin)
+            ptb /= 2;
+        if (umax < min_umax) umax = min_umax;
         c->pipe_tb = ptb;
-        c->pipe_smem = mpt::pipe_smem_bytes(c->Lp, c->N, c->Wcap, ptb);
+        c->pipe_umax = umax;
+        c->pipe_smem = mpt::pipe_smem_bytes(c->Lp, c->N, c->Wcap, ptb, umax);
         c->pipe_max_grid = 0;
         if (c->pipe_smem <= (size_t)smem_optin) {
             int ncl = mpt::pipe_max_clusters(c->pipe_C, c->pipe_smem);
@@ -542,6 +552,7 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
         pa.done = c->done;
         pa.gin = c->gin;
         pa.C = c->pipe_C;
+        pa.umax = c->pipe_umax;
         a.tb = c->pipe_tb;
         ce = cudaMemsetAsync(c->pub, 0, sizeof(unsigned), c->st);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(c->done, 0, sizeof(unsigned) * mpt::PIPE_SETS, c->st);

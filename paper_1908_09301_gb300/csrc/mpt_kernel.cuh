@@ -75,9 +75,10 @@ struct PArgs {
     unsigned *done;  // [PIPE_SETS] workers finished with an index (monotone)
     long long *gin;  // [PIPE_SETS][2][Wcap] inner Cauchy sums (targets beta, gamma)
     int C;           // CTAs of the closer cluster
+    int umax;        // worker units staged per batch
 };
 
-size_t pipe_smem_bytes(int Lp, int N, int Wcap, int tb);
+size_t pipe_smem_bytes(int Lp, int N, int Wcap, int tb, int umax);
 int pipe_max_clusters(int C, size_t smem);
 cudaError_t launch_pipe(const KArgs &a, const PArgs &pa, int grid, size_t smem, cudaStream_t st);
 

@@ -38,6 +38,7 @@ namespace {
 constexpr int CP_C = 8;                               // CTAs of the closer cluster
 constexpr int NA = 8;                                 // A-layout vector slots of the closer
 constexpr int NC = 8;                                 // C-layout vector slots of the closer
+constexpr int HU = NT;                                // Horner units per step (one per thread)
 
 // closer vector slots
 enum { A_SIGMA = 0, A_R, A_B, A_TAU, A_ALPHA0, A_ALPHAM, A_BETAM, A_CI };
@@ -46,13 +47,19 @@ enum { P_SIGMA = 0, P_R = 1, P_B = 2, P_TAU = 3 };
 
 struct PSmem {
     int *expT, *flgT;    // [3][N+1]
-    long long *win;      // [3][wsz] local accumulators (outer terms / inner terms)
-    long long *comb;     // [3][wsz] closer CTA 0: combined windows
+    int *tinfo;          // [max(tb, 64)][4]
+    int *misc;           // [MISC_INTS]
+    // closer CTAs
+    long long *win;      // [3][wsz] outer-term accumulators
+    long long *comb;     // [3][wsz] CTA 0: combined windows
     uint32_t *dig;       // [3][Wcap]
-    uint32_t *newc;      // [3][Lp] plain limbs of the newest number (closer CTA 0)
-    uint32_t *vec;       // closer: [NA][AV] then [NC][CV]; worker: [tb][AV+CV]
-    int *tinfo;          // [tb or 64][4]
-    int *misc;           // [256]
+    uint32_t *newc;      // [3][Lp] plain limbs of the newest number (CTA 0)
+    uint32_t *vec;       // [NA][AV] then [NC][CV]
+    long long *hstage;   // [2 (W+2)][HU + 1] Horner unit results
+    // worker CTAs (same bytes as the closer's part)
+    uint32_t *wvec;      // [tb][AV + CV]
+    long long *stage;    // [2 (W+2)][umax + 1] unit results (odd row stride: no bank conflicts)
+    long long *wwin;     // [2][wsz] inner-sum windows (beta, gamma)
     int AV, CV, M, wsz;
 };
 
@@ -72,6 +79,7 @@ enum {
     MS_HF = 56,      // [3] Horner flags
     MS_RED = 64,     // [8 warps][6] long long reduction scratch: ints 64..159
     MS_STATUS = 160, // CTA-uniform copy of the status word
+    MS_HERR = 161,   // Horner of this CTA failed
     MISC_INTS = 256
 };
 
@@ -85,7 +93,7 @@ __host__ __device__ inline void psizes(int Lp, int Wcap, int &AV, int &CV, int &
     wsz = wsize(Wcap);
 }
 
-__host__ __device__ inline size_t pipe_layout(int Lp, int N, int Wcap, int tb, PSmem *S,
+__host__ __device__ inline size_t pipe_layout(int Lp, int N, int Wcap, int tb, int umax, PSmem *S,
                                               unsigned char *base)
 {
     int AV, CV, M, wsz;
@@ -96,14 +104,17 @@ __host__ __device__ inline size_t pipe_layout(int Lp, int N, int Wcap, int tb, P
         o = al16(o + bytes);
         return base ? base + at : nullptr;
     };
-    int nvec = tb * (AV + CV);
-    int cvec = NA * AV + NC * CV;
-    if (cvec > nvec) nvec = cvec;
     unsigned char *p;
     p = take(sizeof(int) * 3 * (N + 1));
     if (S) S->expT = (int *)p;
     p = take(sizeof(int) * 3 * (N + 1));
     if (S) S->flgT = (int *)p;
+    p = take(sizeof(int) * 4 * (tb > 64 ? tb : 64));
+    if (S) S->tinfo = (int *)p;
+    p = take(sizeof(int) * MISC_INTS);
+    if (S) S->misc = (int *)p;
+    const size_t u0 = o;
+    // closer part
     p = take(sizeof(long long) * 3 * wsz);
     if (S) S->win = (long long *)p;
     p = take(sizeof(long long) * 3 * wsz);
@@ -112,12 +123,20 @@ __host__ __device__ inline size_t pipe_layout(int Lp, int N, int Wcap, int tb, P
     if (S) S->dig = (uint32_t *)p;
     p = take(sizeof(uint32_t) * 3 * Lp);
     if (S) S->newc = (uint32_t *)p;
-    p = take(sizeof(uint32_t) * (size_t)nvec);
+    p = take(sizeof(uint32_t) * (size_t)(NA * AV + NC * CV));
     if (S) S->vec = (uint32_t *)p;
-    p = take(sizeof(int) * 4 * (tb > 64 ? tb : 64));
-    if (S) S->tinfo = (int *)p;
-    p = take(sizeof(int) * MISC_INTS);
-    if (S) S->misc = (int *)p;
+    p = take(sizeof(long long) * 2 * (W + 2) * (size_t)(HU + 1));
+    if (S) S->hstage = (long long *)p;
+    const size_t closer_end = o;
+    // worker part, over the same bytes
+    o = u0;
+    p = take(sizeof(uint32_t) * (size_t)tb * (AV + CV));
+    if (S) S->wvec = (uint32_t *)p;
+    p = take(sizeof(long long) * 2 * (W + 2) * (size_t)(umax + 1));
+    if (S) S->stage = (long long *)p;
+    p = take(sizeof(long long) * 2 * wsz);
+    if (S) S->wwin = (long long *)p;
+    if (closer_end > o) o = closer_end;
     if (S) {
         S->AV = AV;
         S->CV = CV;
@@ -296,19 +315,53 @@ __device__ __forceinline__ Chunking chunking(long long pairs, long long threads,
     return c;
 }
 
+// Chunks per column pair for nt terms on NT threads: the H in 1..4 whose
+// units fill the threads' rounds best (a unit per thread per round), a little
+// biased toward fewer, longer units; units of one batch must fit `umax`.
+__device__ __forceinline__ Chunking worker_chunking(int nt, int P, int umax)
+{
+    int best = 1;
+    double best_score = -1.0;
+    for (int H = 1; H <= 4; H++) {
+        const int CL = ((P + 1 + H - 1) / H) * W;
+        const int He = ((P + 1) * W + CL - 1) / CL;
+        const long long U = (long long)nt * P * He;
+        if (H > 1 && U > umax) break;
+        const double x = (double)U / NT;
+        const double rounds = ceil(x);
+        const double score = x / rounds - 0.03 * (He - 1);
+        if (score > best_score + 1e-9) {
+            best_score = score;
+            best = H;
+        }
+    }
+    Chunking c;
+    c.CL = ((P + 1 + best - 1) / best) * W;
+    c.H = ((P + 1) * W + c.CL - 1) / c.CL;
+    return c;
+}
+
+// Workers: the inner Cauchy sums of index m (pairs a = 1..m-1, which need
+// coefficients up to m-1 only).  Each worker takes a contiguous range of
+// whole products; inside a CTA the units are ordered (chunk, pair, product),
+// so a warp holds few distinct column pairs.  Units write their column
+// digits to a private staging slot; a column reduction then adds each
+// window column once into the global accumulator set.
 __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa)
 {
     const int N1 = a.N + 1, Lp = a.Lp, P = a.P;
     const int nw = gridDim.x - CP_C;
     const int w = blockIdx.x - CP_C;
     const int SL = S.AV + S.CV;
+    const int umax = pa.umax;
+    const int ustride = umax + 1;
     const bool prof_on = (blockIdx.x == gridDim.x - 1);
-    for (int e = threadIdx.x; e < 2 * S.wsz; e += NT) S.win[e] = 0;
-    // C padding of every slot stays zero
+    // C padding of every slot stays zero; windows start empty
     for (int e = threadIdx.x; e < a.tb * S.M; e += NT) {
         int slot = e / S.M, x = e - slot * S.M;
-        if (x >= Lp) S.vec[(size_t)slot * SL + S.AV + phys(x)] = 0u;
+        if (x >= Lp) S.wvec[(size_t)slot * SL + S.AV + phys(x)] = 0u;
     }
+    for (int e = threadIdx.x; e < 2 * S.wsz; e += NT) S.wwin[e] = 0;
     __syncthreads();
     for (long long step = 0; step < a.nsteps; step++) {
         for (int m = 0; m < a.N; m++) {
@@ -332,87 +385,129 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa)
             pr.mark(PR_PLACE);
             if (S.misc[MS_STATUS] != 0) return;  // window too wide: status set, stop
             const int T = 2 * (m - 1);
-            const Chunking ck = chunking((long long)T * P, (long long)nw * NT, P);
-            const long long U = (long long)T * ck.H * P;
-            const long long u0 = U * w / nw, u1 = U * (w + 1) / nw;
-            if (u0 < u1) {
-                const long long per_term = (long long)ck.H * P;
-                const int tA = (int)(u0 / per_term), tB = (int)((u1 - 1) / per_term);
-                for (int tb0 = tA; tb0 <= tB; tb0 += a.tb) {
-                    const int nt = min(a.tb, tB - tb0 + 1);
-                    // per-slot term info and source rows
-                    if (threadIdx.x < nt) {
-                        int tg, neg, ac, ai, bc, bi;
-                        inner_term(m, tb0 + threadIdx.x, tg, neg, ac, ai, bc, bi);
-                        int fa = S.flgT[ac * N1 + ai], fb = S.flgT[bc * N1 + bi];
-                        bool skip = !(fa & F_NZ) || !(fb & F_NZ);
-                        int off = 0;
-                        if (!skip) {
-                            long long lp = (long long)S.expT[ac * N1 + ai] + S.expT[bc * N1 + bi] - 2LL * a.L;
-                            off = (int)(lp - ((long long *)(S.misc + MS_IBASE))[tg]);
-                        }
-                        int sgn = neg ^ (fa & F_NEG) ^ (fb & F_NEG);
-                        S.tinfo[4 * threadIdx.x] = off;
-                        S.tinfo[4 * threadIdx.x + 1] = (skip ? 4 : 0) | (sgn ? 1 : 0) | (tg << 4);
-                        S.tinfo[4 * threadIdx.x + 2] = ac * N1 + ai;
-                        S.tinfo[4 * threadIdx.x + 3] = bc * N1 + bi;
+            const int tA = (int)((long long)T * w / nw), tB = (int)((long long)T * (w + 1) / nw);
+            long long *gset = pa.gin + (size_t)set * 2 * a.Wcap;
+            const Chunking ck = worker_chunking(tB - tA, P, umax);
+            const int per_term = ck.H * P;
+            const int tbw = max(1, min(a.tb, umax / per_term));
+            for (int tb0 = tA; tb0 < tB; tb0 += tbw) {
+                const int nt = min(tbw, tB - tb0);
+                const int U = nt * per_term;
+                // per-slot term info and source rows
+                if (threadIdx.x < nt) {
+                    int tg, neg, ac, ai, bc, bi;
+                    inner_term(m, tb0 + threadIdx.x, tg, neg, ac, ai, bc, bi);
+                    int fa = S.flgT[ac * N1 + ai], fb = S.flgT[bc * N1 + bi];
+                    bool skip = !(fa & F_NZ) || !(fb & F_NZ);
+                    int off = 0;
+                    if (!skip) {
+                        long long lp = (long long)S.expT[ac * N1 + ai] + S.expT[bc * N1 + bi] - 2LL * a.L;
+                        off = (int)(lp - ((long long *)(S.misc + MS_IBASE))[tg]);
                     }
-                    __syncthreads();
-                    // stage alpha_a (A layout) and gamma/beta_{m-a} (C layout): all
-                    // loads of a thread are issued before its stores
-                    {
-                        const int total = nt * 2 * Lp;
-                        for (int e0 = 0; e0 < total; e0 += NT * 8) {
-                            uint32_t v[8];
-                            int dst[8];
-#pragma unroll
-                            for (int k = 0; k < 8; k++) {
-                                const int e = e0 + k * NT + threadIdx.x;
-                                dst[k] = -1;
-                                v[k] = 0u;
-                                if (e < total) {
-                                    const int slot = e / (2 * Lp), r = e - slot * 2 * Lp;
-                                    const int which = r >= Lp, x = r - which * Lp;
-                                    const int row = S.tinfo[4 * slot + 2 + which];
-                                    v[k] = __ldcg(&a.coefL[(size_t)row * Lp + x]);
-                                    dst[k] = slot * SL + (which ? S.AV : 0) + phys(x);
-                                }
-                            }
-#pragma unroll
-                            for (int k = 0; k < 8; k++)
-                                if (dst[k] >= 0) S.vec[dst[k]] = v[k];
-                        }
-                    }
-                    __syncthreads();
-                    pr.mark(PR_STAGE);
-                    const long long ua = max(u0, (long long)tb0 * per_term);
-                    const long long ub = min(u1, (long long)(tb0 + nt) * per_term);
-                    for (long long u = ua + threadIdx.x; u < ub; u += NT) {
-                        const int t = (int)(u / per_term);
-                        const int rem = (int)(u - (long long)t * per_term);
-                        const int h = rem / P, q = rem - h * P;
-                        const int slot = t - tb0;
-                        const int fl = S.tinfo[4 * slot + 1];
-                        if (fl & 4) continue;
-                        const int s0 = h * ck.CL, s1 = min(s0 + ck.CL, (P + 1) * W);
-                        const int tg = (fl >> 4) & 3;
-                        const uint32_t *Av = S.vec + (size_t)slot * SL;
-                        mac_unit<false>(Av, Av + S.AV, q, s0, s1, Lp, S.M,
-                                        S.win + (size_t)(tg - 1) * S.wsz, S.tinfo[4 * slot], fl & 1);
-                    }
-                    __syncthreads();
-                    pr.mark(PR_MAC);
+                    int sgn = neg ^ (fa & F_NEG) ^ (fb & F_NEG);
+                    S.tinfo[4 * threadIdx.x] = off;
+                    S.tinfo[4 * threadIdx.x + 1] = (skip ? 4 : 0) | (sgn ? 1 : 0) | (tg << 4);
+                    S.tinfo[4 * threadIdx.x + 2] = ac * N1 + ai;
+                    S.tinfo[4 * threadIdx.x + 3] = bc * N1 + bi;
                 }
+                __syncthreads();
+                // stage alpha_a (A layout) and gamma/beta_{m-a} (C layout): all
+                // loads of a thread are issued before its stores
+                {
+                    const int total = nt * 2 * Lp;
+                    for (int e0 = 0; e0 < total; e0 += NT * 8) {
+                        uint32_t v[8];
+                        int dst[8];
+#pragma unroll
+                        for (int k = 0; k < 8; k++) {
+                            const int e = e0 + k * NT + threadIdx.x;
+                            dst[k] = -1;
+                            v[k] = 0u;
+                            if (e < total) {
+                                const int slot = e / (2 * Lp), r = e - slot * 2 * Lp;
+                                const int which = r >= Lp, x = r - which * Lp;
+                                const int row = S.tinfo[4 * slot + 2 + which];
+                                v[k] = __ldcg(&a.coefL[(size_t)row * Lp + x]);
+                                dst[k] = slot * SL + (which ? S.AV : 0) + phys(x);
+                            }
+                        }
+#pragma unroll
+                        for (int k = 0; k < 8; k++)
+                            if (dst[k] >= 0) S.wvec[dst[k]] = v[k];
+                    }
+                }
+                __syncthreads();
+                pr.mark(PR_STAGE);
+                // units (chunk h, pair q, product tl): u = (h P + q) nt + tl
+                for (int u = threadIdx.x; u < U; u += NT) {
+                    const int tl = u % nt;
+                    const int hq = u / nt;
+                    const int h = hq / P, q = hq - h * P;
+                    const int fl = S.tinfo[4 * tl + 1];
+                    long long v1[W + 2], v2[W + 2];
+                    if (fl & 4) {
+#pragma unroll
+                        for (int t = 0; t < W + 2; t++) v1[t] = v2[t] = 0;
+                    } else {
+                        const int s0 = h * ck.CL, s1 = min(s0 + ck.CL, (P + 1) * W);
+                        const uint32_t *Av = S.wvec + (size_t)tl * SL;
+                        mac_unit_vals<false>(Av, Av + S.AV, q, s0, s1, Lp, S.M, v1, v2);
+                        if (fl & 1) {
+#pragma unroll
+                            for (int t = 0; t < W + 2; t++) {
+                                v1[t] = -v1[t];
+                                v2[t] = -v2[t];
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int t = 0; t < W + 2; t++) {
+                        S.stage[(size_t)t * ustride + u] = v1[t];
+                        S.stage[(size_t)(W + 2 + t) * ustride + u] = v2[t];
+                    }
+                }
+                __syncthreads();
+                pr.mark(PR_MAC);
+                // reduction: every (pair q, block b, digit k) sums the chunks
+                // of each product with the same target and offset and adds the
+                // sum at column off + b Lp + q W + k of the shared window
+                for (int cb = threadIdx.x; cb < P * 2 * (W + 2); cb += NT) {
+                    const int q = cb / (2 * (W + 2)), r = cb - q * 2 * (W + 2);
+                    const int b = r / (W + 2), k = r - b * (W + 2);
+                    const long long *st = S.stage + (size_t)r * ustride + (size_t)q * nt;
+                    long long sum = 0;
+                    int cur_tg = -1, cur_off = 0;
+                    for (int tl = 0; tl < nt; tl++) {
+                        const int fl = S.tinfo[4 * tl + 1];
+                        if (fl & 4) continue;
+                        const int tg = (fl >> 4) & 3, off = S.tinfo[4 * tl];
+                        if (tg != cur_tg || off != cur_off) {
+                            if (sum)
+                                atomicAdd((unsigned long long *)&S.wwin[(size_t)(cur_tg - 1) * S.wsz +
+                                                                      wphys(cur_off + b * Lp + q * W + k)],
+                                          (unsigned long long)sum);
+                            sum = 0;
+                            cur_tg = tg;
+                            cur_off = off;
+                        }
+                        for (int h = 0; h < ck.H; h++) sum += st[(size_t)h * P * nt + tl];
+                    }
+                    if (sum)
+                        atomicAdd((unsigned long long *)&S.wwin[(size_t)(cur_tg - 1) * S.wsz +
+                                                              wphys(cur_off + b * Lp + q * W + k)],
+                                  (unsigned long long)sum);
+                }
+                __syncthreads();
+                pr.mark(PR_FLUSH);
             }
-            // add the shared windows into the global set and count this CTA done
-            long long *dst = pa.gin + (size_t)set * 2 * a.Wcap;
+            // the shared windows into the global set
             for (int tg = 1; tg <= 2; tg++) {
                 const int wd = S.misc[MS_IWIDTH + tg];
-                long long *src = S.win + (size_t)(tg - 1) * S.wsz;
+                long long *src = S.wwin + (size_t)(tg - 1) * S.wsz;
                 for (int c = threadIdx.x; c < wd; c += NT) {
-                    long long v = src[wphys(c)];
+                    const long long v = src[wphys(c)];
                     if (v) {
-                        atomicAdd((unsigned long long *)&dst[(size_t)(tg - 1) * a.Wcap + c],
+                        atomicAdd((unsigned long long *)&gset[(size_t)(tg - 1) * a.Wcap + c],
                                   (unsigned long long)v);
                         src[wphys(c)] = 0;
                     }
@@ -423,7 +518,6 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa)
                 __threadfence();
                 atomicAdd(&pa.done[set], 1u);
             }
-            pr.mark(PR_FLUSH);
         }
     }
 }
@@ -678,6 +772,162 @@ __device__ void pull_newest(PSmem &S, const KArgs &a, cg::cluster_group &cl, boo
     }
 }
 
+// One Horner chain of Eq. (2) for component c, in one CTA: h_N = c_N,
+// h_i = trunc_L(tau h_{i+1} + c_i) for i = N-1 .. 0, then the new state (and
+// a record).  The product tau h is split into (chunk, pair) units, one per
+// thread; their column digits are staged and summed per (pair, block, digit)
+// into the window, c_i (prefetched from global one step ahead) is added, and
+// warp 0 normalises and truncates.
+__device__ void horner_component(PSmem &S, const KArgs &a, int c, long long step, Prof &pr)
+{
+    const int N1 = a.N + 1, Lp = a.Lp, L = a.L, P = a.P;
+    const int cslot = c == 0 ? C_ALPHAM : (c == 1 ? C_BETAM : C_GAMMAM);
+    uint32_t *hC = S.vec + (size_t)NA * S.AV + (size_t)cslot * S.CV;  // h in C layout
+    const uint32_t *tauA = S.vec + (size_t)A_TAU * S.AV;
+    uint32_t *hp = S.newc + (size_t)c * Lp;                           // h, plain limbs
+    long long *win = S.win;
+    const int tauE = __ldg(&a.parE[P_TAU]), tauF = __ldg(&a.parF[P_TAU]);
+    // chunks: at most one unit per thread
+    int He = HU / P;
+    if (He < 1) He = 1;
+    if (He > P + 1) He = P + 1;
+    const int CL = ((P + 1 + He - 1) / He) * W;
+    He = ((P + 1) * W + CL - 1) / CL;
+    const int U = P * He;
+    int *hE = S.misc + MS_HE + c, *hF = S.misc + MS_HF + c;
+    if (threadIdx.x == 0) {
+        *hE = S.expT[c * N1 + a.N];
+        *hF = S.flgT[c * N1 + a.N];
+    }
+    for (int x = threadIdx.x; x < Lp; x += NT) hp[x] = hC[phys(x)];
+    uint32_t cur[4], nxt[4];
+#pragma unroll
+    for (int r = 0; r < 4; r++) {
+        const int x = threadIdx.x + r * NT;
+        cur[r] = (x < Lp && a.N >= 1) ? __ldcg(&a.coefL[((size_t)c * N1 + a.N - 1) * Lp + x]) : 0u;
+    }
+    __syncthreads();
+    for (int i = a.N - 1; i >= 0; i--) {
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+            const int x = threadIdx.x + r * NT;
+            nxt[r] = (i > 0 && x < Lp) ? __ldcg(&a.coefL[((size_t)c * N1 + i - 1) * Lp + x]) : 0u;
+        }
+        // window: the product tau h and the lone c_i
+        const int he = *hE, hf = *hF;
+        const int ce = S.expT[c * N1 + i], cf = S.flgT[c * N1 + i];
+        const bool prod = (hf & F_NZ) && (tauF & F_NZ);
+        const bool lone = (cf & F_NZ) != 0;
+        const long long lpp = (long long)tauE + he - 2LL * L, lpa = (long long)ce - L;
+        long long lo = LLONG_MAX, hi = LLONG_MIN;
+        if (prod) {
+            lo = min(lo, lpp);
+            hi = max(hi, lpp + 2LL * Lp + 2);
+        }
+        if (lone) {
+            lo = min(lo, lpa);
+            hi = max(hi, lpa + Lp + 2);
+        }
+        int width = 0;
+        if (hi > lo) {
+            if (hi - lo > a.Wcap) {
+                if (threadIdx.x == 0) {
+                    atomicCAS(a.status, 0, DEV_ERANGE);
+                    S.misc[MS_HERR] = 1;
+                }
+                break;  // uniform: every thread computed the same width
+            }
+            width = (int)(hi - lo);
+        }
+        const int offp = (int)(lpp - lo), offa = (int)(lpa - lo);
+        const bool pneg = ((hf ^ tauF) & F_NEG) != 0;
+        if (prod && threadIdx.x < U) {
+            const int h = threadIdx.x / P, q = threadIdx.x - h * P;
+            const int s0 = h * CL, s1 = min(s0 + CL, (P + 1) * W);
+            long long v1[W + 2], v2[W + 2];
+            mac_unit_vals<false>(tauA, hC, q, s0, s1, Lp, S.M, v1, v2);
+#pragma unroll
+            for (int t = 0; t < W + 2; t++) {
+                S.hstage[(size_t)t * (HU + 1) + threadIdx.x] = pneg ? -v1[t] : v1[t];
+                S.hstage[(size_t)(W + 2 + t) * (HU + 1) + threadIdx.x] = pneg ? -v2[t] : v2[t];
+            }
+        }
+        __syncthreads();
+        pr.mark(PR_HMAC);
+        if (prod) {
+            for (int cb = threadIdx.x; cb < P * 2 * (W + 2); cb += NT) {
+                const int q = cb / (2 * (W + 2)), r = cb - q * 2 * (W + 2);
+                const int b = r / (W + 2), k = r - b * (W + 2);
+                long long sum = 0;
+                for (int h = 0; h < He; h++) sum += S.hstage[(size_t)r * (HU + 1) + h * P + q];
+                if (sum)
+                    atomicAdd((unsigned long long *)&win[wphys(offp + b * Lp + q * W + k)],
+                              (unsigned long long)sum);
+            }
+        }
+        if (lone) {
+#pragma unroll
+            for (int r = 0; r < 4; r++) {
+                const int x = threadIdx.x + r * NT;
+                if (x < Lp && cur[r]) {
+                    const long long v = (cf & F_NEG) ? -(long long)cur[r] : (long long)cur[r];
+                    atomicAdd((unsigned long long *)&win[wphys(offa + x)], (unsigned long long)v);
+                }
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            int e = 0, f = 0;
+            if (width > 0) {
+                Norm nr = warp_normalize(win, S.dig, width, a.status);
+                for (int cc = lane; cc < width; cc += 32) win[wphys(cc)] = 0;
+                if (nr.top >= 0) {
+                    long long eq = warp_divide(S.dig, nr.top, lo, 1u, L, hp);
+                    if (eq > (1LL << 30) || eq < -(1LL << 30)) {
+                        if (lane == 0) {
+                            atomicCAS(a.status, 0, DEV_ERANGE);
+                            S.misc[MS_HERR] = 1;
+                        }
+                        eq = 0;
+                    }
+                    e = (int)eq;
+                    f = F_NZ | (nr.neg ? F_NEG : 0);
+                }
+            }
+            if (!(f & F_NZ))
+                for (int x = lane; x < L; x += 32) hp[x] = 0u;
+            __syncwarp();
+            for (int x = lane; x < Lp; x += 32) hC[phys(x)] = x < L ? hp[x] : 0u;
+            if (lane == 0) {
+                *hE = e;
+                *hF = f;
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) cur[r] = nxt[r];
+        __syncthreads();
+        pr.mark(PR_HCLOSE);
+        if (S.misc[MS_HERR]) break;
+    }
+    // the new state and, when due, a record
+    const long long rec = (a.record_every > 0 && ((step + 1) % a.record_every) == 0)
+                              ? (step + 1) / a.record_every - 1 : -1;
+    for (int x = threadIdx.x; x < Lp; x += NT) {
+        a.stL[(size_t)c * Lp + x] = hp[x];
+        if (rec >= 0 && x < L) a.recL[((size_t)rec * 3 + c) * L + x] = hp[x];
+    }
+    if (threadIdx.x == 0) {
+        a.stE[c] = *hE;
+        a.stF[c] = *hF;
+        if (rec >= 0) {
+            a.recS[rec * 3 + c] = (*hF & F_NEG) ? 1 : 0;
+            a.recE[rec * 3 + c] = *hE;
+        }
+    }
+    __threadfence();
+}
+
 __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa)
 {
     cg::cluster_group cl = cg::this_cluster();
@@ -869,113 +1119,22 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa)
             pr.mark(PR_X4);
         }
         if (stop) break;
-        // Horner (Eq. (2)): h_N = c_N (already in the newest slots)
+        // Horner (Eq. (2)), one component per CTA (ranks 0..2), no cluster
+        // barrier inside: h_N = c_N, h_i = trunc_L(tau h_{i+1} + c_i)
         Prof ph(a, prof_on, S.misc);
-        pull_newest(S, a, cl, false);
-        if (threadIdx.x < 3) {
-            S.misc[MS_HE + threadIdx.x + 0] = S.expT[threadIdx.x * N1 + a.N];
-            S.misc[MS_HF + threadIdx.x + 0] = S.flgT[threadIdx.x * N1 + a.N];
-        }
+        if (threadIdx.x == 0) S.misc[MS_HERR] = 0;
         __syncthreads();
-        cl.sync();
-        const int tauE = __ldg(&a.parE[P_TAU]), tauF = __ldg(&a.parF[P_TAU]);
-        for (int i = a.N - 1; i >= 0; i--) {
-            // terms: tau * h_c (dense, CTAs 1..C-1) and c_i (lone, CTA 0)
-            int nterm = 0;
-            long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
-            long long hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
-            if (threadIdx.x == 0) S.misc[MS_STATUS] = 0;
-            for (int c = 0; c < 3 && threadIdx.x == 0; c++) {
-                const int he = misc0[MS_HE + c], hf = misc0[MS_HF + c];
-                if ((hf & F_NZ) && (tauF & F_NZ)) {
-                    OTerm t;
-                    t.kind = 0;
-                    t.tg = c;
-                    t.neg = (hf ^ tauF) & F_NEG;
-                    t.aslot = A_TAU;
-                    t.bslot = C_H0 + c;
-                    t.lp = (long long)tauE + he - 2LL * L;
-                    t.v = 0;
-                    ot[nterm++] = t;
-                }
-            }
-            if (threadIdx.x == 0) {
-                for (int k = 0; k < nterm; k++) {
-                    lo[ot[k].tg] = min(lo[ot[k].tg], ot[k].lp);
-                    hi[ot[k].tg] = max(hi[ot[k].tg], term_top(ot[k], Lp));
-                }
-                S.misc[MS_NTERM] = nterm;
-            }
-            block_window(S, a, lo, hi, MS_OBASE, MS_OWIDTH);
-            nterm = S.misc[MS_NTERM];
-            if (rank == 0) {
-                // the lone c_i: its own window bounds, then the combined ones
-                if (threadIdx.x < 3) {
-                    const int c = threadIdx.x;
-                    const int ce = S.expT[c * N1 + i], cf = S.flgT[c * N1 + i];
-                    const long long lp = (long long)ce - L;
-                    ll_at(S.misc, MS_IBASE + 2 * c) = lp;
-                    S.misc[MS_IWIDTH + c] = (cf & F_NZ) ? Lp + 2 : 0;
-                }
-                __syncthreads();
-                combine_bases(S, a, true);
-                __syncthreads();
-                const bool bad = S.misc[MS_STATUS] != 0;
-                for (int e = threadIdx.x; e < 3 * Lp && !bad; e += NT) {
-                    const int c = e / Lp, x = e - c * Lp;
-                    if (!(S.flgT[c * N1 + i] & F_NZ)) continue;
-                    long long v = __ldcg(&a.coefL[((size_t)c * N1 + i) * Lp + x]);
-                    if (S.flgT[c * N1 + i] & F_NEG) v = -v;
-                    const long long shift =
-                        ll_at(S.misc, MS_IBASE + 2 * c) - ll_at(S.misc, MS_BASE + 2 * c);
-                    if (v) S.comb[(size_t)c * S.wsz + wphys((int)(x + shift))] += v;
-                }
-                if (threadIdx.x == 0) S.misc[MS_ERR_A] = bad || ld_relaxed_int(a.status) != 0;
-            } else if (S.misc[MS_STATUS] == 0) {
-                outer_units(S, a, ot, nterm, rank, C);
-            }
-            cl.sync();
-            ph.mark(PR_HMAC);
-            stop = misc0[MS_ERR_A] != 0;
-            if (!stop) reduce_outer(S, a, cl, rank, C);
-            cl.sync();
-            if (stop) break;
-            for (int e = threadIdx.x; e < 3 * S.wsz; e += NT) S.win[e] = 0;
-            if (rank == 0) {
-                int *eo = S.misc + MS_HE, *fo = S.misc + MS_HF;
-                close_three(S, a, 1u, eo, fo);
-                __syncthreads();
-                if (threadIdx.x == 0) S.misc[MS_ERR_C] = ld_relaxed_int(a.status) != 0;
-            }
-            cl.sync();
-            ph.mark(PR_HCLOSE);
-            stop = misc0[MS_ERR_C] != 0;
-            if (stop) break;
-            pull_newest(S, a, cl, false);
-            __syncthreads();
-        }
-        if (stop) break;
-        // the new state (and a record) from CTA 0; then the next step
-        if (rank == 0) {
-            const long long rec = (a.record_every > 0 && ((step + 1) % a.record_every) == 0)
-                                      ? (step + 1) / a.record_every - 1 : -1;
-            for (int e = threadIdx.x; e < 3 * Lp; e += NT) {
-                a.stL[e] = S.newc[e];
-                const int comp = e / Lp, x = e - comp * Lp;
-                if (rec >= 0 && x < L) a.recL[((size_t)rec * 3 + comp) * L + x] = S.newc[e];
-            }
-            if (threadIdx.x < 3) {
-                a.stE[threadIdx.x] = S.misc[MS_HE + threadIdx.x];
-                a.stF[threadIdx.x] = S.misc[MS_HF + threadIdx.x];
-                if (rec >= 0) {
-                    a.recS[rec * 3 + threadIdx.x] = (S.misc[MS_HF + threadIdx.x] & F_NEG) ? 1 : 0;
-                    a.recE[rec * 3 + threadIdx.x] = S.misc[MS_HE + threadIdx.x];
-                }
-            }
-            __threadfence();
-        }
+        if (rank < 3) horner_component(S, a, rank, step, ph);
+        __syncthreads();
         ph.mark(PR_HORNER);
-        cl.sync();
+        cl.sync();  // the new state is in global memory
+        {
+            // stop if any component failed (each CTA reads the same three flags)
+            int bad = 0;
+            for (int r = 0; r < 3; r++) bad |= cl.map_shared_rank(S.misc, r)[MS_HERR];
+            stop = bad != 0;
+        }
+        cl.sync();  // flags read; the next step may reuse them
     }
     cl.sync();  // the only way out of the closer
 }
@@ -984,7 +1143,7 @@ __global__ void __launch_bounds__(NT, 1) pipe_kernel(KArgs a, PArgs pa)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     PSmem S;
-    pipe_layout(a.Lp, a.N, a.Wcap, a.tb, &S, smem_raw);
+    pipe_layout(a.Lp, a.N, a.Wcap, a.tb, pa.umax, &S, smem_raw);
     const bool prof_cta = blockIdx.x == 0 || blockIdx.x == gridDim.x - 1;
     if (threadIdx.x < PROF_SLOTS) ((long long *)(S.misc + MS_PROF))[threadIdx.x] = 0;
     __syncthreads();
@@ -1002,9 +1161,9 @@ __global__ void __launch_bounds__(NT, 1) pipe_kernel(KArgs a, PArgs pa)
 
 }  // namespace
 
-size_t pipe_smem_bytes(int Lp, int N, int Wcap, int tb)
+size_t pipe_smem_bytes(int Lp, int N, int Wcap, int tb, int umax)
 {
-    return pipe_layout(Lp, N, Wcap, tb, nullptr, nullptr);
+    return pipe_layout(Lp, N, Wcap, tb, umax, nullptr, nullptr);
 }
 
 static cudaLaunchConfig_t pipe_config(int grid, int C, size_t smem, cudaStream_t st,
