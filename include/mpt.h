@@ -190,6 +190,45 @@ int mpt_get_profile(mpt_ctx *ctx, int64_t *cycles, int n);
 int mpt_int_peak_run(int variant, int threads, int iters, double *mean_cycles, double *ms,
                      int *distinct_sms, int *grid_out);
 
+/*
+ * Allocation-free stepping (the paper has no counterpart; it is a service of
+ * this library).  Some callers cannot call cudaMalloc when they step: code
+ * whose device memory belongs to a pool it may not grow, a plug-in of a
+ * runtime that forbids allocation after start-up, or code that must not
+ * synchronise with the allocator.  mpt_integrate_noalloc runs nsteps Taylor
+ * steps (the same arithmetic as mpt_integrate, bit-identical results) with
+ * all working memory in one static device array of
+ * MPT_NOALLOC_SCRATCH_BYTES (4 MiB) that every GPU loading this library
+ * holds until the process exits; it calls no allocating routine.
+ *
+ * Arguments: L limbs and order N as for mpt_init; the parameters sigma, R,
+ * b, tau as 4 numbers (par_signs[4], par_exps[4], par_limbs[4][L]); the
+ * state x, y, z as 3 numbers (signs[3], exps[3], limbs[3][L]), read at the
+ * start and overwritten with the state after nsteps steps.  All six arrays
+ * are in the interchange layout and must be memory the current device can
+ * read and write (device, managed or registered host memory); they stay the
+ * caller's.  Work is queued on cuda_stream (0 = legacy default stream) and
+ * the call returns when it is done.
+ *
+ * Limits and errors: MPT_EINVAL for sizes outside those of mpt_init, for a
+ * null or unreachable pointer, for a malformed number, and when L and N need
+ * more scratch than the array holds (about 12 (N+1) L bytes plus a few
+ * kilobytes: L <= 64 fits every N, L = 208 (2000 digits) fits N <= 1641,
+ * L = 1024 fits N <= 319); the message gives the bytes needed.  On any error
+ * the caller's state is left as it was.
+ *
+ * The first call on a device takes the array's device address and queries
+ * the device (with that device current); make that first call before any
+ * stream capture.  Every call on a device shares the one array and clears
+ * the parts that must start at zero itself; calls that overlap on the GPU
+ * (two host threads, or two streams at once) race on it and must be
+ * serialised by the caller.
+ */
+#define MPT_NOALLOC_SCRATCH_BYTES 4194304u
+int mpt_integrate_noalloc(int L, int N, int64_t nsteps, const int32_t *par_signs,
+                          const int32_t *par_exps, const uint32_t *par_limbs, int32_t *signs,
+                          int32_t *exps, uint32_t *limbs, uint64_t cuda_stream);
+
 /* Message for an error code; message of the calling thread's last error. */
 const char *mpt_strerror(int code);
 const char *mpt_last_error(void);

@@ -51,6 +51,15 @@ struct DeviceGuard {
 
 }  // namespace
 
+namespace mpt {
+// sets the calling thread's mpt_last_error() message from another translation unit
+int record_error(int code, const char *msg)
+{
+    g_last_error = msg;
+    return code;
+}
+}  // namespace mpt
+
 struct mpt_ctx {
     int L = 0, Lp = 0, P = 0, N = 0, Wcap = 0, tb = 0;
     int dev = 0, sms = 0;

@@ -57,6 +57,8 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
                                         ctypes.POINTER(ctypes.c_int)]),
+    "mpt_integrate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp,
+                                             vp, vp, vp, vp, ctypes.c_uint64]),
     "mpt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mpt_last_error": (ctypes.c_char_p, []),
 }
@@ -253,6 +255,24 @@ class Context:
         c = ctypes.c_int()
         _check(lib().mpt_get_launch(self._h, ctypes.byref(c)))
         return c.value
+
+
+def integrate_noalloc(L: int, N: int, nsteps: int, params, state, stream: int | None = None):
+    """nsteps Taylor steps through ``mpt_integrate_noalloc``, which keeps its
+    working memory in a static device array instead of allocating, for callers
+    that may not allocate device memory while they step.
+
+    ``params`` = (signs[4], exps[4], limbs[4, L]) for sigma, R, b, tau and
+    ``state`` = (signs[3], exps[3], limbs[3, L]), which is overwritten with the
+    new state: contiguous torch tensors (int32 / int32 / int32 or uint32
+    viewed as 32-bit) on the current CUDA device.  Calls that overlap on the
+    GPU race on the shared array."""
+    if stream is None:
+        stream = _current_stream()
+    ps, pe, pl = params
+    ss, se, sl = state
+    _check(lib().mpt_integrate_noalloc(int(L), int(N), int(nsteps), _ptr(ps), _ptr(pe), _ptr(pl),
+                                       _ptr(ss), _ptr(se), _ptr(sl), ctypes.c_uint64(int(stream))))
 
 
 def int_peak(variant: int, iters: int = 20000, threads: int = 1024):
