@@ -42,8 +42,11 @@ UNIT = "steps/s"
 # one exact limb product needs a low and a high half, so the limb-product
 # roofline is half of it.
 IMAD_PER_SM_CLK = 64
-PROFILE = os.path.join(ROOT, "profiles", "taylor_kernel_k2000_n1000.md")
-KERNEL_SOURCES = ["paper_1908_09301_gb300/csrc/mpt_step.cu",
+# ncu summary of the dominant kernel on this workload (DRAM bytes per launch),
+# valid while the kernel's sources hash to the value recorded in it
+PROFILE = os.path.join(ROOT, "profiles", "pipe_kernel_k2000_n1000.md")
+KERNEL_SOURCES = ["paper_1908_09301_gb300/csrc/mpt_pipe.cu",
+                  "paper_1908_09301_gb300/csrc/mpt_common.cuh",
                   "paper_1908_09301_gb300/csrc/mpt_kernel.cuh"]
 
 

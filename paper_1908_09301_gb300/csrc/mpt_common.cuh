@@ -1,7 +1,8 @@
-// mpt_common.cuh -- device building blocks of the multiple-precision Taylor
-// step (Sec. 2 of Dimova et al., arXiv 1908.09301): exact limb products into
-// int64 column windows, carry normalisation, division by a small integer with
-// truncation to L limbs.  Shared by the kernels of this library.
+// mpt_common.cuh -- device building blocks of the pipelined multiple-precision
+// Taylor step (Sec. 2 of Dimova et al., arXiv 1908.09301): exact sums of limb
+// products in int64 column windows, carry normalisation, division by a small
+// integer with truncation to L limbs.  The block-level routines assume PT
+// threads per CTA.
 #pragma once
 #include <climits>
 #include <cstdint>
@@ -12,14 +13,17 @@
 namespace mpt {
 
 constexpr unsigned FULL = 0xffffffffu;
+constexpr int NWARPS = PT / 32;
 
-// Shared-memory layout of an operand vector: one padding word every 8 words,
-// so that lanes reading words 8 apart hit different banks.
-__host__ __device__ __forceinline__ int phys(int x) { return x + (x >> 3); }
+// ------------------------------------------------------------------ operand layout
 
-// int64 accumulator windows use the same skew (one padding column every 8).
-__host__ __device__ __forceinline__ int wphys(int c) { return c + (c >> 3); }
-__host__ __device__ __forceinline__ int wsize(int Wcap) { return wphys(Wcap) + 1; }
+// Operand vectors in shared memory: limb x sits at gpos(x); every group of
+// W = 8 limbs starts on a 48-byte boundary, so a group is two 128-bit loads and
+// eight consecutive groups start on eight different 4-bank windows.
+constexpr int GS = 12;  // words per limb group
+__host__ __device__ __forceinline__ int gpos(int x) { return (x >> 3) * GS + (x & 7); }
+// words of a vector of n limbs (n a multiple of W)
+__host__ __device__ __forceinline__ int vwords(int n) { return (n >> 3) * GS; }
 
 // one 32x32 limb product added into a 96-bit column (c0, c1, c2)
 __device__ __forceinline__ void mac_cc(uint32_t a, uint32_t b, uint32_t &c0, uint32_t &c1,
@@ -89,150 +93,91 @@ __host__ __device__ __forceinline__ uint32_t mod_inv(uint32_t n, const Divisor &
     return n - div_inv(n, v) * v.d;
 }
 
-// ------------------------------------------------------------------ limb-product units
+#ifdef __CUDACC__
 
-// Columns of the exact product A*B (Lp x Lp limbs, column c = sum_i a_i b_{c-i}).
-// A thread owns column pair q: block1 = [qW, qW+W), block2 = [qW+Lp, qW+Lp+W);
-// the pair holds W*Lp products and is walked as s = 0 .. (P+1)W-1 (block1
-// for s < (q+1)W with i = s, block2 after with i = s - W).  The W b-limbs in
-// registers slide down one limb per step through a cyclic copy C of B padded
-// with W zeros (C[x] = b_x for x < Lp, 0 below M = Lp + W), so the hand-over
-// from block1 to block2 needs no reload.  A unit covers steps [s0, s1)
-// (multiples of W).  The block1 sums are saved at the hand-over; the copy is
-// predicated per lane and only issued in chunks where some lane among the
-// ones running together hands over (a vote over the active lanes: a lane that
-// needs the copy always takes it, the others copy nothing), so lanes of one
-// warp never diverge and callers may run units in loops of unequal length.
-//
-// Output: v1[t] (t < W+2) is the block1 contribution to column qW + t,
-// v2[t] the block2 contribution to column qW + Lp + t, as signed int64
-// digits of the exact 96-bit column sums.
-template <bool SPARSE>
-__device__ __forceinline__ void mac_unit_vals(const uint32_t *A, const uint32_t *C, int q, int s0,
-                                              int s1, int Lp, int M, long long v1[W + 2],
-                                              long long v2[W + 2])
+// ------------------------------------------------------------------ limb products
+
+// One chunk of a unit walk.  A unit q of the product A' * C (A' of M = (P+1)W
+// limbs, C of Lp limbs kept as a cyclic vector of period M with zeros at
+// [Lp, M)) owns columns qW..qW+W-1 of block 0 and the same columns plus M of
+// block 1.  Walking the limbs of A' in chunks of W, chunk j pairs a_{jW+u}
+// with c_{(qW + k - jW - u) mod M} in column k; chunks j <= q land in block
+// 0 and chunks j > q in block 1 (the limbs that wrap into the zero padding
+// between the two contribute nothing, so the split may be made per chunk).
+// gA = j, gC0 = (q - j) mod (P+1), gC1 = (q - j - 1) mod (P+1) are limb groups.
+__device__ __forceinline__ void chunk_mac(const uint32_t *A, const uint32_t *C, int gA, int gC0,
+                                          int gC1, uint32_t (&c0)[W], uint32_t (&c1)[W],
+                                          uint32_t (&c2)[W])
 {
-    uint32_t a0[W], a1[W], a2[W], k0[W], k1[W], k2[W], bw[W];
-    {
-        int x0 = q * W - s0;
-        if (x0 < 0) x0 += M;  // aligned to W, so the W limbs do not wrap
-        const uint32_t *Cp = C + phys(x0);
+    const uint4 *pa = reinterpret_cast<const uint4 *>(A + gA * GS);
+    const uint4 *pb = reinterpret_cast<const uint4 *>(C + gC0 * GS);
+    const uint4 *pn = reinterpret_cast<const uint4 *>(C + gC1 * GS);
+    const uint4 a_lo = pa[0], a_hi = pa[1], b_lo = pb[0], b_hi = pb[1], n_lo = pn[0], n_hi = pn[1];
+    const uint32_t av[W] = {a_lo.x, a_lo.y, a_lo.z, a_lo.w, a_hi.x, a_hi.y, a_hi.z, a_hi.w};
+    const uint32_t bw[W] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
+    const uint32_t bn[W] = {n_lo.x, n_lo.y, n_lo.z, n_lo.w, n_hi.x, n_hi.y, n_hi.z, n_hi.w};
 #pragma unroll
-        for (int k = 0; k < W; k++) {
-            a0[k] = a1[k] = a2[k] = 0u;
-            k0[k] = k1[k] = k2[k] = 0u;
-            bw[k] = Cp[k];
-        }
-    }
-    const int jt = q + 1;  // chunk at which block2 starts
-    for (int j = s0 / W; j < s1 / W; j++) {
-        const bool snap = (j == jt);
-        if (__any_sync(__activemask(), snap)) {
+    for (int u = 0; u < W; u++) {
 #pragma unroll
-            for (int k = 0; k < W; k++) {
-                k0[k] = snap ? a0[k] : k0[k];
-                k1[k] = snap ? a1[k] : k1[k];
-                k2[k] = snap ? a2[k] : k2[k];
-            }
+        for (int k = W - 1; k >= 0; k--) {
+            const uint32_t b = (k >= u) ? bw[k - u] : bn[W + k - u];
+            mac_cc(av[u], b, c0[k], c1[k], c2[k]);
         }
-        const int ib = (j < jt) ? j * W : (j - 1) * W;
-        const uint32_t *Ap = A + phys(ib);
-        int xg = (q - j - 1) * W;
-        if (xg < 0) xg += M;
-        const uint32_t *Cp = C + phys(xg);
-        uint32_t av[W], bn[W];
-#pragma unroll
-        for (int u = 0; u < W; u++) {
-            av[u] = Ap[u];
-            bn[u] = Cp[W - 1 - u];
-        }
-#pragma unroll
-        for (int u = 0; u < W; u++) {
-            if (!SPARSE || av[u] != 0u) {
-#pragma unroll
-                for (int k = W - 1; k >= 0; k--) mac_cc(av[u], bw[k], a0[k], a1[k], a2[k]);
-            }
-#pragma unroll
-            for (int k = W - 1; k > 0; k--) bw[k] = bw[k - 1];
-            bw[0] = bn[u];
-        }
-    }
-    // block1 = saved sums (or all of it when the hand-over lies beyond s1)
-    if (jt * W >= s1) {
-#pragma unroll
-        for (int k = 0; k < W; k++) {
-            k0[k] = a0[k];
-            k1[k] = a1[k];
-            k2[k] = a2[k];
-        }
-    }
-#pragma unroll
-    for (int t = 0; t < W + 2; t++) {
-        long long x1 = 0, x2 = 0;
-        if (t < W) {
-            x1 += k0[t];
-            x2 += (long long)a0[t] - k0[t];
-        }
-        if (t >= 1 && t - 1 < W) {
-            x1 += k1[t - 1];
-            x2 += (long long)a1[t - 1] - k1[t - 1];
-        }
-        if (t >= 2 && t - 2 < W) {
-            x1 += k2[t - 2];
-            x2 += (long long)a2[t - 2] - k2[t - 2];
-        }
-        v1[t] = x1;
-        v2[t] = x2;
     }
 }
 
-// the unit's contributions added (negated when `neg`) into an int64 column
-// window `win` (skewed layout) at column offset `off`
-template <bool SPARSE>
-__device__ __forceinline__ void mac_unit(const uint32_t *A, const uint32_t *C, int q, int s0,
-                                         int s1, int Lp, int M, long long *win, int off, bool neg)
+// int64 digit t (t < W+2) of the 96-bit columns (c0, c1, c2)[k]: the column
+// sums as sum_t digit_t 2^(32t)
+__device__ __forceinline__ long long col_digit(const uint32_t (&c0)[W], const uint32_t (&c1)[W],
+                                               const uint32_t (&c2)[W], int t)
 {
-    long long v1[W + 2], v2[W + 2];
-    mac_unit_vals<SPARSE>(A, C, q, s0, s1, Lp, M, v1, v2);
-    const int c1 = off + q * W, c2 = c1 + Lp;
-#pragma unroll
-    for (int t = 0; t < W + 2; t++) {
-        long long x1 = neg ? -v1[t] : v1[t];
-        long long x2 = neg ? -v2[t] : v2[t];
-        if (x1) atomicAdd((unsigned long long *)&win[wphys(c1 + t)], (unsigned long long)x1);
-        if (x2) atomicAdd((unsigned long long *)&win[wphys(c2 + t)], (unsigned long long)x2);
-    }
+    long long v = 0;
+    if (t < W) v += c0[t];
+    if (t >= 1 && t - 1 < W) v += c1[t - 1];
+    if (t >= 2 && t - 2 < W) v += c2[t - 2];
+    return v;
 }
 
-// a lone number +-c (staged in A layout): limbs [qW, qW+W) into the window
-__device__ __forceinline__ void add_unit(const uint32_t *A, int q, long long *win, int off, bool neg)
+// ------------------------------------------------------------------ block reductions
+
+__device__ __forceinline__ long long warp_min_ll(long long v)
 {
-#pragma unroll
-    for (int k = 0; k < W; k++) {
-        long long v = A[phys(q * W + k)];
-        if (v) atomicAdd((unsigned long long *)&win[wphys(off + q * W + k)],
-                         (unsigned long long)(neg ? -v : v));
+    for (int o = 16; o; o >>= 1) {
+        long long w = __shfl_xor_sync(FULL, v, o);
+        v = w < v ? w : v;
     }
+    return v;
+}
+__device__ __forceinline__ long long warp_max_ll(long long v)
+{
+    for (int o = 16; o; o >>= 1) {
+        long long w = __shfl_xor_sync(FULL, v, o);
+        v = w > v ? w : v;
+    }
+    return v;
 }
 
-// v * c for a one-limb multiplier v (c staged in A layout): limbs [qW, qW+W)
-__device__ __forceinline__ void scaled_unit(uint32_t v, const uint32_t *A, int q, long long *win,
-                                            int off, bool neg)
+// block-wide min (max) of v, returned in every thread; red holds >= NWARPS
+// long longs; two __syncthreads.
+__device__ __forceinline__ long long block_min_ll(long long v, long long *red)
 {
-    long long lo[W + 1];
-#pragma unroll
-    for (int k = 0; k <= W; k++) lo[k] = 0;
-#pragma unroll
-    for (int k = 0; k < W; k++) {
-        uint64_t p = (uint64_t)v * A[phys(q * W + k)];
-        lo[k] += (long long)(uint32_t)p;
-        lo[k + 1] += (long long)(p >> 32);
-    }
-#pragma unroll
-    for (int k = 0; k <= W; k++) {
-        long long x = neg ? -lo[k] : lo[k];
-        if (x) atomicAdd((unsigned long long *)&win[wphys(off + q * W + k)], (unsigned long long)x);
-    }
+    v = warp_min_ll(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    long long r = red[0];
+    for (int w = 1; w < NWARPS; w++) r = red[w] < r ? red[w] : r;
+    __syncthreads();
+    return r;
+}
+__device__ __forceinline__ long long block_max_ll(long long v, long long *red)
+{
+    v = warp_max_ll(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    long long r = red[0];
+    for (int w = 1; w < NWARPS; w++) r = red[w] > r ? red[w] : r;
+    __syncthreads();
+    return r;
 }
 
 // ------------------------------------------------------------------ close: normalise, divide
@@ -242,104 +187,213 @@ struct Norm {
     int top;  // index of the top non-zero digit, -1 for zero
 };
 
-// Exact value of Wn int64 columns (sum col[c] 2^(32c), skewed layout in
-// shared memory) as sign and magnitude digits.  One warp; lane l owns columns
-// [lK, lK+K).  Local carries first, then carries that cross lanes ride up one
-// lane per round until none is left (a carry is absorbed or passed on, so 32
-// rounds always suffice).
-__device__ Norm warp_normalize(const long long *col, uint32_t *dig, int Wn, int *status)
+// A carry map: the adjustment (-1, 0 or +1) that leaves a thread's digits
+// for each adjustment that arrives from below.  Three 2-bit fields (value +
+// 1) for arrivals -1, 0, +1.
+__device__ __forceinline__ int cmap_apply(int f, int x) { return ((f >> (2 * (x + 1))) & 3) - 1; }
+// g after f
+__device__ __forceinline__ int cmap_compose(int g, int f)
 {
-    const int lane = threadIdx.x & 31;
-    const int K = (Wn + 31) >> 5;
-    const int c0 = lane * K;
-    const int c1 = min(c0 + K, Wn);
-    long long carry = 0;
-    for (int c = c0; c < c1; c += 8) {
-        long long v[8];
+    int r = 0;
 #pragma unroll
-        for (int k = 0; k < 8; k++) v[k] = (c + k < c1) ? col[wphys(c + k)] : 0;
-#pragma unroll
-        for (int k = 0; k < 8; k++) {
-            if (c + k < c1) {
-                long long t = v[k] + carry;
-                dig[c + k] = (uint32_t)t;
-                carry = t >> 32;
-            }
-        }
+    for (int x = -1; x <= 1; x++) r |= (cmap_apply(g, cmap_apply(f, x)) + 1) << (2 * (x + 1));
+    return r;
+}
+constexpr int CMAP_ID = (0 << 0) | (1 << 2) | (2 << 4);
+
+// carry out of adding cin to the digits dig[c0..c1) (c1 > c0); in {-1, 0, 1}
+// when |cin| < 2^32
+__device__ __forceinline__ int carry_through(const uint32_t *dig, int c0, int c1, long long cin)
+{
+    long long c = cin;
+    for (int x = c0; x < c1 && c != 0; x++) {
+        const long long v = (long long)dig[x] + c;
+        c = v >> 32;
     }
-    long long top = 0;
-    bool settled = false;
-    for (int round = 0; round < 40; round++) {
-        top += __shfl_sync(FULL, carry, 31);
-        long long cin = __shfl_up_sync(FULL, carry, 1);
-        if (lane == 0) cin = 0;
-        if (!__any_sync(FULL, cin != 0)) {
-            settled = true;
-            break;
-        }
-        long long c = cin;
-        for (int cc = c0; cc < c1 && c != 0; cc++) {
-            long long v = (long long)dig[cc] + c;
-            dig[cc] = (uint32_t)v;
-            c = v >> 32;
-        }
-        carry = c;
-    }
-    if (!settled && lane == 0) atomicCAS(status, 0, DEV_INTERNAL);
+    return (int)c;
+}
+
+constexpr int KMAX = 8;      // columns per thread the normalisation keeps in registers
+constexpr int RED_LL = 96;   // long longs of scratch the block routines need
+
+// Exact value of Wn int64 columns (sum col[c] 2^(32c), plain layout) as sign
+// and magnitude digits dig[0..Wn), Wn <= KK PT.  Thread t owns columns
+// [tKK, tKK+KK) and folds them into digits (kept in registers) and a local
+// carry (|carry| < 2^31).  The carry of thread t-1 moves thread t's carry out
+// by -1, 0 or +1 more, a function of what thread t-1 itself received, so these
+// adjustments come from one scan of 3-entry carry maps (within each warp,
+// then over the warps in warp 0, which also yields the sign), and are then
+// applied.  One merged reduction gives the lowest non-zero digit and the top
+// digit.  The magnitude is 2^(32 Wn) - D when the value is negative.  `red`
+// holds RED_LL long longs.  Needs |V| < 2^(32 Wn) (else status DEV_INTERNAL).
+template <int KK>
+__device__ Norm block_normalize_k(const long long *col, uint32_t *dig, int Wn, long long *red,
+                                  int *status)
+{
     Norm r;
-    r.neg = top < 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int c0 = min(tid * KK, Wn), nk = min(c0 + KK, Wn) - c0;
+    uint32_t d[KK];
+    long long lc = 0;
+#pragma unroll
+    for (int k = 0; k < KK; k++) {
+        d[k] = 0u;
+        if (k < nk) {
+            const long long v = col[c0 + k] + lc;
+            d[k] = (uint32_t)v;
+            lc = v >> 32;
+        }
+    }
+    long long *lcw = red;                  // [NWARPS] carries of lane 31
+    int *mapw = (int *)(red + NWARPS);     // [NWARPS] warp maps
+    int *pre = mapw + NWARPS;              // [NWARPS] maps of all lower warps
+    long long *fin = red + 2 * NWARPS;     // [0] top thread's carry, [1] final carry, [2+3w..] z, t0, t1
+    long long lprev = __shfl_up_sync(FULL, lc, 1);
+    if (lane == 31) lcw[warp] = lc;
+    if (nk > 0 && c0 + nk == Wn) fin[0] = lc;
+    __syncthreads();
+    if (lane == 0) lprev = warp ? lcw[warp - 1] : 0;
+    int f = CMAP_ID;
+    if (nk > 0) {
+        f = 0;
+#pragma unroll
+        for (int x = -1; x <= 1; x++) {
+            long long c = lprev + x;
+#pragma unroll
+            for (int k = 0; k < KK; k++)
+                if (k < nk) c = ((long long)d[k] + c) >> 32;
+            f |= ((int)c + 1) << (2 * (x + 1));
+        }
+    }
+    int F = f;  // inclusive scan of maps, lowest thread first
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int G = __shfl_up_sync(FULL, F, o);
+        if (lane >= o) F = cmap_compose(F, G);
+    }
+    if (lane == 31) mapw[warp] = F;
+    __syncthreads();
+    if (warp == 0) {
+        int G = lane < NWARPS ? mapw[lane] : CMAP_ID;
+#pragma unroll
+        for (int o = 1; o < NWARPS; o <<= 1) {
+            const int H = __shfl_up_sync(FULL, G, o);
+            if (lane >= o) G = cmap_compose(G, H);
+        }
+        int E = __shfl_up_sync(FULL, G, 1);
+        if (lane == 0) E = CMAP_ID;
+        if (lane < NWARPS) pre[lane] = E;
+        if (lane == NWARPS - 1) fin[1] = fin[0] + cmap_apply(G, 0);
+    }
+    __syncthreads();
+    int ex = __shfl_up_sync(FULL, F, 1);
+    if (lane == 0) ex = CMAP_ID;
+    const int din = cmap_apply(cmap_compose(ex, pre[warp]), 0);
+    long long cin = lprev + din;
+    long long z = LLONG_MAX, t0 = -1, t1 = -1;
+#pragma unroll
+    for (int k = 0; k < KK; k++) {
+        if (k < nk) {
+            const long long v = (long long)d[k] + cin;
+            d[k] = (uint32_t)v;
+            cin = v >> 32;
+            dig[c0 + k] = d[k];
+            if (d[k]) {
+                z = min(z, (long long)(c0 + k));
+                t0 = c0 + k;
+            }
+            if (d[k] != 0xffffffffu) t1 = c0 + k;
+        }
+    }
+    const long long topc = fin[1];
+    z = warp_min_ll(z);
+    t0 = warp_max_ll(t0);
+    t1 = warp_max_ll(t1);
+    if (lane == 0) {
+        fin[2 + 3 * warp] = z;
+        fin[3 + 3 * warp] = t0;
+        fin[4 + 3 * warp] = t1;
+    }
+    __syncthreads();
+    {
+        // the warps' values, reduced across lanes (lane w holds warp w's)
+        long long zz = LLONG_MAX, a0 = -1, a1 = -1;
+        if (lane < NWARPS) {
+            zz = fin[2 + 3 * lane];
+            a0 = fin[3 + 3 * lane];
+            a1 = fin[4 + 3 * lane];
+        }
+        z = warp_min_ll(zz);
+        t0 = warp_max_ll(a0);
+        t1 = warp_max_ll(a1);
+    }
+    if (topc != 0 && topc != -1 && tid == 0) atomicCAS(status, 0, DEV_INTERNAL);
+    r.neg = topc < 0;
+    r.top = (int)(r.neg ? max(t1, z) : t0);
     if (r.neg) {
         // |V| = 2^(32 Wn) - D: digits below the lowest non-zero one stay 0,
         // that one becomes 2^32 - d, the ones above are complemented
-        int zl = 0x7fffffff;
-        for (int c = c1 - 1; c >= c0; c--)
-            if (dig[c]) zl = c;
-        int z = zl;
-        for (int o = 16; o; o >>= 1) z = min(z, __shfl_xor_sync(FULL, z, o));
-        for (int c = c0; c < c1; c++) {
-            if (c > z) dig[c] = ~dig[c];
-            else if (c == z) dig[c] = 0u - dig[c];
+#pragma unroll
+        for (int k = 0; k < KK; k++) {
+            const int c = c0 + k;
+            if (k < nk) {
+                if (c > z) dig[c] = ~d[k];
+                else if (c == z) dig[c] = 0u - d[k];
+            }
         }
+        __syncthreads();
     }
-    int tl = -1;
-    for (int c = c0; c < c1; c++)
-        if (dig[c]) tl = c;
-    for (int o = 16; o; o >>= 1) tl = max(tl, __shfl_xor_sync(FULL, tl, o));
-    r.top = tl;
-    __syncwarp();
     return r;
+}
+
+__device__ Norm block_normalize(const long long *col, uint32_t *dig, int Wn, long long *red,
+                                int *status)
+{
+    if (Wn <= 0) {
+        Norm r;
+        r.neg = 0;
+        r.top = -1;
+        return r;
+    }
+    if (Wn <= PT) return block_normalize_k<1>(col, dig, Wn, red, status);
+    if (Wn <= 2 * PT) return block_normalize_k<2>(col, dig, Wn, red, status);
+    if (Wn <= 4 * PT) return block_normalize_k<4>(col, dig, Wn, red, status);
+    return block_normalize_k<KMAX>(col, dig, Wn, red, status);
 }
 
 // trunc_L(|E| / d) for |E| = sum_c dig[c] 2^(32(base+c)) with top digit t:
 // writes L limbs to out and returns the exponent.  Only limbs of |E| at or
 // above the quotient's lowest kept position matter,
 // floor(|E| / (d 2^(32 s))) = floor(floor(|E| / 2^(32 s)) / d); below the
-// window's lowest limb they are zero.  The long division runs on 32 lanes at
-// once: each lane's chunk is the affine map r -> (2^(32 len) r + chunk) mod d
-// on the running remainder, the maps are composed with a shuffle scan, then
-// every lane divides its chunk starting from its incoming remainder.
-__device__ long long warp_divide(const uint32_t *dig, int t, long long base, uint32_t d, int L,
-                                 uint32_t *out)
+// window's lowest limb they are zero.  The long division runs on all
+// threads: each thread's chunk of digits (the top chunk in thread 0) is the
+// affine map r -> (2^(32 len) r + chunk) mod d of the running remainder; the
+// maps are composed with a scan within each warp and one over the warps (in
+// warp 0), then every thread divides its chunk from its incoming remainder.
+// d < 2^16; `red` holds >= 4 NWARPS ints.  Ends with __syncthreads (out is
+// complete).
+__device__ long long block_divide(const uint32_t *dig, int t, long long base, const Divisor &dv,
+                                  int L, uint32_t *out, int *red)
 {
-    const int lane = threadIdx.x & 31;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long T = base + t + 1;
+    const uint32_t d = dv.d;
     const long long eq = (dig[t] >= d) ? T : T - 1;
     const long long s = eq - L;
-    const int nX = (int)(T - s);
-    const int KX = (nX + 31) >> 5;
-    const int jhi = min(nX - lane * KX, nX);
+    const int nX = (int)(T - s);  // L or L+1 digits j = 0 .. nX-1, bottom up
+    const int KX = (nX + PT - 1) / PT;
+    const int jhi = max(nX - tid * KX, 0);  // this thread: digits [jlo, jhi)
     const int jlo = max(jhi - KX, 0);
     auto X = [&](int j) -> uint32_t {
-        long long idx = s + j - base;
+        const long long idx = s + j - base;
         return idx >= 0 ? dig[idx] : 0u;
     };
     if (d == 1u) {
         for (int j = jhi - 1; j >= jlo; j--)
             if (j < L) out[j] = X(j);
-        __syncwarp();
+        __syncthreads();
         return eq;
     }
-    const Divisor dv = make_divisor(d);
     uint32_t t32 = 1;
     (void)divstep(t32, 0u, dv);  // 2^32 mod d
     uint32_t V = 0, Pm = 1;
@@ -347,21 +401,51 @@ __device__ long long warp_divide(const uint32_t *dig, int t, long long base, uin
         (void)divstep(V, X(j), dv);
         Pm = mod_inv(Pm * t32, dv);
     }
+    // inclusive scan: (P2, V2) after (P1, V1) = (P2 P1, P2 V1 + V2) mod d
+#pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        uint32_t Po = __shfl_up_sync(FULL, Pm, o);
-        uint32_t Vo = __shfl_up_sync(FULL, V, o);
+        const uint32_t Po = __shfl_up_sync(FULL, Pm, o);
+        const uint32_t Vo = __shfl_up_sync(FULL, V, o);
         if (lane >= o) {
             V = mod_inv(Pm * Vo + V, dv);
             Pm = mod_inv(Pm * Po, dv);
         }
     }
-    uint32_t r = __shfl_up_sync(FULL, V, 1);
-    if (lane == 0) r = 0;
+    int *wP = red, *wV = red + NWARPS, *eV = red + 2 * NWARPS;
+    if (lane == 31) {
+        wP[warp] = (int)Pm;
+        wV[warp] = (int)V;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t GP = lane < NWARPS ? (uint32_t)wP[lane] : 1u;
+        uint32_t GV = lane < NWARPS ? (uint32_t)wV[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < NWARPS; o <<= 1) {
+            const uint32_t Po = __shfl_up_sync(FULL, GP, o);
+            const uint32_t Vo = __shfl_up_sync(FULL, GV, o);
+            if (lane >= o) {
+                GV = mod_inv(GP * Vo + GV, dv);
+                GP = mod_inv(GP * Po, dv);
+            }
+        }
+        uint32_t EV = __shfl_up_sync(FULL, GV, 1);  // remainder leaving all lower warps
+        if (lane == 0) EV = 0;
+        if (lane < NWARPS) eV[lane] = (int)EV;
+    }
+    __syncthreads();
+    const uint32_t rin = (uint32_t)eV[warp];
+    uint32_t Pe = __shfl_up_sync(FULL, Pm, 1), Ve = __shfl_up_sync(FULL, V, 1);
+    if (lane == 0) {
+        Pe = 1;
+        Ve = 0;
+    }
+    uint32_t r = mod_inv(Pe * rin + Ve, dv);
     for (int j = jhi - 1; j >= jlo; j--) {
-        uint32_t qd = divstep(r, X(j), dv);
+        const uint32_t qd = divstep(r, X(j), dv);
         if (j < L) out[j] = qd;
     }
-    __syncwarp();
+    __syncthreads();
     return eq;
 }
 
@@ -372,9 +456,16 @@ __device__ __forceinline__ void cp_async4(uint32_t *dst_smem, const uint32_t *sr
     unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src_gmem) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all()
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src_gmem)
 {
-    asm volatile("cp.async.wait_all;" ::: "memory");
+    unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src_gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
 // ------------------------------------------------------------------ flags
@@ -385,9 +476,9 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p)
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release_u32(unsigned *p, unsigned v)
+__device__ __forceinline__ void red_release_add_u32(unsigned *p, unsigned v)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 __device__ __forceinline__ int ld_relaxed_int(const int *p)
 {
@@ -395,5 +486,7 @@ __device__ __forceinline__ int ld_relaxed_int(const int *p)
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+
+#endif  // __CUDACC__
 
 }  // namespace mpt

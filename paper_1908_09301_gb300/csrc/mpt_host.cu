@@ -86,13 +86,13 @@ struct mpt_ctx {
     long long spin_limit = mpt::DEFAULT_SPIN_LIMIT;
     // pipelined kernel (closer cluster + workers)
     int kind_req = 0;           // 0 auto, 1 lockstep, 2 pipelined
-    int pipe_C = 8;             // CTAs in the closer cluster (fixed by the kernel)
-    int pipe_max_grid = 0;      // co-resident CTAs in whole clusters
+    int pipe_C = 3;             // bracket CTAs of the pipelined kernel (fixed by the kernel)
+    int pipe_max_grid = 0;      // co-resident CTAs of the pipelined kernel
     int pipe_tb = 0;
-    int pipe_umax = 0;
     size_t pipe_smem = 0;
     unsigned *pub = nullptr, *done = nullptr;
     long long *gin = nullptr;
+    long long *imid = nullptr;
     // parameters in the interchange layout (host)
     int32_t par_s[4] = {0, 0, 0, 0}, par_e[4] = {0, 0, 0, 0};
     std::vector<uint32_t> par_l;
@@ -105,7 +105,7 @@ namespace {
 int kind_for(const mpt_ctx *c)
 {
     if (c->kind_req == 1) return 1;
-    bool pipe_ok = c->pipe_max_grid >= 2 * c->pipe_C && c->N >= 3;
+    bool pipe_ok = c->pipe_max_grid >= c->pipe_C + 1 && c->N >= 3;
     if (c->kind_req == 2) return pipe_ok ? 2 : 1;
     double work = (double)c->N * c->Lp * c->Lp;
     return (pipe_ok && work >= 5e5) ? 2 : 1;
@@ -114,11 +114,10 @@ int kind_for(const mpt_ctx *c)
 int pipe_grid_for(const mpt_ctx *c)
 {
     int g = c->pipe_max_grid;
-    int lim = (c->sms / c->pipe_C) * c->pipe_C;
-    if (g > lim) g = lim;
+    if (g > c->sms) g = c->sms;
     if (c->ctas_req > 0) {
-        int r = c->ctas_req / c->pipe_C * c->pipe_C;
-        if (r < 2 * c->pipe_C) r = 2 * c->pipe_C;
+        int r = c->ctas_req;
+        if (r < c->pipe_C + 1) r = c->pipe_C + 1;
         if (r < g) g = r;
     }
     return g;
@@ -205,7 +204,7 @@ void free_all(mpt_ctx *c)
 {
     void *ptrs[] = {c->coefL, c->coefE, c->coefF, c->parL, c->parE, c->parF, c->stL, c->stBackL,
                     c->stE, c->stF, c->stBackEF, c->gwin, c->bar, c->status, c->recS, c->recE,
-                    c->recL, c->prof, c->pub, c->done, c->gin};
+                    c->recL, c->prof, c->pub, c->done, c->gin, c->imid};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -315,24 +314,17 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
         return fail(MPT_ECUDA, "kernel does not fit on the device");
     }
     {
-        // worker staging: operand slots for up to 32 products and as many
-        // unit results as fit next to them (at least one product's units)
-        int ptb = 32, umax = 4096;
-        const int min_umax = 4 * c->P;
-        while (umax > min_umax &&
-               mpt::pipe_smem_bytes(c->Lp, c->N, c->Wcap, ptb, umax) > (size_t)smem_optin)
-            umax -= 64;
-        while (ptb > 8 && mpt::pipe_smem_bytes(c->Lp, c->N, c->Wcap, ptb, umax) > (size_t)smem_optin)
-            ptb /= 2;
-        if (umax < min_umax) umax = min_umax;
+        // worker term slots: as many as fit (at most pipe_tb_max())
+        int ptb = mpt::pipe_tb_max();
+        while (ptb > 1 && mpt::pipe_smem_bytes(L, c->Lp, c->N, c->Wcap, ptb) > (size_t)smem_optin)
+            ptb--;
         c->pipe_tb = ptb;
-        c->pipe_umax = umax;
-        c->pipe_smem = mpt::pipe_smem_bytes(c->Lp, c->N, c->Wcap, ptb, umax);
+        c->pipe_smem = mpt::pipe_smem_bytes(L, c->Lp, c->N, c->Wcap, ptb);
+        c->pipe_C = mpt::pipe_closer_ctas();
         c->pipe_max_grid = 0;
         if (c->pipe_smem <= (size_t)smem_optin) {
-            int ncl = mpt::pipe_max_clusters(c->pipe_C, c->pipe_smem);
+            c->pipe_max_grid = mpt::pipe_max_ctas(c->pipe_smem);
             (void)cudaGetLastError();
-            c->pipe_max_grid = ncl * c->pipe_C;
         }
     }
     const size_t N1 = (size_t)c->N + 1;
@@ -353,6 +345,7 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
     if (ce == cudaSuccess) ce = dalloc(&c->pub, 1);
     if (ce == cudaSuccess) ce = dalloc(&c->done, mpt::PIPE_SETS);
     if (ce == cudaSuccess) ce = dalloc(&c->gin, (size_t)mpt::PIPE_SETS * 2 * c->Wcap);
+    if (ce == cudaSuccess) ce = dalloc(&c->imid, (size_t)mpt::PIPE_SETS * 4);
     if (ce != cudaSuccess) {
         free_all(c);
         delete c;
@@ -561,8 +554,8 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
         pa.done = c->done;
         pa.gin = c->gin;
         pa.C = c->pipe_C;
-        pa.umax = c->pipe_umax;
-        a.tb = c->pipe_tb;
+        pa.imid = c->imid;
+        pa.tb = c->pipe_tb;
         ce = cudaMemsetAsync(c->pub, 0, sizeof(unsigned), c->st);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(c->done, 0, sizeof(unsigned) * mpt::PIPE_SETS, c->st);
         if (ce == cudaSuccess)

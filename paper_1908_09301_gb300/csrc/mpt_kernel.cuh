@@ -7,7 +7,8 @@
 namespace mpt {
 
 constexpr int W = 8;         // columns per limb-product block (register tile)
-constexpr int NT = 256;      // threads per CTA
+constexpr int NT = 256;      // threads per CTA of the lock-step kernel
+constexpr int PT = 512;      // threads per CTA of the pipelined kernel
 constexpr int MAX_L = 1024;  // limbs per number
 constexpr int MAX_N = 4096;  // Taylor order (exponent tables live in shared memory)
 
@@ -71,15 +72,19 @@ enum ProfSlot {
 constexpr int PIPE_SETS = 8;  // rotating global accumulator sets / completion counters
 
 struct PArgs {
-    unsigned *pub;   // [1] published coefficients of the launch (monotone)
-    unsigned *done;  // [PIPE_SETS] workers finished with an index (monotone)
-    long long *gin;  // [PIPE_SETS][2][Wcap] inner Cauchy sums (targets beta, gamma)
-    int C;           // CTAs of the closer cluster
-    int umax;        // worker units staged per batch
+    unsigned *pub;    // [1] component publications of the launch (monotone, 3 per coefficient)
+    unsigned *done;   // [PIPE_SETS] workers finished with an index (monotone)
+    long long *gin;   // [PIPE_SETS][2][Wcap] inner Cauchy sums (targets beta', gamma')
+    long long *imid;  // [PIPE_SETS][4] inner-sum windows without the two newest pairs
+    int C;            // bracket CTAs (pipe_closer_ctas())
+    int tb;           // worker term slots per batch (<= pipe_tb_max())
 };
 
-size_t pipe_smem_bytes(int Lp, int N, int Wcap, int tb, int umax);
-int pipe_max_clusters(int C, size_t smem);
+size_t pipe_smem_bytes(int L, int Lp, int N, int Wcap, int tb);
+int pipe_tb_max();
+int pipe_closer_ctas();
+// co-resident CTAs of the pipelined kernel (one per SM at most; 0 on error)
+int pipe_max_ctas(size_t smem);
 cudaError_t launch_pipe(const KArgs &a, const PArgs &pa, int grid, size_t smem, cudaStream_t st);
 
 // dynamic shared memory bytes for a configuration

@@ -1,105 +1,133 @@
 // mpt_pipe.cu -- pipelined multiple-precision Taylor step (Sec. 2 of Dimova
-// et al., arXiv 1908.09301) for large L x N: one persistent launch, two roles.
+// et al., arXiv 1908.09301) for large L x N: one persistent cooperative
+// launch, one CTA per SM, two roles.
 //
-//  * The critical path (one CTA cluster, "closer"): for each index m it forms
-//    the terms of Eq. (3)'s brackets that involve the newest coefficient m --
-//    the "outer" Cauchy products alpha_m gamma_0, alpha_0 gamma_m,
-//    alpha_m beta_0, alpha_0 beta_m and the linear terms sigma beta_m,
-//    sigma alpha_m, R alpha_m, b gamma_m, beta_m -- split over the cluster's
-//    CTAs, reduces them through distributed shared memory, adds the "inner"
-//    sums computed by the workers, normalises, divides by (m+1) and
-//    publishes coefficient m+1.  After index N-1 it runs the three Horner
-//    chains of Eq. (2), h_i = trunc_L(tau h_{i+1} + c_i), the same way.
-//  * The bulk ("workers", every other CTA): the inner part of the Cauchy
-//    sums, sum_{a=1}^{m-1} alpha_a gamma_{m-a} and alpha_a beta_{m-a}, which
-//    needs only coefficients up to m-1, so it is computed while the closer
-//    is still finishing index m-1.  Each worker takes a contiguous slice of
-//    the (product, chunk, column pair) units, accumulates exact int64 column
-//    windows in shared memory, adds them into a global window set and counts
-//    itself done.
+//  * Workers (every CTA but the first three) compute the inner part of
+//    Eq. (3)'s Cauchy sums of index m,
+//        Y_m = -sum_{a=1}^{m-1} alpha_a gamma_{m-a},  Z_m = sum_{a=1}^{m-1} alpha_a beta_{m-a},
+//    which needs coefficients up to m-1 only, while the bracket CTAs are
+//    still finishing coefficient m.  A worker takes a contiguous range of the
+//    2(m-1) terms.  All of its terms of one target are summed in one frame:
+//    a term whose lowest limb lies d = 8 d_hi + d_lo limbs above the window
+//    base has its first factor staged shifted up by d_lo limbs (and
+//    complemented when the term is negative; the complement's correction is
+//    added separately), so the terms with equal d_hi share columns and are
+//    accumulated in the same registers.  The CTA's window is added into a
+//    global window set and the worker counts itself done.
+//  * The bracket CTAs 0, 1, 2 own Eq. (3)'s brackets alpha', beta', gamma'.
+//    Each forms its products of the newest coefficient m with numbers fixed
+//    for the step (beta': alpha_m gamma_0, gamma_m alpha_0; gamma':
+//    alpha_m beta_0, beta_m alpha_0, gamma_m b) as one term group, adds its
+//    one-limb and lone terms and the workers' inner sums, normalises,
+//    divides by (m+1) and publishes its component of coefficient m+1; the
+//    three exchange components through global memory.  After index N-1 each
+//    runs the Horner chain of Eq. (2) for its component,
+//    h_i = trunc_L(tau h_{i+1} + c_i).
 //
-// Hand-over: a monotone "published" counter (release/acquire) and per-set
-// monotone completion counters; every wait is bounded and ends the launch
-// with a status code when it expires.  Integer sums are exact and
-// associative, so the result does not depend on the split.
+// Limb products use units: unit q of a product A' * C (A' of M = (P+1)W
+// limbs, C of Lp limbs) owns columns qW..qW+W-1 of two blocks (block 1 is M
+// columns up); R threads share a unit, each taking a contiguous share of its
+// (term, chunk) sequence, in which every term's block-0 chunks come before
+// any block-1 chunk, so a thread switches blocks at most once.  The shares
+// are summed through shared memory per (unit, block, digit), then added into
+// the window one column per thread.
+//
+// Hand-over: a monotone "published" counter (release/acquire, 3 per
+// coefficient) and per-set monotone completion counters; every wait is
+// bounded and ends the launch with a status code when it expires.  Integer
+// sums are exact and associative, so the result does not depend on the split.
 #include <climits>
 #include <cstdint>
-#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include "mpt_common.cuh"
 #include "mpt_kernel.cuh"
 
-namespace cg = cooperative_groups;
-
 namespace mpt {
 namespace {
 
-constexpr int CP_C = 8;                               // CTAs of the closer cluster
-constexpr int NA = 8;                                 // A-layout vector slots of the closer
-constexpr int NC = 8;                                 // C-layout vector slots of the closer
-constexpr int HU = NT;                                // Horner units per step (one per thread)
+constexpr int NCL = 3;           // bracket CTAs
+constexpr int NA = 4;            // A' slots of a bracket CTA: 3 product terms, Horner's h
+constexpr int NC = 4;            // C slots: 3 fixed factors, tau
+constexpr int NTERM = 3;         // product terms of a bracket
+constexpr int TI = 8;            // ints of term info per slot
+constexpr int TB_MAX = 32;       // worker slots per batch (one warp finds the groups)
 
-// closer vector slots
-enum { A_SIGMA = 0, A_R, A_B, A_TAU, A_ALPHA0, A_ALPHAM, A_BETAM, A_CI };
-enum { C_GAMMA0 = 0, C_BETA0, C_GAMMAM, C_BETAM, C_ALPHAM, C_H0, C_H1, C_H2 };
 enum { P_SIGMA = 0, P_R = 1, P_B = 2, P_TAU = 3 };
 
-struct PSmem {
-    int *expT, *flgT;    // [3][N+1]
-    int *tinfo;          // [max(tb, 64)][4]
-    int *misc;           // [MISC_INTS]
-    // closer CTAs
-    long long *win;      // [3][wsz] outer-term accumulators
-    long long *comb;     // [3][wsz] CTA 0: combined windows
-    uint32_t *dig;       // [3][Wcap]
-    uint32_t *newc;      // [3][Lp] plain limbs of the newest number (CTA 0)
-    uint32_t *vec;       // [NA][AV] then [NC][CV]
-    long long *hstage;   // [2 (W+2)][HU + 1] Horner unit results
-    // worker CTAs (same bytes as the closer's part)
-    uint32_t *wvec;      // [tb][AV + CV]
-    long long *stage;    // [2 (W+2)][umax + 1] unit results (odd row stride: no bank conflicts)
-    long long *wwin;     // [2][wsz] inner-sum windows (beta, gamma)
-    int AV, CV, M, wsz;
+enum {
+    MS_STATUS = 0,  // CTA-uniform copy of the status word
+    MS_NRUN = 1,    // term groups of the batch / bracket
+    MS_NEWE = 2,    // [2] exponent and flags of this CTA's newest number
+    MS_PSCAL = 8,   // [3][2] sigma, R, b: single non-zero limb index (or -1), value
+    MS_WLO = 16,    // [4] long long window bases (ints 16..23)
+    MS_WID = 24,    // [4] window widths (workers); bracket CTAs: [4] long long inner-window
+                    // table of the next index (ints 24..31, MS_IMID)
+    MS_IMID = 24,
+    MS_BK = 32,     // [32] bracket setup (ints 32..63)
+    MS_RED = 64,    // [RED_LL] long long scratch of the block routines (ints 64..255)
+    MS_RUN = 256,   // [TB_MAX] group starts
+    MS_RUNE = 288,  // [TB_MAX] group ends
+    MS_PROF = 320,  // [PROF_SLOTS] long long (ints 320..351)
+    MISC_INTS = 352
 };
 
+// bracket setup (ints at MS_BK): lo (long long), width, simple parts, terms, inner sums
 enum {
-    MS_BASE = 0,     // [3] long long: window base of each target (ints 0..5)
-    MS_WIDTH = 8,    // [3]
-    MS_OBASE = 12,   // [3] long long: outer-terms base (ints 12..17)
-    MS_OWIDTH = 20,  // [3]
-    MS_IBASE = 24,   // [3] long long: inner-terms base (ints 24..29)
-    MS_IWIDTH = 32,  // [3]
-    MS_NTERM = 36,   // number of outer terms
-    MS_ERR_A = 37,   // closer: stop flag set before barrier #1 (read by the whole cluster)
-    MS_ERR_C = 38,   // closer: stop flag set before barrier #3
-    MS_PSCAL = 40,   // [3][2] parameter sigma, R, b: single non-zero limb index (or -1), value
-    MS_UNITS = 48,   // unit bookkeeping
-    MS_HE = 52,      // [3] Horner exponents
-    MS_HF = 56,      // [3] Horner flags
-    MS_RED = 64,     // [8 warps][6] long long reduction scratch: ints 64..159
-    MS_STATUS = 160, // CTA-uniform copy of the status word
-    MS_HERR = 161,   // Horner of this CTA failed
-    MISC_INTS = 256
+    BK_LO = 0,      // long long (2 ints)
+    BK_WIDTH = 2,
+    BK_NSIMPLE = 3,
+    BK_SIMPLE = 4,  // [2][4]: kind (1 lone, 2 scaled), neg, offset, component
+    BK_SV = 12,     // [2] scaled: the parameter's limb
+    BK_INNER = 14,  // offset of the inner sums (or -1)
+    BK_IWIDTH = 15,
+    BK_TERM = 16,   // [NTERM][4]: present, component of A, neg, d
+};
+
+// Geometry of the unit walk (host and device)
+struct Geo {
+    int L, Lp, P, P1, M, VW, R, WW, GW, N1;
+    __host__ __device__ Geo(int L_, int Lp_, int N, int Wcap)
+    {
+        L = L_;
+        Lp = Lp_;
+        P = Lp / W;
+        P1 = P + 1;
+        M = P1 * W;
+        VW = vwords(M);
+        R = PT / P1;
+        if (R < 1) R = 1;
+        WW = Wcap + 4 * W;
+        GW = 2 * M + 2;
+        N1 = N + 1;
+    }
+};
+
+struct PSmem {
+    int *expT, *flgT;  // [3][N+1]
+    int *misc;         // [MISC_INTS]
+    int *tinfo;        // [TB_MAX][TI] term info
+    long long *stage;  // [P1 (R + 3)][W+2] unit digit sums
+    long long *win;    // [2][WW] windows
+    uint32_t *dig;     // [WW] normalised digits
+    // workers
+    uint32_t *araw;    // [2][TB][Lp] first factors as loaded
+    uint32_t *cc;      // [2][TB][VW] second factors (cyclic, zero above Lp)
+    uint32_t *ash;     // [TB][VW] first factors shifted / complemented
+    // bracket CTAs (same bytes as the workers' part)
+    uint32_t *vA;      // [NA][VW]
+    uint32_t *vC;      // [NC][VW]
+    uint32_t *raw;     // [3][Lp] limbs of the current coefficient; [2] also Horner's h
+    uint32_t *newc;    // [Lp] this CTA's newest number
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline void psizes(int Lp, int Wcap, int &AV, int &CV, int &M, int &wsz)
-{
-    M = Lp + W;
-    AV = phys(Lp - 1) + 2;
-    CV = phys(M - 1) + 2;
-    wsz = wsize(Wcap);
-}
-
-__host__ __device__ inline size_t pipe_layout(int Lp, int N, int Wcap, int tb, int umax, PSmem *S,
+__host__ __device__ inline size_t pipe_layout(const Geo &G, int N, int TB, PSmem *S,
                                               unsigned char *base)
 {
-    int AV, CV, M, wsz;
-    psizes(Lp, Wcap, AV, CV, M, wsz);
     size_t o = 0;
-    auto take = [&](size_t bytes) {
+    auto take = [&](size_t bytes) -> unsigned char * {
         size_t at = o;
         o = al16(o + bytes);
         return base ? base + at : nullptr;
@@ -109,105 +137,41 @@ __host__ __device__ inline size_t pipe_layout(int Lp, int N, int Wcap, int tb, i
     if (S) S->expT = (int *)p;
     p = take(sizeof(int) * 3 * (N + 1));
     if (S) S->flgT = (int *)p;
-    p = take(sizeof(int) * 4 * (tb > 64 ? tb : 64));
-    if (S) S->tinfo = (int *)p;
     p = take(sizeof(int) * MISC_INTS);
     if (S) S->misc = (int *)p;
-    const size_t u0 = o;
-    // closer part
-    p = take(sizeof(long long) * 3 * wsz);
-    if (S) S->win = (long long *)p;
-    p = take(sizeof(long long) * 3 * wsz);
-    if (S) S->comb = (long long *)p;
-    p = take(sizeof(uint32_t) * 3 * Wcap);
-    if (S) S->dig = (uint32_t *)p;
-    p = take(sizeof(uint32_t) * 3 * Lp);
-    if (S) S->newc = (uint32_t *)p;
-    p = take(sizeof(uint32_t) * (size_t)(NA * AV + NC * CV));
-    if (S) S->vec = (uint32_t *)p;
-    p = take(sizeof(long long) * 2 * (W + 2) * (size_t)(HU + 1));
-    if (S) S->hstage = (long long *)p;
-    const size_t closer_end = o;
-    // worker part, over the same bytes
-    o = u0;
-    p = take(sizeof(uint32_t) * (size_t)tb * (AV + CV));
-    if (S) S->wvec = (uint32_t *)p;
-    p = take(sizeof(long long) * 2 * (W + 2) * (size_t)(umax + 1));
+    p = take(sizeof(int) * TB_MAX * TI);
+    if (S) S->tinfo = (int *)p;
+    p = take(sizeof(long long) * (size_t)G.P1 * (G.R + 3) * (W + 2));
     if (S) S->stage = (long long *)p;
-    p = take(sizeof(long long) * 2 * wsz);
-    if (S) S->wwin = (long long *)p;
-    if (closer_end > o) o = closer_end;
-    if (S) {
-        S->AV = AV;
-        S->CV = CV;
-        S->M = M;
-        S->wsz = wsz;
-    }
+    p = take(sizeof(long long) * 2 * (size_t)G.WW);
+    if (S) S->win = (long long *)p;
+    p = take(sizeof(uint32_t) * (size_t)G.WW);
+    if (S) S->dig = (uint32_t *)p;
+    const size_t u0 = o;
+    p = take(sizeof(uint32_t) * 2 * (size_t)TB * G.Lp);
+    if (S) S->araw = (uint32_t *)p;
+    p = take(sizeof(uint32_t) * 2 * (size_t)TB * G.VW);
+    if (S) S->cc = (uint32_t *)p;
+    p = take(sizeof(uint32_t) * (size_t)TB * G.VW);
+    if (S) S->ash = (uint32_t *)p;
+    const size_t worker_end = o;
+    o = u0;
+    p = take(sizeof(uint32_t) * NA * (size_t)G.VW);
+    if (S) S->vA = (uint32_t *)p;
+    p = take(sizeof(uint32_t) * NC * (size_t)G.VW);
+    if (S) S->vC = (uint32_t *)p;
+    p = take(sizeof(uint32_t) * 3 * (size_t)G.Lp);
+    if (S) S->raw = (uint32_t *)p;
+    p = take(sizeof(uint32_t) * (size_t)G.Lp);
+    if (S) S->newc = (uint32_t *)p;
+    if (worker_end > o) o = worker_end;
     return o;
 }
 
 __device__ __forceinline__ long long &ll_at(int *misc, int slot) { return ((long long *)(misc + slot))[0]; }
 
-// --------------------------------------------------------------- small helpers
-
-__device__ __forceinline__ long long warp_min_ll(long long v)
-{
-    for (int o = 16; o; o >>= 1) {
-        long long w = __shfl_xor_sync(FULL, v, o);
-        v = w < v ? w : v;
-    }
-    return v;
-}
-__device__ __forceinline__ long long warp_max_ll(long long v)
-{
-    for (int o = 16; o; o >>= 1) {
-        long long w = __shfl_xor_sync(FULL, v, o);
-        v = w > v ? w : v;
-    }
-    return v;
-}
-
-// block min/max of lo[t], hi[t] for t < 3 -> misc[base_slot + 2t] (ll), misc[width_slot + t];
-// width > Wcap sets the status word (ERANGE) and width 0
-__device__ void block_window(PSmem &S, const KArgs &a, long long lo[3], long long hi[3],
-                             int base_slot, int width_slot)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    long long *red = (long long *)(S.misc + MS_RED);
-    for (int t = 0; t < 3; t++) {
-        long long l = warp_min_ll(lo[t]), h = warp_max_ll(hi[t]);
-        if (lane == 0) {
-            red[warp * 6 + t] = l;
-            red[warp * 6 + 3 + t] = h;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < 3) {
-        const int t = threadIdx.x;
-        long long l = red[t], h = red[3 + t];
-        for (int w = 1; w < NT / 32; w++) {
-            l = min(l, red[w * 6 + t]);
-            h = max(h, red[w * 6 + 3 + t]);
-        }
-        int width = 0;
-        if (h > l) {
-            if (h - l > a.Wcap) {
-                atomicCAS(a.status, 0, DEV_ERANGE);
-                S.misc[MS_STATUS] = DEV_ERANGE;
-            } else {
-                width = (int)(h - l);
-            }
-        }
-        ((long long *)(S.misc + base_slot))[t] = (h > l) ? l : 0;
-        S.misc[width_slot + t] = width;
-    }
-    __syncthreads();
-}
-
-// Per-phase cycle counters of thread 0 of the closer's CTA 0 and of the last
+// Per-phase cycle counters of thread 0 of one closer CTA and of the last
 // worker, accumulated in shared memory and written out at the end.
-constexpr int MS_PROF = 192;  // [PROF_SLOTS] long long: ints 192..223
-
 struct Prof {
     long long *p;
     long long t;
@@ -230,8 +194,8 @@ struct Prof {
     }
 };
 
-// bounded wait until *flag >= target (thread 0); status checked on the way.
-// Returns false (CTA-uniform) when the launch must stop.
+// bounded wait until *flag >= target (thread 0), the status word checked on
+// the way.  Returns false (CTA-uniform) when the launch must stop.
 __device__ bool wait_geq(PSmem &S, const KArgs &a, const unsigned *flag, unsigned target)
 {
     if (threadIdx.x == 0) {
@@ -256,113 +220,306 @@ __device__ bool wait_geq(PSmem &S, const KArgs &a, const unsigned *flag, unsigne
     return S.misc[MS_STATUS] == 0;
 }
 
-// --------------------------------------------------------------- workers
+// ------------------------------------------------------------------ unit products
 
-// inner Cauchy terms of index m: t < m-1 -> Y: -alpha_a gamma_{m-a}, a = t+1;
-// otherwise Z: +alpha_a beta_{m-a}, a = t-(m-1)+1
-__device__ __forceinline__ void inner_term(int m, int t, int &tg, int &neg, int &acomp, int &aidx,
-                                           int &bcomp, int &bidx)
+// Sum over the n terms in slots [s0, s0+n) of A'_s * C_s (A'_s = Abase + s VW,
+// C_s = Cbase + s VW), exact, added into win[coff + c], c < 2M+2.  With `tinfo`, slots flagged negative hold the
+// complement of the shifted first factor over its Lp limbs, and the
+// complement's correction
+// (+C 2^(32 d) + ~C 2^(32 (d+Lp)) + 2^(32 (d+Lp)) - 2^(32 (d+2Lp))) is added
+// as well.  neg_all negates the whole sum.  Every thread of the CTA calls
+// this; it starts and ends with __syncthreads.
+__device__ void group_products(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
+                               int n, const int *tinfo, bool neg_all, long long *stage,
+                               long long *win, int coff)
 {
-    if (t < m - 1) {
-        tg = 1;
-        neg = 1;
-        acomp = 0;
-        aidx = t + 1;
-        bcomp = 2;
-        bidx = m - aidx;
-    } else {
-        tg = 2;
-        neg = 0;
-        acomp = 0;
-        aidx = t - (m - 1) + 1;
-        bcomp = 1;
-        bidx = m - aidx;
-    }
-}
-
-// window placement of the inner terms of index m (targets 1 = Y, 2 = Z)
-__device__ void inner_windows(PSmem &S, const KArgs &a, int m, int base_slot, int width_slot)
-{
-    const int N1 = a.N + 1;
-    long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
-    long long hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
-    const int T = 2 * (m - 1);
-    for (int t = threadIdx.x; t < T; t += NT) {
-        int tg, neg, ac, ai, bc, bi;
-        inner_term(m, t, tg, neg, ac, ai, bc, bi);
-        int fa = S.flgT[ac * N1 + ai], fb = S.flgT[bc * N1 + bi];
-        if (!(fa & F_NZ) || !(fb & F_NZ)) continue;
-        long long lp = (long long)S.expT[ac * N1 + ai] + S.expT[bc * N1 + bi] - 2LL * a.L;
-        lo[tg] = min(lo[tg], lp);
-        hi[tg] = max(hi[tg], lp + 2LL * a.Lp + 2);
-    }
-    block_window(S, a, lo, hi, base_slot, width_slot);
-}
-
-struct Chunking {
-    int H;   // chunks per column pair
-    int CL;  // steps per chunk (multiple of W)
-};
-
-__device__ __forceinline__ Chunking chunking(long long pairs, long long threads, int P)
-{
-    // enough units that every thread has about one and a half
-    long long want = (3 * threads + 2 * pairs - 1) / (2 * pairs);
-    int H = (int)min((long long)(P + 1), max(1LL, want));
-    Chunking c;
-    c.CL = ((P + 1 + H - 1) / H) * W;
-    c.H = ((P + 1) * W + c.CL - 1) / c.CL;
-    return c;
-}
-
-// Chunks per column pair for nt terms on NT threads: the H in 1..4 whose
-// units fill the threads' rounds best (a unit per thread per round), a little
-// biased toward fewer, longer units; units of one batch must fit `umax`.
-__device__ __forceinline__ Chunking worker_chunking(int nt, int P, int umax)
-{
-    int best = 1;
-    double best_score = -1.0;
-    for (int H = 1; H <= 4; H++) {
-        const int CL = ((P + 1 + H - 1) / H) * W;
-        const int He = ((P + 1) * W + CL - 1) / CL;
-        const long long U = (long long)nt * P * He;
-        if (H > 1 && U > umax) break;
-        const double x = (double)U / NT;
-        const double rounds = ceil(x);
-        const double score = x / rounds - 0.03 * (He - 1);
-        if (score > best_score + 1e-9) {
-            best_score = score;
-            best = H;
+    const int tid = threadIdx.x;
+    uint32_t a0[W], a1[W], a2[W], x0[W], x1[W], x2[W];
+#pragma unroll
+    for (int k = 0; k < W; k++) a0[k] = a1[k] = a2[k] = x0[k] = x1[k] = x2[k] = 0u;
+    int key = -1;
+    bool strad = false, b1only = false;  // share straddles the block switch / lies in block 1
+    // threads per unit
+    const int Re = G.R;
+    __syncthreads();
+    if (tid < G.P1 * Re && n > 0) {
+        const int q = tid / Re, r = tid - q * Re;
+        key = q;
+        const int I = n * G.P1;
+        const int i0 = I * r / Re, i1 = I * (r + 1) / Re;
+        const int nA = n * (q + 1);  // block-0 items: chunks 0..q of every term
+        strad = i0 < nA && i1 > nA;
+        b1only = i0 >= nA;
+        const int lenB = G.P - q;    // block-1 chunks per term
+        int t, j, ph;
+        if (i0 < nA) {
+            ph = 0;
+            t = i0 / (q + 1);
+            j = i0 - t * (q + 1);
+        } else {
+            ph = 1;
+            const int ib = i0 - nA;
+            t = ib / lenB;
+            j = q + 1 + ib - t * lenB;
+        }
+        const uint32_t *Ap = Abase + (size_t)(s0 + t) * G.VW, *Cp = Cbase + (size_t)(s0 + t) * G.VW;
+        for (int it = i0; it < i1; it++) {
+            const bool sw = (it == nA);  // first block-1 item: keep the block-0 sums
+            if (__any_sync(__activemask(), sw)) {
+#pragma unroll
+                for (int k = 0; k < W; k++) {
+                    x0[k] = sw ? a0[k] : x0[k];
+                    x1[k] = sw ? a1[k] : x1[k];
+                    x2[k] = sw ? a2[k] : x2[k];
+                }
+            }
+            int gc0 = q - j;
+            if (gc0 < 0) gc0 += G.P1;
+            const int gc1 = gc0 == 0 ? G.P : gc0 - 1;
+            chunk_mac(Ap, Cp, j, gc0, gc1, a0, a1, a2);
+            j++;
+            bool next = false;
+            if (ph == 0) {
+                if (j > q) {
+                    j = 0;
+                    next = true;
+                    if (++t == n) {
+                        ph = 1;
+                        t = 0;
+                        j = q + 1;
+                    }
+                }
+            } else if (j == G.P1) {
+                j = q + 1;
+                t++;
+                next = true;
+            }
+            if (next) {
+                Ap = Abase + (size_t)(s0 + t) * G.VW;
+                Cp = Cbase + (size_t)(s0 + t) * G.VW;
+            }
+        }
+        if (i1 <= nA) {
+#pragma unroll
+            for (int k = 0; k < W; k++) {
+                x0[k] = a0[k];
+                x1[k] = a1[k];
+                x2[k] = a2[k];
+            }
         }
     }
-    Chunking c;
-    c.CL = ((P + 1 + best - 1) / best) * W;
-    c.H = ((P + 1) * W + c.CL - 1) / c.CL;
-    return c;
+    // Each thread's share lies in block 0, in block 1, or straddles the switch
+    // once (at most one thread per unit).  A thread stores the digits of its
+    // block (block 0 when straddling, whose block-1 digits go to a slot of
+    // the unit), the shares are summed per (unit, block, digit), and one
+    // thread per window column adds the column.
+    constexpr int ND = W + 2;
+    long long *st0 = stage;                                // [P1 Re][ND]
+    long long *st1 = st0 + (size_t)G.P1 * G.R * ND;        // [P1][ND] straddlers' block 1
+    long long *tot = st1 + (size_t)G.P1 * ND;              // [P1][2][ND]
+    if (key >= 0) {
+        long long *dst = st0 + (size_t)tid * ND;
+        long long *dst1 = st1 + (size_t)key * ND;
+#pragma unroll
+        for (int t = 0; t < ND; t++) {
+            const long long bx = col_digit(x0, x1, x2, t), ba = col_digit(a0, a1, a2, t);
+            dst[t] = b1only ? ba : bx;
+            if (strad) dst1[t] = ba - bx;
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < G.P1 * 2 * ND; e += PT) {
+        const int u = e / (2 * ND), rem = e - u * 2 * ND, b = rem / ND, t = rem - b * ND;
+        const int I = n * G.P1, nAu = n * (u + 1);
+        // rs: the last thread whose share starts at or below the switch
+        int rs = Re;
+        bool sS = false;
+        if (nAu < I) {
+            rs = ((nAu + 1) * Re + I - 1) / I - 1;
+            sS = (I * rs / Re) < nAu;
+        }
+        const long long *src = st0 + (size_t)u * Re * ND + t;
+        long long sum = 0;
+        if (b == 0) {
+            const int r1 = sS ? rs + 1 : rs;
+            for (int r = 0; r < r1; r++) sum += src[(size_t)r * ND];
+        } else if (rs < Re) {
+            for (int r = sS ? rs + 1 : rs; r < Re; r++) sum += src[(size_t)r * ND];
+            if (sS) sum += st1[(size_t)u * ND + t];
+        }
+        tot[e] = sum;
+    }
+    __syncthreads();
+    for (int c = tid; c < G.GW; c += PT) {
+        long long s = 0;
+        if (n > 0) {
+            if (c < G.M + 2) {
+                const int u = c / W;
+                if (u <= G.P) s += tot[(u * 2) * ND + c - u * W];
+                if (u >= 1 && c - (u - 1) * W < ND) s += tot[((u - 1) * 2) * ND + c - (u - 1) * W];
+            }
+            const int c1 = c - G.M;
+            if (c1 >= 0) {
+                const int u = c1 / W;
+                if (u <= G.P) s += tot[(u * 2 + 1) * ND + c1 - u * W];
+                if (u >= 1 && c1 - (u - 1) * W < ND) s += tot[((u - 1) * 2 + 1) * ND + c1 - (u - 1) * W];
+            }
+        }
+        if (tinfo) {
+            // complement corrections of the negative terms
+            for (int sl = s0; sl < s0 + n; sl++) {
+                const int *ti = tinfo + sl * TI;
+                if (!ti[1]) continue;
+                const int y = c - ti[2];
+                const uint32_t *Cs = Cbase + (size_t)sl * G.VW;
+                if (y >= 0 && y < G.Lp) s += Cs[gpos(y)];
+                else if (y >= G.Lp && y < 2 * G.Lp) s += (uint32_t)~Cs[gpos(y - G.Lp)];
+                if (y == G.Lp) s += 1;
+                if (y == 2 * G.Lp) s -= 1;
+            }
+        }
+        if (s) win[coff + c] += neg_all ? -s : s;
+    }
+    __syncthreads();
 }
 
-// Workers: the inner Cauchy sums of index m (pairs a = 1..m-1, which need
-// coefficients up to m-1 only).  Each worker takes a contiguous range of
-// whole products; inside a CTA the units are ordered (chunk, pair, product),
-// so a warp holds few distinct column pairs.  Units write their column
-// digits to a private staging slot; a column reduction then adds each
-// window column once into the global accumulator set.
-__device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa)
+// ------------------------------------------------------------------ workers
+
+// term t of index m: Y (tg 0) for t < m-1 with a = t+1 and second factor
+// gamma_{m-a}; Z (tg 1) after, a = t-(m-1)+1, beta_{m-a}.  Rows of coefL.
+__device__ __forceinline__ void inner_term(int m, int t, int N1, int &tg, int &arow, int &crow,
+                                           int &a)
 {
-    const int N1 = a.N + 1, Lp = a.Lp, P = a.P;
-    const int nw = gridDim.x - CP_C;
-    const int w = blockIdx.x - CP_C;
-    const int SL = S.AV + S.CV;
-    const int umax = pa.umax;
-    const int ustride = umax + 1;
-    const bool prof_on = (blockIdx.x == gridDim.x - 1);
-    // C padding of every slot stays zero; windows start empty
-    for (int e = threadIdx.x; e < a.tb * S.M; e += NT) {
-        int slot = e / S.M, x = e - slot * S.M;
-        if (x >= Lp) S.wvec[(size_t)slot * SL + S.AV + phys(x)] = 0u;
+    if (t < m - 1) {
+        tg = 0;
+        a = t + 1;
+        crow = 2 * N1 + (m - a);
+    } else {
+        tg = 1;
+        a = t - (m - 1) + 1;
+        crow = N1 + (m - a);
     }
-    for (int e = threadIdx.x; e < 2 * S.wsz; e += NT) S.wwin[e] = 0;
+    arow = a;
+}
+
+// Window of the inner sums of index m (targets Y, Z): the pairs a = 2..m-2
+// come from the table the closer filled one period earlier, the two extreme
+// pairs (a = 1 and a = m-1, which involve coefficient m-1) are added here.
+__device__ void inner_window(const KArgs &a, const long long mid[4], const int *expT,
+                             const int *flgT, int m, long long lo[2], long long hi[2])
+{
+    const int N1 = a.N + 1;
+    lo[0] = mid[0];
+    hi[0] = mid[1];
+    lo[1] = mid[2];
+    hi[1] = mid[3];
+    const int ends[2] = {1, m - 1};
+    for (int e = 0; e < (m - 1 == 1 ? 1 : 2); e++) {
+        const int aa = ends[e];
+        for (int tg = 0; tg < 2; tg++) {
+            const int crow = (tg == 0 ? 2 : 1) * N1 + (m - aa);
+            if (!(flgT[aa] & F_NZ) || !(flgT[crow] & F_NZ)) continue;
+            const long long lp = (long long)expT[aa] + expT[crow] - 2LL * a.L;
+            lo[tg] = min(lo[tg], lp);
+            hi[tg] = max(hi[tg], lp + 2LL * a.Lp + 2);
+        }
+    }
+}
+
+// cp.async the factors of slots [0, nb) of the batch (m, tb0) into buffer
+// buf, 16 bytes a copy (the first factor plain, the second into its cyclic
+// layout: a group of W limbs is two 16-byte pieces); mode 0 every slot, 1 all
+// but the late ones, 2 only the late ones (late: a factor is coefficient m-1)
+__device__ void issue_loads(PSmem &S, const KArgs &a, const Geo &G, int TB, int buf, int m, int tb0,
+                            int nb, int mode)
+{
+    const int Lp = G.Lp, q4 = Lp / 4, per = 2 * q4;
+    for (int e = threadIdx.x; e < nb * per; e += PT) {
+        const int sl = e / per, r = e - sl * per;
+        int tg, arow, crow, aa;
+        inner_term(m, tb0 + sl, G.N1, tg, arow, crow, aa);
+        const bool late = (aa == m - 1) || (aa == 1);
+        if ((mode == 1 && late) || (mode == 2 && !late)) continue;
+        if (r < q4) {
+            cp_async16(S.araw + ((size_t)buf * TB + sl) * Lp + 4 * r, a.coefL + (size_t)arow * Lp + 4 * r);
+        } else {
+            const int x4 = r - q4, g = x4 >> 1, h = x4 & 1;
+            cp_async16(S.cc + ((size_t)buf * TB + sl) * G.VW + g * GS + 4 * h,
+                       a.coefL + (size_t)crow * Lp + 8 * g + 4 * h);
+        }
+    }
+}
+
+// term info (warp 0), staged first factors and term groups of the batch in
+// buffer buf
+__device__ void prepare_batch(PSmem &S, const KArgs &a, const Geo &G, int TB, int buf, int m,
+                              int tb0, int nb)
+{
+    (void)a;
+    if (threadIdx.x < 32) {
+        const long long *wlo = (const long long *)(S.misc + MS_WLO);
+        const int lane = threadIdx.x;
+        int key = -1;
+        if (lane < nb) {
+            int tg, arow, crow, aa;
+            inner_term(m, tb0 + lane, G.N1, tg, arow, crow, aa);
+            const int fa = S.flgT[arow], fc = S.flgT[crow];
+            const int neg = (tg == 0 ? 1 : 0) ^ (((fa ^ fc) & F_NEG) ? 1 : 0);
+            int d = 0;
+            if ((fa & F_NZ) && (fc & F_NZ)) {
+                d = (int)((long long)S.expT[arow] + S.expT[crow] - 2LL * G.L - wlo[tg]);
+                key = (tg << 20) | (d >> 3);
+            }
+            int *ti = S.tinfo + lane * TI;
+            ti[0] = tg;
+            ti[1] = neg;
+            ti[2] = d & 7;
+            ti[3] = d >> 3;
+            ti[4] = key;
+        }
+        const int kprev = __shfl_up_sync(FULL, key, 1), knext = __shfl_down_sync(FULL, key, 1);
+        const bool st = key >= 0 && (lane == 0 || kprev != key);
+        const bool en = key >= 0 && (lane == 31 || knext != key);
+        const unsigned Sm = __ballot_sync(FULL, st), Em = __ballot_sync(FULL, en);
+        const unsigned lt = (1u << lane) - 1u;
+        if (st) S.misc[MS_RUN + __popc(Sm & lt)] = lane;
+        if (en) S.misc[MS_RUNE + __popc(Em & lt)] = lane + 1;
+        if (lane == 0) S.misc[MS_NRUN] = __popc(Sm);
+    }
     __syncthreads();
+    for (int sl = 0; sl < nb; sl++) {
+        const int *ti = S.tinfo + sl * TI;
+        if (ti[4] < 0) continue;
+        const int dl = ti[2];
+        const uint32_t inv = ti[1] ? 0xffffffffu : 0u;
+        const uint32_t *src = S.araw + ((size_t)buf * TB + sl) * G.Lp;
+        uint32_t *dst = S.ash + (size_t)sl * G.VW;
+        for (int x = threadIdx.x; x < G.M; x += PT) {
+            const int y = x - dl;
+            dst[gpos(x)] = (y >= 0 && y < G.Lp) ? (src[y] ^ inv) : 0u;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &G)
+{
+    const int N1 = G.N1, Lp = G.Lp, TB = pa.tb;
+    const int nw = gridDim.x - NCL;
+    const int w = blockIdx.x - NCL;
+    const bool prof_on = (blockIdx.x == gridDim.x - 1);
+    // zero padding of the second factors stays zero; windows start empty
+    for (int e = threadIdx.x; e < 2 * TB * G.M; e += PT) {
+        const int s = e / G.M, x = e - s * G.M;
+        if (x >= Lp) S.cc[(size_t)s * G.VW + gpos(x)] = 0u;
+    }
+    for (int e = threadIdx.x; e < 2 * G.WW; e += PT) S.win[e] = 0;
+    __syncthreads();
+    int bcount = 0;        // batches so far (buffer = parity)
+    bool pf = false;       // the batch at (pf_step, pf_m, pf_tb0) is loading
+    bool pf_late = false;  // ... without its late terms
+    long long pf_step = -1;
+    int pf_m = -1, pf_tb0 = -1;
     for (long long step = 0; step < a.nsteps; step++) {
         for (int m = 0; m < a.N; m++) {
             const long long g = step * a.N + m;
@@ -372,144 +529,99 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa)
                 continue;
             }
             Prof pr(a, prof_on, S.misc);
-            if (!wait_geq(S, a, pa.pub, (unsigned)(step * N1 + m))) return;
+            if (!wait_geq(S, a, pa.pub, (unsigned)(3 * (step * N1 + m)))) {
+                cp_async_wait<0>();
+                return;
+            }
             pr.mark(PR_BARRIER);
-            // exponent / flag of coefficient m-1 (published with it)
             if (threadIdx.x < 3) {
                 const int idx = threadIdx.x * N1 + m - 1;
                 S.expT[idx] = __ldcg(&a.coefE[idx]);
                 S.flgT[idx] = __ldcg(&a.coefF[idx]);
             }
             __syncthreads();
-            inner_windows(S, a, m, MS_IBASE, MS_IWIDTH);
+            if (threadIdx.x == 0) {
+                long long lo[2], hi[2], mid[4];
+                for (int k = 0; k < 4; k++) mid[k] = __ldcg(&pa.imid[(size_t)set * 4 + k]);
+                inner_window(a, mid, S.expT, S.flgT, m, lo, hi);
+                for (int tg = 0; tg < 2; tg++) {
+                    int width = 0;
+                    if (hi[tg] > lo[tg]) {
+                        if (hi[tg] - lo[tg] > a.Wcap) {
+                            atomicCAS(a.status, 0, DEV_ERANGE);
+                            S.misc[MS_STATUS] = DEV_ERANGE;
+                        } else {
+                            width = (int)(hi[tg] - lo[tg]);
+                        }
+                    }
+                    ll_at(S.misc, MS_WLO + 2 * tg) = hi[tg] > lo[tg] ? lo[tg] : 0;
+                    S.misc[MS_WID + tg] = width;
+                }
+            }
+            __syncthreads();
             pr.mark(PR_PLACE);
-            if (S.misc[MS_STATUS] != 0) return;  // window too wide: status set, stop
+            if (S.misc[MS_STATUS] != 0) {
+                cp_async_wait<0>();
+                return;
+            }
             const int T = 2 * (m - 1);
             const int tA = (int)((long long)T * w / nw), tB = (int)((long long)T * (w + 1) / nw);
-            long long *gset = pa.gin + (size_t)set * 2 * a.Wcap;
-            const Chunking ck = worker_chunking(tB - tA, P, umax);
-            const int per_term = ck.H * P;
-            const int tbw = max(1, min(a.tb, umax / per_term));
-            for (int tb0 = tA; tb0 < tB; tb0 += tbw) {
-                const int nt = min(tbw, tB - tb0);
-                const int U = nt * per_term;
-                // per-slot term info and source rows
-                if (threadIdx.x < nt) {
-                    int tg, neg, ac, ai, bc, bi;
-                    inner_term(m, tb0 + threadIdx.x, tg, neg, ac, ai, bc, bi);
-                    int fa = S.flgT[ac * N1 + ai], fb = S.flgT[bc * N1 + bi];
-                    bool skip = !(fa & F_NZ) || !(fb & F_NZ);
-                    int off = 0;
-                    if (!skip) {
-                        long long lp = (long long)S.expT[ac * N1 + ai] + S.expT[bc * N1 + bi] - 2LL * a.L;
-                        off = (int)(lp - ((long long *)(S.misc + MS_IBASE))[tg]);
-                    }
-                    int sgn = neg ^ (fa & F_NEG) ^ (fb & F_NEG);
-                    S.tinfo[4 * threadIdx.x] = off;
-                    S.tinfo[4 * threadIdx.x + 1] = (skip ? 4 : 0) | (sgn ? 1 : 0) | (tg << 4);
-                    S.tinfo[4 * threadIdx.x + 2] = ac * N1 + ai;
-                    S.tinfo[4 * threadIdx.x + 3] = bc * N1 + bi;
-                }
-                __syncthreads();
-                // stage alpha_a (A layout) and gamma/beta_{m-a} (C layout): all
-                // loads of a thread are issued before its stores
-                {
-                    const int total = nt * 2 * Lp;
-                    for (int e0 = 0; e0 < total; e0 += NT * 8) {
-                        uint32_t v[8];
-                        int dst[8];
-#pragma unroll
-                        for (int k = 0; k < 8; k++) {
-                            const int e = e0 + k * NT + threadIdx.x;
-                            dst[k] = -1;
-                            v[k] = 0u;
-                            if (e < total) {
-                                const int slot = e / (2 * Lp), r = e - slot * 2 * Lp;
-                                const int which = r >= Lp, x = r - which * Lp;
-                                const int row = S.tinfo[4 * slot + 2 + which];
-                                v[k] = __ldcg(&a.coefL[(size_t)row * Lp + x]);
-                                dst[k] = slot * SL + (which ? S.AV : 0) + phys(x);
-                            }
-                        }
-#pragma unroll
-                        for (int k = 0; k < 8; k++)
-                            if (dst[k] >= 0) S.wvec[dst[k]] = v[k];
+            for (int tb0 = tA; tb0 < tB; tb0 += TB) {
+                const int nb = min(TB, tB - tb0);
+                const int buf = bcount & 1;
+                const bool was_pf = pf && pf_step == step && pf_m == m && pf_tb0 == tb0;
+                if (!was_pf) issue_loads(S, a, G, TB, buf, m, tb0, nb, 0);
+                else if (pf_late) issue_loads(S, a, G, TB, buf, m, tb0, nb, 2);
+                cp_async_commit();
+                // prefetch the next batch: the rest of this index, or the first
+                // batch of index m+1 without its late terms
+                pf = false;
+                if (tb0 + TB < tB) {
+                    pf = true;
+                    pf_late = false;
+                    pf_step = step;
+                    pf_m = m;
+                    pf_tb0 = tb0 + TB;
+                    issue_loads(S, a, G, TB, buf ^ 1, m, pf_tb0, min(TB, tB - pf_tb0), 0);
+                } else if (m + 1 < a.N) {
+                    const int T2 = 2 * m;
+                    const int tA2 = (int)((long long)T2 * w / nw), tB2 = (int)((long long)T2 * (w + 1) / nw);
+                    if (tB2 > tA2) {
+                        pf = true;
+                        pf_late = true;
+                        pf_step = step;
+                        pf_m = m + 1;
+                        pf_tb0 = tA2;
+                        issue_loads(S, a, G, TB, buf ^ 1, m + 1, tA2, min(TB, tB2 - tA2), 1);
                     }
                 }
+                cp_async_commit();
+                pr.mark(PR_X1);
+                cp_async_wait<1>();
                 __syncthreads();
                 pr.mark(PR_STAGE);
-                // units (chunk h, pair q, product tl): u = (h P + q) nt + tl
-                for (int u = threadIdx.x; u < U; u += NT) {
-                    const int tl = u % nt;
-                    const int hq = u / nt;
-                    const int h = hq / P, q = hq - h * P;
-                    const int fl = S.tinfo[4 * tl + 1];
-                    long long v1[W + 2], v2[W + 2];
-                    if (fl & 4) {
-#pragma unroll
-                        for (int t = 0; t < W + 2; t++) v1[t] = v2[t] = 0;
-                    } else {
-                        const int s0 = h * ck.CL, s1 = min(s0 + ck.CL, (P + 1) * W);
-                        const uint32_t *Av = S.wvec + (size_t)tl * SL;
-                        mac_unit_vals<false>(Av, Av + S.AV, q, s0, s1, Lp, S.M, v1, v2);
-                        if (fl & 1) {
-#pragma unroll
-                            for (int t = 0; t < W + 2; t++) {
-                                v1[t] = -v1[t];
-                                v2[t] = -v2[t];
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int t = 0; t < W + 2; t++) {
-                        S.stage[(size_t)t * ustride + u] = v1[t];
-                        S.stage[(size_t)(W + 2 + t) * ustride + u] = v2[t];
-                    }
-                }
-                __syncthreads();
-                pr.mark(PR_MAC);
-                // reduction: every (pair q, block b, digit k) sums the chunks
-                // of each product with the same target and offset and adds the
-                // sum at column off + b Lp + q W + k of the shared window
-                for (int cb = threadIdx.x; cb < P * 2 * (W + 2); cb += NT) {
-                    const int q = cb / (2 * (W + 2)), r = cb - q * 2 * (W + 2);
-                    const int b = r / (W + 2), k = r - b * (W + 2);
-                    const long long *st = S.stage + (size_t)r * ustride + (size_t)q * nt;
-                    long long sum = 0;
-                    int cur_tg = -1, cur_off = 0;
-                    for (int tl = 0; tl < nt; tl++) {
-                        const int fl = S.tinfo[4 * tl + 1];
-                        if (fl & 4) continue;
-                        const int tg = (fl >> 4) & 3, off = S.tinfo[4 * tl];
-                        if (tg != cur_tg || off != cur_off) {
-                            if (sum)
-                                atomicAdd((unsigned long long *)&S.wwin[(size_t)(cur_tg - 1) * S.wsz +
-                                                                      wphys(cur_off + b * Lp + q * W + k)],
-                                          (unsigned long long)sum);
-                            sum = 0;
-                            cur_tg = tg;
-                            cur_off = off;
-                        }
-                        for (int h = 0; h < ck.H; h++) sum += st[(size_t)h * P * nt + tl];
-                    }
-                    if (sum)
-                        atomicAdd((unsigned long long *)&S.wwin[(size_t)(cur_tg - 1) * S.wsz +
-                                                              wphys(cur_off + b * Lp + q * W + k)],
-                                  (unsigned long long)sum);
-                }
-                __syncthreads();
+                prepare_batch(S, a, G, TB, buf, m, tb0, nb);
                 pr.mark(PR_FLUSH);
+                const int nrun = S.misc[MS_NRUN];
+                for (int rr = 0; rr < nrun; rr++) {
+                    const int rs = S.misc[MS_RUN + rr], re = S.misc[MS_RUNE + rr];
+                    const int *ti = S.tinfo + rs * TI;
+                    group_products(G, S.ash, S.cc + (size_t)buf * TB * G.VW, rs, re - rs, S.tinfo,
+                                   false, S.stage, S.win + (size_t)ti[0] * G.WW, ti[3] * W);
+                }
+                pr.mark(PR_MAC);
+                bcount++;
             }
-            // the shared windows into the global set
-            for (int tg = 1; tg <= 2; tg++) {
-                const int wd = S.misc[MS_IWIDTH + tg];
-                long long *src = S.wwin + (size_t)(tg - 1) * S.wsz;
-                for (int c = threadIdx.x; c < wd; c += NT) {
-                    const long long v = src[wphys(c)];
+            // the CTA's windows into the global set
+            for (int tg = 0; tg < 2; tg++) {
+                const int wd = S.misc[MS_WID + tg];
+                long long *src = S.win + (size_t)tg * G.WW;
+                long long *dst = pa.gin + ((size_t)set * 2 + tg) * a.Wcap;
+                for (int c = threadIdx.x; c < wd; c += PT) {
+                    const long long v = src[c];
                     if (v) {
-                        atomicAdd((unsigned long long *)&gset[(size_t)(tg - 1) * a.Wcap + c],
-                                  (unsigned long long)v);
-                        src[wphys(c)] = 0;
+                        atomicAdd((unsigned long long *)&dst[c], (unsigned long long)v);
+                        src[c] = 0;
                     }
                 }
             }
@@ -518,303 +630,254 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa)
                 __threadfence();
                 atomicAdd(&pa.done[set], 1u);
             }
+            pr.mark(PR_CLOSE);
         }
     }
+    cp_async_wait<0>();
 }
 
-// --------------------------------------------------------------- closer (cluster)
+// ------------------------------------------------------------------ bracket CTAs
 
-struct OTerm {
-    int kind;   // 0 dense product, 1 one-limb parameter times a number, 2 lone number
-    int tg, neg;
-    int aslot, bslot;  // A slot (product / scaled source / lone number), C slot (product)
-    long long lp;      // lowest limb position of the term
-    uint32_t v;        // one-limb multiplier
-};
-
-// The terms of Eq. (3)'s brackets at index m that involve coefficient m
-// (all of them for m = 0).  Operands are in the closer's slots.
-__device__ int outer_terms(PSmem &S, const KArgs &a, int m, OTerm *ot)
+// raw limbs -> operand slot (the zero padding above Lp is never written)
+__device__ __forceinline__ void to_slot(uint32_t *dst, const uint32_t *src, int Lp)
 {
-    const int N1 = a.N + 1;
-    const int eA0 = S.expT[0 * N1], fA0 = S.flgT[0 * N1];
-    const int eB0 = S.expT[1 * N1], fB0 = S.flgT[1 * N1];
+    for (int x = threadIdx.x; x < Lp; x += PT) dst[gpos(x)] = src[x];
+}
+
+// Setup of bracket c at index m (thread 0): the simple parts (a lone number,
+// a number times a one-limb parameter), the product terms (a component of
+// coefficient m times the fixed number in C slot k) and the inner sums; the
+// window (base, width) and each part's offset in it; the term groups.
+// Returns false (status set) when the window is wider than Wcap.
+__device__ bool bracket_setup(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &G, int c, int m,
+                              int set)
+{
+    const int N1 = G.N1, L = G.L, Lp = G.Lp;
+    int *bk = S.misc + MS_BK;
+    const int eA = S.expT[m], fA = S.flgT[m];
+    const int eB = S.expT[N1 + m], fB = S.flgT[N1 + m];
+    const int eG = S.expT[2 * N1 + m], fG = S.flgT[2 * N1 + m];
+    const int eA0 = S.expT[0], fA0 = S.flgT[0];
+    const int eB0 = S.expT[N1], fB0 = S.flgT[N1];
     const int eG0 = S.expT[2 * N1], fG0 = S.flgT[2 * N1];
-    const int eAm = S.expT[0 * N1 + m], fAm = S.flgT[0 * N1 + m];
-    const int eBm = S.expT[1 * N1 + m], fBm = S.flgT[1 * N1 + m];
-    const int eGm = S.expT[2 * N1 + m], fGm = S.flgT[2 * N1 + m];
-    int n = 0;
-    auto prod = [&](int tg, int neg, int aslot, int ea, int fa, int bslot, int eb, int fb) {
-        if (!(fa & F_NZ) || !(fb & F_NZ)) return;
-        OTerm t;
-        t.kind = 0;
-        t.tg = tg;
-        t.neg = neg ^ (fa & F_NEG) ^ (fb & F_NEG);
-        t.aslot = aslot;
-        t.bslot = bslot;
-        t.lp = (long long)ea + eb - 2LL * a.L;
-        t.v = 0;
-        ot[n++] = t;
-    };
-    auto param = [&](int tg, int neg, int p, int aslot_p, int src_aslot, int src_cslot, int ec,
-                     int fc) {
+    int sk[2] = {0, 0}, sneg[2] = {0, 0}, scomp[2] = {0, 0};
+    uint32_t sv[2] = {0u, 0u};
+    long long slp[2] = {0, 0};
+    int tp[NTERM] = {0, 0, 0}, tcomp[NTERM] = {0, 0, 0}, tneg[NTERM] = {0, 0, 0};
+    long long tlp[NTERM] = {0, 0, 0};
+    int ns = 0;
+    // parameter p times component comp of coefficient m (exponent e, flags f)
+    auto param = [&](int p, int comp, int e, int f, int neg, int tslot) {
         const int pe = __ldg(&a.parE[p]), pf = __ldg(&a.parF[p]);
-        if (!(pf & F_NZ) || !(fc & F_NZ)) return;
+        if (!(pf & F_NZ) || !(f & F_NZ)) return;
+        const int nn = neg ^ (((pf ^ f) & F_NEG) ? 1 : 0);
         const int i0 = S.misc[MS_PSCAL + 2 * p];
-        if (i0 >= 0) {  // one non-zero limb v at index i0: v * c shifted
-            OTerm t;
-            t.kind = 1;
-            t.tg = tg;
-            t.neg = neg ^ (pf & F_NEG) ^ (fc & F_NEG);
-            t.aslot = src_aslot;
-            t.bslot = -1;
-            t.lp = (long long)pe - a.L + i0 + (long long)ec - a.L;
-            t.v = (uint32_t)S.misc[MS_PSCAL + 2 * p + 1];
-            ot[n++] = t;
+        if (i0 >= 0) {
+            sk[ns] = 2;
+            sneg[ns] = nn;
+            scomp[ns] = comp;
+            sv[ns] = (uint32_t)S.misc[MS_PSCAL + 2 * p + 1];
+            slp[ns] = (long long)pe - L + i0 + (long long)e - L;
+            ns++;
         } else {
-            prod(tg, neg, aslot_p, pe, pf, src_cslot, ec, fc);
+            tp[tslot] = 1;
+            tcomp[tslot] = comp;
+            tneg[tslot] = nn;
+            tlp[tslot] = (long long)pe + e - 2LL * L;
         }
     };
-    if (m == 0) {
-        prod(1, 1, A_ALPHA0, eA0, fA0, C_GAMMA0, eG0, fG0);
-        prod(2, 0, A_ALPHA0, eA0, fA0, C_BETA0, eB0, fB0);
+    // component comp of coefficient m times a fixed number (e0, f0)
+    auto term = [&](int tslot, int comp, int e, int f, int e0, int f0, int neg) {
+        if (!(f & F_NZ) || !(f0 & F_NZ)) return;
+        tp[tslot] = 1;
+        tcomp[tslot] = comp;
+        tneg[tslot] = neg ^ (((f ^ f0) & F_NEG) ? 1 : 0);
+        tlp[tslot] = (long long)e + e0 - 2LL * L;
+    };
+    if (c == 0) {
+        param(P_SIGMA, 1, eB, fB, 0, 0);  // + sigma beta_m   (C slot 0: sigma)
+        param(P_SIGMA, 0, eA, fA, 1, 1);  // - sigma alpha_m  (C slot 1: sigma)
+    } else if (c == 1) {
+        term(0, 0, eA, fA, eG0, fG0, 1);             // - alpha_m gamma_0  (C slot 0: gamma_0)
+        if (m > 0) term(1, 2, eG, fG, eA0, fA0, 1);  // - gamma_m alpha_0  (C slot 1: alpha_0)
+        param(P_R, 0, eA, fA, 0, 2);                  // + R alpha_m        (C slot 2: R)
+        if (fB & F_NZ) {                              // - beta_m
+            sk[ns] = 1;
+            sneg[ns] = 1 ^ ((fB & F_NEG) ? 1 : 0);
+            scomp[ns] = 1;
+            slp[ns] = (long long)eB - L;
+            ns++;
+        }
     } else {
-        prod(1, 1, A_ALPHAM, eAm, fAm, C_GAMMA0, eG0, fG0);
-        prod(1, 1, A_ALPHA0, eA0, fA0, C_GAMMAM, eGm, fGm);
-        prod(2, 0, A_ALPHAM, eAm, fAm, C_BETA0, eB0, fB0);
-        prod(2, 0, A_ALPHA0, eA0, fA0, C_BETAM, eBm, fBm);
+        term(0, 0, eA, fA, eB0, fB0, 0);             // + alpha_m beta_0   (C slot 0: beta_0)
+        if (m > 0) term(1, 1, eB, fB, eA0, fA0, 0);  // + beta_m alpha_0   (C slot 1: alpha_0)
+        term(2, 2, eG, fG, __ldg(&a.parE[P_B]), __ldg(&a.parF[P_B]), 1);  // - gamma_m b (C slot 2: b)
     }
-    {
-        const int pe = __ldg(&a.parE[P_B]), pf = __ldg(&a.parF[P_B]);
-        prod(2, 1, A_B, pe, pf, C_GAMMAM, eGm, fGm);
+    long long lo = LLONG_MAX, hi = LLONG_MIN;
+    for (int k = 0; k < ns; k++) {
+        lo = min(lo, slp[k]);
+        hi = max(hi, slp[k] + Lp + 2);
     }
-    param(0, 0, P_SIGMA, A_SIGMA, A_BETAM, C_BETAM, eBm, fBm);
-    param(0, 1, P_SIGMA, A_SIGMA, A_ALPHAM, C_ALPHAM, eAm, fAm);
-    param(1, 0, P_R, A_R, A_ALPHAM, C_ALPHAM, eAm, fAm);
-    if (fBm & F_NZ) {
-        OTerm t;
-        t.kind = 2;
-        t.tg = 1;
-        t.neg = 1 ^ (fBm & F_NEG);
-        t.aslot = A_BETAM;
-        t.bslot = -1;
-        t.lp = (long long)eBm - a.L;
-        t.v = 0;
-        ot[n++] = t;
+    for (int k = 0; k < NTERM; k++)
+        if (tp[k]) {
+            lo = min(lo, tlp[k]);
+            hi = max(hi, tlp[k] + 2LL * Lp + 2);
+        }
+    long long ilo = 0, ihi = 0;
+    if (c > 0 && m >= 2) {
+        long long l2[2], h2[2];
+        inner_window(a, (const long long *)(S.misc + MS_IMID), S.expT, S.flgT, m, l2, h2);
+        ilo = l2[c - 1];
+        ihi = h2[c - 1];
+        if (ihi > ilo) {
+            lo = min(lo, ilo);
+            hi = max(hi, ihi);
+        }
     }
-    return n;
-}
-
-__device__ __forceinline__ long long term_top(const OTerm &t, int Lp)
-{
-    return t.kind == 0 ? t.lp + 2LL * Lp + 2 : t.lp + Lp + 2;
-}
-
-// outer units of the cluster CTAs 1..C-1 (CTA 0 only combines)
-__device__ void outer_units(PSmem &S, const KArgs &a, const OTerm *ot, int nterm, int rank, int C)
-{
-    const int P = a.P, Lp = a.Lp;
-    int nd = 0;
-    for (int k = 0; k < nterm; k++) nd += ot[k].kind == 0;
-    const Chunking ck = chunking((long long)max(nd, 1) * P, (long long)(C - 1) * NT, P);
-    const long long Ud = (long long)nd * ck.H * P;
-    const long long U = Ud + (long long)(nterm - nd) * P;
-    const long long u0 = U * (rank - 1) / (C - 1), u1 = U * rank / (C - 1);
-    for (long long u = u0 + threadIdx.x; u < u1; u += NT) {
-        int k, h = 0, q;
-        if (u < Ud) {
-            int di = (int)(u / ((long long)ck.H * P));
-            int rem = (int)(u - (long long)di * ck.H * P);
-            h = rem / P;
-            q = rem - h * P;
-            // di-th dense term
-            k = 0;
-            for (int c = 0;; k++)
-                if (ot[k].kind == 0 && c++ == di) break;
+    int width = 0;
+    if (hi > lo) {
+        if (hi - lo > a.Wcap) {
+            atomicCAS(a.status, 0, DEV_ERANGE);
+            return false;
+        }
+        width = (int)(hi - lo);
+    } else {
+        lo = 0;
+    }
+    ((long long *)(bk + BK_LO))[0] = lo;
+    bk[BK_WIDTH] = width;
+    bk[BK_NSIMPLE] = ns;
+    for (int k = 0; k < ns; k++) {
+        bk[BK_SIMPLE + 4 * k] = sk[k];
+        bk[BK_SIMPLE + 4 * k + 1] = sneg[k];
+        bk[BK_SIMPLE + 4 * k + 2] = (int)(slp[k] - lo);
+        bk[BK_SIMPLE + 4 * k + 3] = scomp[k];
+        bk[BK_SV + k] = (int)sv[k];
+    }
+    const bool inner = c > 0 && m >= 2 && ihi > ilo;
+    bk[BK_INNER] = inner ? (int)(ilo - lo) : -1;
+    bk[BK_IWIDTH] = inner ? (int)(ihi - ilo) : 0;
+    int nrun = 0, prev_dhi = -1;
+    for (int k = 0; k < NTERM; k++) {
+        const int d = tp[k] ? (int)(tlp[k] - lo) : 0;
+        bk[BK_TERM + 4 * k] = tp[k];
+        bk[BK_TERM + 4 * k + 1] = tcomp[k];
+        bk[BK_TERM + 4 * k + 2] = tneg[k];
+        bk[BK_TERM + 4 * k + 3] = d;
+        int *ti = S.tinfo + k * TI;
+        ti[1] = tneg[k];
+        ti[2] = d & 7;
+        ti[3] = d >> 3;
+        // groups: maximal runs of present terms with equal d_hi
+        if (!tp[k]) {
+            prev_dhi = -1;
+            continue;
+        }
+        if (prev_dhi == (d >> 3)) {
+            S.misc[MS_RUNE + nrun - 1] = k + 1;
         } else {
-            int si = (int)((u - Ud) / P);
-            q = (int)(u - Ud - (long long)si * P);
-            k = 0;
-            for (int c = 0;; k++)
-                if (ot[k].kind != 0 && c++ == si) break;
+            S.misc[MS_RUN + nrun] = k;
+            S.misc[MS_RUNE + nrun] = k + 1;
+            nrun++;
         }
-        const OTerm &t = ot[k];
-        long long *win = S.win + (size_t)t.tg * S.wsz;
-        const int off = (int)(t.lp - ll_at(S.misc, MS_OBASE + 2 * t.tg));
-        const uint32_t *Av = S.vec + (size_t)t.aslot * S.AV;
-        if (t.kind == 0) {
-            const uint32_t *Cv = S.vec + (size_t)NA * S.AV + (size_t)t.bslot * S.CV;
-            const int s0 = h * ck.CL, s1 = min(s0 + ck.CL, (P + 1) * W);
-            mac_unit<false>(Av, Cv, q, s0, s1, Lp, S.M, win, off, t.neg);
-        } else if (t.kind == 1) {
-            scaled_unit(t.v, Av, q, win, off, t.neg);
-        } else {
-            add_unit(Av, q, win, off, t.neg);
-        }
+        prev_dhi = d >> 3;
     }
+    S.misc[MS_NRUN] = nrun;
+    return true;
 }
 
-// combined window of each target from the outer and the inner bases
-__device__ void combine_bases(PSmem &S, const KArgs &a, bool have_inner)
+// the bracket's lone and one-limb-parameter parts into win (thread t owns
+// columns t mod PT)
+__device__ void add_simple_parts(const PSmem &S, const Geo &G, long long *win, int width)
 {
-    if (threadIdx.x < 3) {
-        const int t = threadIdx.x;
-        const int ow = S.misc[MS_OWIDTH + t], iw = have_inner ? S.misc[MS_IWIDTH + t] : 0;
-        const long long ob = ll_at(S.misc, MS_OBASE + 2 * t), ib = ll_at(S.misc, MS_IBASE + 2 * t);
-        long long lo = LLONG_MAX, hi = LLONG_MIN;
-        if (ow) {
-            lo = min(lo, ob);
-            hi = max(hi, ob + ow);
-        }
-        if (iw) {
-            lo = min(lo, ib);
-            hi = max(hi, ib + iw);
-        }
-        int width = 0;
-        if (hi > lo) {
-            if (hi - lo > a.Wcap) {
-                atomicCAS(a.status, 0, DEV_ERANGE);
-                S.misc[MS_STATUS] = DEV_ERANGE;
-            } else {
-                width = (int)(hi - lo);
-            }
-        }
-        ll_at(S.misc, MS_BASE + 2 * t) = (hi > lo) ? lo : 0;
-        S.misc[MS_WIDTH + t] = width;
-    }
-}
-
-// Sum the outer windows of CTAs 1..C-1 into CTA 0's combined windows; every
-// CTA of the cluster takes a slice of the columns.
-__device__ void reduce_outer(PSmem &S, const KArgs &a, cg::cluster_group &cl, int rank, int C)
-{
-    int *misc0 = cl.map_shared_rank(S.misc, 0);
-    long long *comb0 = cl.map_shared_rank(S.comb, 0);
-    for (int t = 0; t < 3; t++) {
-        const int ow = S.misc[MS_OWIDTH + t];
-        if (!ow) continue;
-        const long long shift = ll_at(S.misc, MS_OBASE + 2 * t) - ll_at(misc0, MS_BASE + 2 * t);
-        const int c0 = ow * rank / C, c1 = ow * (rank + 1) / C;
-        for (int c = c0 + threadIdx.x; c < c1; c += NT) {
+    const int *bk = S.misc + MS_BK;
+    const int ns = bk[BK_NSIMPLE];
+    for (int cc = threadIdx.x; cc < width; cc += PT) {
+        long long s = 0;
+        for (int k = 0; k < ns; k++) {
+            const int kind = bk[BK_SIMPLE + 4 * k], neg = bk[BK_SIMPLE + 4 * k + 1];
+            const int y = cc - bk[BK_SIMPLE + 4 * k + 2];
+            const uint32_t *X = S.raw + (size_t)bk[BK_SIMPLE + 4 * k + 3] * G.Lp;
             long long v = 0;
-#pragma unroll
-            for (int r = 1; r < CP_C; r++) {
-                long long *wr = cl.map_shared_rank(S.win, r);
-                v += wr[(size_t)t * S.wsz + wphys(c)];
-            }
-            if (v) {
-                long long *dst = comb0 + (size_t)t * S.wsz + wphys((int)(c + shift));
-                *dst += v;
-            }
-        }
-    }
-}
-
-// close the three brackets in CTA 0 (warps 0..2): normalise, divide by d
-// (d = 1 truncates), write limbs to newc[t], return via misc exps/flags
-__device__ void close_three(PSmem &S, const KArgs &a, uint32_t d, int *outE, int *outF)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < 3) {
-        const int t = warp;
-        const int wd = S.misc[MS_WIDTH + t];
-        uint32_t *out = S.newc + (size_t)t * a.Lp;
-        int e = 0, f = 0;
-        if (wd > 0) {
-            uint32_t *dig = S.dig + (size_t)t * a.Wcap;
-            long long *col = S.comb + (size_t)t * S.wsz;
-            Norm nr = warp_normalize(col, dig, wd, a.status);
-            for (int c = lane; c < wd; c += 32) col[wphys(c)] = 0;
-            if (nr.top >= 0) {
-                long long eq = warp_divide(dig, nr.top, ll_at(S.misc, MS_BASE + 2 * t), d, a.L, out);
-                if (eq > (1LL << 30) || eq < -(1LL << 30)) {
-                    if (lane == 0) atomicCAS(a.status, 0, DEV_ERANGE);
-                    eq = 0;
-                }
-                e = (int)eq;
-                f = F_NZ | (nr.neg ? F_NEG : 0);
-            }
-        }
-        if (!(f & F_NZ))
-            for (int x = lane; x < a.L; x += 32) out[x] = 0u;
-        for (int x = a.L + lane; x < a.Lp; x += 32) out[x] = 0u;
-        __syncwarp();
-        if (lane == 0) {
-            outE[t] = e;
-            outF[t] = f;
-        }
-    }
-}
-
-// copy the newest number (3 components, plain limbs in CTA 0's newc) into
-// this CTA's slots in A and C layout
-__device__ void pull_newest(PSmem &S, const KArgs &a, cg::cluster_group &cl, bool coefficient)
-{
-    const uint32_t *src = cl.map_shared_rank(S.newc, 0);
-    const int Lp = a.Lp;
-    uint32_t *A = S.vec, *Cb = S.vec + (size_t)NA * S.AV;
-    for (int e = threadIdx.x; e < 3 * Lp; e += NT) {
-        const int comp = e / Lp, x = e - comp * Lp;
-        const uint32_t v = src[e];
-        if (coefficient) {
-            if (comp == 0) {
-                A[(size_t)A_ALPHAM * S.AV + phys(x)] = v;
-                Cb[(size_t)C_ALPHAM * S.CV + phys(x)] = v;
-            } else if (comp == 1) {
-                A[(size_t)A_BETAM * S.AV + phys(x)] = v;
-                Cb[(size_t)C_BETAM * S.CV + phys(x)] = v;
+            if (kind == 1) {
+                if (y >= 0 && y < G.Lp) v = X[y];
             } else {
-                Cb[(size_t)C_GAMMAM * S.CV + phys(x)] = v;
+                const uint32_t pv = (uint32_t)bk[BK_SV + k];
+                if (y >= 0 && y < G.Lp) v += (uint32_t)((uint64_t)pv * X[y]);
+                if (y >= 1 && y <= G.Lp) v += (long long)(((uint64_t)pv * X[y - 1]) >> 32);
             }
-        } else {
-            Cb[(size_t)(C_H0 + comp) * S.CV + phys(x)] = v;
+            s += neg ? -v : v;
         }
+        if (s) win[cc] += s;
     }
 }
 
-// One Horner chain of Eq. (2) for component c, in one CTA: h_N = c_N,
-// h_i = trunc_L(tau h_{i+1} + c_i) for i = N-1 .. 0, then the new state (and
-// a record).  The product tau h is split into (chunk, pair) units, one per
-// thread; their column digits are staged and summed per (pair, block, digit)
-// into the window, c_i (prefetched from global one step ahead) is added, and
-// warp 0 normalises and truncates.
-__device__ void horner_component(PSmem &S, const KArgs &a, int c, long long step, Prof &pr)
+// normalise win[0..width) (base lo) and divide by dv.d into L limbs of out;
+// zero the window.  Exponent and flags via e, f; false on a range error
+// (status set).
+__device__ bool close_bracket(PSmem &S, const KArgs &a, const Geo &G, long long *win, int width,
+                              long long lo, const Divisor &dv, uint32_t *out, int &e, int &f)
 {
-    const int N1 = a.N + 1, Lp = a.Lp, L = a.L, P = a.P;
-    const int cslot = c == 0 ? C_ALPHAM : (c == 1 ? C_BETAM : C_GAMMAM);
-    uint32_t *hC = S.vec + (size_t)NA * S.AV + (size_t)cslot * S.CV;  // h in C layout
-    const uint32_t *tauA = S.vec + (size_t)A_TAU * S.AV;
-    uint32_t *hp = S.newc + (size_t)c * Lp;                           // h, plain limbs
+    e = 0;
+    f = 0;
+    bool ok = true;
+    int top = -1, neg = 0;
+    if (width > 0) {
+        const Norm nr = block_normalize(win, S.dig, width, (long long *)(S.misc + MS_RED), a.status);
+        top = nr.top;
+        neg = nr.neg;
+    }
+    if (top >= 0) {
+        const long long eq = block_divide(S.dig, top, lo, dv, G.L, out, S.misc + MS_RED);
+        if (eq > (1LL << 30) || eq < -(1LL << 30)) {
+            if (threadIdx.x == 0) atomicCAS(a.status, 0, DEV_ERANGE);
+            ok = false;
+        } else {
+            e = (int)eq;
+            f = F_NZ | (neg ? F_NEG : 0);
+        }
+    }
+    if (!(f & F_NZ))
+        for (int x = threadIdx.x; x < G.L; x += PT) out[x] = 0u;
+    for (int c = threadIdx.x; c < width; c += PT) win[c] = 0;
+    __syncthreads();
+    return ok;
+}
+
+// One Horner chain of Eq. (2) for component c on this CTA: h_N = c_N,
+// h_i = trunc_L(tau h_{i+1} + c_i) for i = N-1 .. 0, then the new state (and
+// a record).  h_N is this CTA's newest number.
+__device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, long long step,
+                                 Prof &pr)
+{
+    const int N1 = G.N1, Lp = G.Lp, L = G.L;
+    uint32_t *hA = S.vA + 3 * (size_t)G.VW;        // h as first factor (slot 3)
+    const uint32_t *tauC = S.vC + 3 * (size_t)G.VW; // tau (slot 3)
+    uint32_t *hp = S.raw + 2 * (size_t)Lp;     // h, plain limbs
     long long *win = S.win;
     const int tauE = __ldg(&a.parE[P_TAU]), tauF = __ldg(&a.parF[P_TAU]);
-    // chunks: at most one unit per thread
-    int He = HU / P;
-    if (He < 1) He = 1;
-    if (He > P + 1) He = P + 1;
-    const int CL = ((P + 1 + He - 1) / He) * W;
-    He = ((P + 1) * W + CL - 1) / CL;
-    const int U = P * He;
-    int *hE = S.misc + MS_HE + c, *hF = S.misc + MS_HF + c;
-    if (threadIdx.x == 0) {
-        *hE = S.expT[c * N1 + a.N];
-        *hF = S.flgT[c * N1 + a.N];
+    const uint32_t *cN = S.newc;
+    int he = S.misc[MS_NEWE], hf = S.misc[MS_NEWE + 1];
+    for (int x = threadIdx.x; x < Lp; x += PT) {
+        hp[x] = cN[x];
+        hA[gpos(x)] = cN[x];
     }
-    for (int x = threadIdx.x; x < Lp; x += NT) hp[x] = hC[phys(x)];
-    uint32_t cur[4], nxt[4];
+    const Divisor one = make_divisor(1u);
+    constexpr int CR = MAX_L / PT;
+    uint32_t cur[CR], nxt[CR];
 #pragma unroll
-    for (int r = 0; r < 4; r++) {
-        const int x = threadIdx.x + r * NT;
+    for (int r = 0; r < CR; r++) {
+        const int x = threadIdx.x + r * PT;
         cur[r] = (x < Lp && a.N >= 1) ? __ldcg(&a.coefL[((size_t)c * N1 + a.N - 1) * Lp + x]) : 0u;
     }
     __syncthreads();
+    bool ok = true;
     for (int i = a.N - 1; i >= 0; i--) {
 #pragma unroll
-        for (int r = 0; r < 4; r++) {
-            const int x = threadIdx.x + r * NT;
+        for (int r = 0; r < CR; r++) {
+            const int x = threadIdx.x + r * PT;
             nxt[r] = (i > 0 && x < Lp) ? __ldcg(&a.coefL[((size_t)c * N1 + i - 1) * Lp + x]) : 0u;
         }
-        // window: the product tau h and the lone c_i
-        const int he = *hE, hf = *hF;
         const int ce = S.expT[c * N1 + i], cf = S.flgT[c * N1 + i];
         const bool prod = (hf & F_NZ) && (tauF & F_NZ);
         const bool lone = (cf & F_NZ) != 0;
@@ -831,133 +894,77 @@ __device__ void horner_component(PSmem &S, const KArgs &a, int c, long long step
         int width = 0;
         if (hi > lo) {
             if (hi - lo > a.Wcap) {
-                if (threadIdx.x == 0) {
-                    atomicCAS(a.status, 0, DEV_ERANGE);
-                    S.misc[MS_HERR] = 1;
-                }
+                if (threadIdx.x == 0) atomicCAS(a.status, 0, DEV_ERANGE);
+                ok = false;
                 break;  // uniform: every thread computed the same width
             }
             width = (int)(hi - lo);
         }
-        const int offp = (int)(lpp - lo), offa = (int)(lpa - lo);
-        const bool pneg = ((hf ^ tauF) & F_NEG) != 0;
-        if (prod && threadIdx.x < U) {
-            const int h = threadIdx.x / P, q = threadIdx.x - h * P;
-            const int s0 = h * CL, s1 = min(s0 + CL, (P + 1) * W);
-            long long v1[W + 2], v2[W + 2];
-            mac_unit_vals<false>(tauA, hC, q, s0, s1, Lp, S.M, v1, v2);
-#pragma unroll
-            for (int t = 0; t < W + 2; t++) {
-                S.hstage[(size_t)t * (HU + 1) + threadIdx.x] = pneg ? -v1[t] : v1[t];
-                S.hstage[(size_t)(W + 2 + t) * (HU + 1) + threadIdx.x] = pneg ? -v2[t] : v2[t];
-            }
-        }
-        __syncthreads();
+        if (prod)
+            group_products(G, hA, tauC, 0, 1, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.stage, win,
+                           (int)(lpp - lo));
         pr.mark(PR_HMAC);
-        if (prod) {
-            for (int cb = threadIdx.x; cb < P * 2 * (W + 2); cb += NT) {
-                const int q = cb / (2 * (W + 2)), r = cb - q * 2 * (W + 2);
-                const int b = r / (W + 2), k = r - b * (W + 2);
-                long long sum = 0;
-                for (int h = 0; h < He; h++) sum += S.hstage[(size_t)r * (HU + 1) + h * P + q];
-                if (sum)
-                    atomicAdd((unsigned long long *)&win[wphys(offp + b * Lp + q * W + k)],
-                              (unsigned long long)sum);
-            }
-        }
         if (lone) {
+            const int offa = (int)(lpa - lo);
 #pragma unroll
-            for (int r = 0; r < 4; r++) {
-                const int x = threadIdx.x + r * NT;
-                if (x < Lp && cur[r]) {
-                    const long long v = (cf & F_NEG) ? -(long long)cur[r] : (long long)cur[r];
-                    atomicAdd((unsigned long long *)&win[wphys(offa + x)], (unsigned long long)v);
-                }
+            for (int r = 0; r < CR; r++) {
+                const int x = threadIdx.x + r * PT;
+                if (x < Lp && cur[r]) win[offa + x] += (cf & F_NEG) ? -(long long)cur[r] : (long long)cur[r];
             }
         }
         __syncthreads();
-        if (threadIdx.x < 32) {
-            const int lane = threadIdx.x;
-            int e = 0, f = 0;
-            if (width > 0) {
-                Norm nr = warp_normalize(win, S.dig, width, a.status);
-                for (int cc = lane; cc < width; cc += 32) win[wphys(cc)] = 0;
-                if (nr.top >= 0) {
-                    long long eq = warp_divide(S.dig, nr.top, lo, 1u, L, hp);
-                    if (eq > (1LL << 30) || eq < -(1LL << 30)) {
-                        if (lane == 0) {
-                            atomicCAS(a.status, 0, DEV_ERANGE);
-                            S.misc[MS_HERR] = 1;
-                        }
-                        eq = 0;
-                    }
-                    e = (int)eq;
-                    f = F_NZ | (nr.neg ? F_NEG : 0);
-                }
-            }
-            if (!(f & F_NZ))
-                for (int x = lane; x < L; x += 32) hp[x] = 0u;
-            __syncwarp();
-            for (int x = lane; x < Lp; x += 32) hC[phys(x)] = x < L ? hp[x] : 0u;
-            if (lane == 0) {
-                *hE = e;
-                *hF = f;
-            }
+        int e, f;
+        if (!close_bracket(S, a, G, win, width, lo, one, hp, e, f)) {
+            ok = false;
+            break;
         }
+        for (int x = threadIdx.x; x < Lp; x += PT) hA[gpos(x)] = x < L ? hp[x] : 0u;
+        he = e;
+        hf = f;
 #pragma unroll
-        for (int r = 0; r < 4; r++) cur[r] = nxt[r];
+        for (int r = 0; r < CR; r++) cur[r] = nxt[r];
         __syncthreads();
         pr.mark(PR_HCLOSE);
-        if (S.misc[MS_HERR]) break;
     }
-    // the new state and, when due, a record
+    if (!ok) return false;
     const long long rec = (a.record_every > 0 && ((step + 1) % a.record_every) == 0)
                               ? (step + 1) / a.record_every - 1 : -1;
-    for (int x = threadIdx.x; x < Lp; x += NT) {
-        a.stL[(size_t)c * Lp + x] = hp[x];
-        if (rec >= 0 && x < L) a.recL[((size_t)rec * 3 + c) * L + x] = hp[x];
+    for (int x = threadIdx.x; x < Lp; x += PT) {
+        const uint32_t v = x < L ? hp[x] : 0u;
+        a.stL[(size_t)c * Lp + x] = v;
+        if (rec >= 0 && x < L) a.recL[((size_t)rec * 3 + c) * L + x] = v;
     }
     if (threadIdx.x == 0) {
-        a.stE[c] = *hE;
-        a.stF[c] = *hF;
+        a.stE[c] = he;
+        a.stF[c] = hf;
         if (rec >= 0) {
-            a.recS[rec * 3 + c] = (*hF & F_NEG) ? 1 : 0;
-            a.recE[rec * 3 + c] = *hE;
+            a.recS[rec * 3 + c] = (hf & F_NEG) ? 1 : 0;
+            a.recE[rec * 3 + c] = he;
         }
     }
     __threadfence();
+    return true;
 }
 
-__device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa)
+
+// Bracket CTA c: coefficient component c of every index, then Horner.
+__device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &G)
 {
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int C = CP_C;
-    const int N1 = a.N + 1, Lp = a.Lp, L = a.L;
-    uint32_t *A = S.vec, *Cb = S.vec + (size_t)NA * S.AV;
-    OTerm *ot = (OTerm *)(S.tinfo);  // up to 10 terms (tinfo holds >= 64 x 4 ints)
-    const bool prof_on = (rank == 0);
-    int *misc0 = cl.map_shared_rank(S.misc, 0);
-    // zero windows and C padding; parameters into A slots
-    for (int e = threadIdx.x; e < 3 * S.wsz; e += NT) {
-        S.win[e] = 0;
-        S.comb[e] = 0;
-    }
-    for (int e = threadIdx.x; e < NC * S.M; e += NT) {
-        int slot = e / S.M, x = e - slot * S.M;
-        if (x >= Lp) Cb[(size_t)slot * S.CV + phys(x)] = 0u;
-    }
-    for (int e = threadIdx.x; e < 4 * Lp; e += NT) {
-        int p = e / Lp, x = e - p * Lp;
-        A[(size_t)p * S.AV + phys(x)] = __ldg(&a.parL[(size_t)p * Lp + x]);  // A_SIGMA.. = P_*
-    }
+    const int c = blockIdx.x;
+    const int N1 = G.N1, Lp = G.Lp;
+    const bool prof_on = (c == 1);
+    for (int e = threadIdx.x; e < NA * G.VW; e += PT) S.vA[e] = 0u;
+    for (int e = threadIdx.x; e < NC * G.VW; e += PT) S.vC[e] = 0u;
+    for (int e = threadIdx.x; e < 3 * Lp; e += PT) S.raw[e] = 0u;
+    for (int e = threadIdx.x; e < Lp; e += PT) S.newc[e] = 0u;
+    for (int e = threadIdx.x; e < 2 * G.WW; e += PT) S.win[e] = 0;
     if (threadIdx.x < 3) {
         // single non-zero limb of sigma, R, b (else -1)
         const int p = threadIdx.x;
         int cnt = 0, i0 = -1;
         uint32_t v = 0;
         for (int x = 0; x < Lp; x++) {
-            uint32_t l = __ldg(&a.parL[(size_t)p * Lp + x]);
+            const uint32_t l = __ldg(&a.parL[(size_t)p * Lp + x]);
             if (l) {
                 cnt++;
                 i0 = x;
@@ -967,241 +974,213 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa)
         S.misc[MS_PSCAL + 2 * p] = cnt == 1 ? i0 : -1;
         S.misc[MS_PSCAL + 2 * p + 1] = (int)v;
     }
-    if (rank == 0 && threadIdx.x == 0) {
-        S.misc[MS_ERR_A] = 0;
-        S.misc[MS_ERR_C] = 0;
+    __syncthreads();
+    // fixed factors: sigma (alpha'), R (beta'), b (gamma'), tau (Horner)
+    if (c == 0) {
+        to_slot(S.vC, a.parL + (size_t)P_SIGMA * Lp, Lp);
+        to_slot(S.vC + G.VW, a.parL + (size_t)P_SIGMA * Lp, Lp);
     }
-    cl.sync();
-    // stop: the cluster-wide decision to end the launch.  It is only ever read
-    // from CTA 0's shared memory between two cluster barriers, so every CTA of
-    // the cluster takes the same branch, and the launch leaves through one
-    // final cluster barrier: no CTA exits while a peer may still read its
-    // shared memory.
-    bool stop = false;
-    for (long long step = 0; step < a.nsteps && !stop; step++) {
-        // the state is coefficient 0 (Sec. 2): into every CTA's slots and tables
-        for (int e = threadIdx.x; e < 3 * Lp; e += NT) {
-            const int comp = e / Lp, x = e - comp * Lp;
-            const uint32_t v = __ldcg(&a.stL[e]);
-            if (comp == 0) {
-                A[(size_t)A_ALPHA0 * S.AV + phys(x)] = v;
-                A[(size_t)A_ALPHAM * S.AV + phys(x)] = v;
-                Cb[(size_t)C_ALPHAM * S.CV + phys(x)] = v;
-            } else if (comp == 1) {
-                Cb[(size_t)C_BETA0 * S.CV + phys(x)] = v;
-                A[(size_t)A_BETAM * S.AV + phys(x)] = v;
-                Cb[(size_t)C_BETAM * S.CV + phys(x)] = v;
-            } else {
-                Cb[(size_t)C_GAMMA0 * S.CV + phys(x)] = v;
-                Cb[(size_t)C_GAMMAM * S.CV + phys(x)] = v;
-            }
-            if (rank == 0) a.coefL[(size_t)comp * N1 * Lp + x] = v;
+    if (c == 1) to_slot(S.vC + 2 * (size_t)G.VW, a.parL + (size_t)P_R * Lp, Lp);
+    if (c == 2) to_slot(S.vC + 2 * (size_t)G.VW, a.parL + (size_t)P_B * Lp, Lp);
+    to_slot(S.vC + 3 * (size_t)G.VW, a.parL + (size_t)P_TAU * Lp, Lp);
+    __syncthreads();
+    for (long long step = 0; step < a.nsteps; step++) {
+        // the state is coefficient 0 (Sec. 2): publish this CTA's component,
+        // then take all three
+        for (int x = threadIdx.x; x < Lp; x += PT)
+            a.coefL[(size_t)c * N1 * Lp + x] = __ldcg(&a.stL[(size_t)c * Lp + x]);
+        if (threadIdx.x == 0) {
+            a.coefE[c * N1] = __ldcg(&a.stE[c]);
+            a.coefF[c * N1] = __ldcg(&a.stF[c]);
         }
+        __syncthreads();
+        if (threadIdx.x == 0) red_release_add_u32(pa.pub, 1u);
+        if (!wait_geq(S, a, pa.pub, (unsigned)(3 * (step * N1 + 1)))) return;
         if (threadIdx.x < 3) {
-            const int e = __ldcg(&a.stE[threadIdx.x]), f = __ldcg(&a.stF[threadIdx.x]);
-            S.expT[threadIdx.x * N1] = e;
-            S.flgT[threadIdx.x * N1] = f;
-            if (rank == 0) {
-                a.coefE[threadIdx.x * N1] = e;
-                a.coefF[threadIdx.x * N1] = f;
-            }
+            S.expT[threadIdx.x * N1] = __ldcg(&a.coefE[threadIdx.x * N1]);
+            S.flgT[threadIdx.x * N1] = __ldcg(&a.coefF[threadIdx.x * N1]);
+        }
+        for (int e = threadIdx.x; e < 3 * Lp; e += PT) {
+            const int comp = e / Lp, x = e - comp * Lp;
+            S.raw[e] = __ldcg(&a.coefL[((size_t)comp * N1) * Lp + x]);
+        }
+        __syncthreads();
+        if (c == 1) {
+            to_slot(S.vC, S.raw + 2 * (size_t)Lp, Lp);  // gamma_0
+            to_slot(S.vC + G.VW, S.raw, Lp);            // alpha_0
+        } else if (c == 2) {
+            to_slot(S.vC, S.raw + Lp, Lp);              // beta_0
+            to_slot(S.vC + G.VW, S.raw, Lp);            // alpha_0
         }
         __syncthreads();
         for (int m = 0; m < a.N; m++) {
             Prof pr(a, prof_on, S.misc);
             const long long g = step * a.N + m;
             const int set = (int)(g % PIPE_SETS);
-            const bool have_inner = m >= 2;
-            // (A) outer terms and their windows; CTA 0 also places the inner
-            // windows and fetches the workers' inner sums
-            if (threadIdx.x == 0) {
-                S.misc[MS_NTERM] = outer_terms(S, a, m, ot);
-                S.misc[MS_STATUS] = 0;
-            }
+            const Divisor dvm = make_divisor((uint32_t)(m + 1));
+            if (threadIdx.x == 0) S.misc[MS_STATUS] = bracket_setup(S, a, pa, G, c, m, set) ? 0 : 1;
             __syncthreads();
-            const int nterm = S.misc[MS_NTERM];
-            {
-                long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
-                long long hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
-                if (threadIdx.x == 0)
-                    for (int k = 0; k < nterm; k++) {
-                        lo[ot[k].tg] = min(lo[ot[k].tg], ot[k].lp);
-                        hi[ot[k].tg] = max(hi[ot[k].tg], term_top(ot[k], Lp));
-                    }
-                block_window(S, a, lo, hi, MS_OBASE, MS_OWIDTH);
+            if (S.misc[MS_STATUS]) return;
+            const int *bk = S.misc + MS_BK;
+            const long long lo = ((const long long *)(bk + BK_LO))[0];
+            const int width = bk[BK_WIDTH];
+            long long *win = S.win;
+            // first factors of the product terms: component shifted by d_lo,
+            // complemented when the term is negative
+            for (int k = 0; k < NTERM; k++) {
+                if (!bk[BK_TERM + 4 * k]) continue;
+                const uint32_t *src = S.raw + (size_t)bk[BK_TERM + 4 * k + 1] * Lp;
+                const uint32_t inv = bk[BK_TERM + 4 * k + 2] ? 0xffffffffu : 0u;
+                const int dl = bk[BK_TERM + 4 * k + 3] & 7;
+                uint32_t *dst = S.vA + (size_t)k * G.VW;
+                for (int x = threadIdx.x; x < G.M; x += PT) {
+                    const int y = x - dl;
+                    dst[gpos(x)] = (y >= 0 && y < Lp) ? (src[y] ^ inv) : 0u;
+                }
             }
-            if (rank == 0) {
-                if (have_inner) inner_windows(S, a, m, MS_IBASE, MS_IWIDTH);
-                combine_bases(S, a, have_inner);
-                __syncthreads();
-                pr.mark(PR_PLACE);
-                const bool bad = S.misc[MS_STATUS] != 0;
-                if (have_inner && !bad) {
-                    // every worker has added its inner sums of index m
-                    const unsigned target =
-                        (unsigned)((g / PIPE_SETS + 1) * (long long)(gridDim.x - CP_C));
-                    const bool ok = wait_geq(S, a, pa.done + set, target);
-                    pr.mark(PR_BARRIER);
-                    if (ok) {
-                        const long long *gs = pa.gin + (size_t)set * 2 * a.Wcap;
-                        for (int t = 1; t <= 2; t++) {
-                            const int iw = S.misc[MS_IWIDTH + t];
-                            const long long shift =
-                                ll_at(S.misc, MS_IBASE + 2 * t) - ll_at(S.misc, MS_BASE + 2 * t);
-                            long long *gg = (long long *)gs + (size_t)(t - 1) * a.Wcap;
-                            for (int c0 = 0; c0 < iw; c0 += 4 * NT) {
-                                long long v[4];
-#pragma unroll
-                                for (int k = 0; k < 4; k++) {
-                                    const int c = c0 + k * NT + threadIdx.x;
-                                    v[k] = c < iw ? __ldcg(&gg[c]) : 0;
-                                }
-#pragma unroll
-                                for (int k = 0; k < 4; k++) {
-                                    const int c = c0 + k * NT + threadIdx.x;
-                                    if (v[k]) {
-                                        S.comb[(size_t)t * S.wsz + wphys((int)(c + shift))] += v[k];
-                                        gg[c] = 0;
-                                    }
-                                }
-                            }
+            add_simple_parts(S, G, win, width);
+            pr.mark(PR_PLACE);
+            const int nrun = S.misc[MS_NRUN];
+            for (int rr = 0; rr < nrun; rr++) {
+                const int rs = S.misc[MS_RUN + rr], re = S.misc[MS_RUNE + rr];
+                group_products(G, S.vA, S.vC, rs, re - rs, S.tinfo, false, S.stage, win,
+                               S.tinfo[rs * TI + 3] * W);
+            }
+            pr.mark(PR_MAC);
+            if (bk[BK_INNER] >= 0) {
+                // every worker has added its inner sums of index m
+                const unsigned target = (unsigned)((g / PIPE_SETS + 1) * (long long)(gridDim.x - NCL));
+                if (!wait_geq(S, a, pa.done + set, target)) return;
+                pr.mark(PR_BARRIER);
+                long long *gg = pa.gin + ((size_t)set * 2 + (c - 1)) * a.Wcap;
+                const int off = bk[BK_INNER], iw = bk[BK_IWIDTH];
+                for (int cc = threadIdx.x; cc < width; cc += PT) {
+                    const int y = cc - off;
+                    if (y >= 0 && y < iw) {
+                        const long long v = __ldcg(&gg[y]);
+                        if (v) {
+                            win[cc] += v;
+                            gg[y] = 0;
                         }
                     }
-                    pr.mark(PR_STAGE);
                 }
-                if (threadIdx.x == 0) S.misc[MS_ERR_A] = bad || ld_relaxed_int(a.status) != 0;
-            } else if (S.misc[MS_STATUS] == 0) {
-                outer_units(S, a, ot, nterm, rank, C);
-            }
-            cl.sync();  // #1: outer partial windows and the inner sums are in place
-            pr.mark(PR_MAC);
-            stop = misc0[MS_ERR_A] != 0;
-            if (!stop) reduce_outer(S, a, cl, rank, C);
-            pr.mark(PR_X1);
-            cl.sync();  // #2: CTA 0 holds the full brackets
-            pr.mark(PR_X2);
-            if (stop) break;
-            for (int e = threadIdx.x; e < 3 * S.wsz; e += NT) S.win[e] = 0;
-            pr.mark(PR_FLUSH);
-            if (rank == 0) {
-                int *eo = S.misc + MS_HE, *fo = S.misc + MS_HF;
-                close_three(S, a, (uint32_t)(m + 1), eo, fo);
-                __syncthreads();
-                pr.mark(PR_X5);
-                if (threadIdx.x < 3) {
-                    S.expT[threadIdx.x * N1 + m + 1] = eo[threadIdx.x];
-                    S.flgT[threadIdx.x * N1 + m + 1] = fo[threadIdx.x];
-                    a.coefE[threadIdx.x * N1 + m + 1] = eo[threadIdx.x];
-                    a.coefF[threadIdx.x * N1 + m + 1] = fo[threadIdx.x];
-                }
-                for (int e = threadIdx.x; e < 3 * Lp; e += NT) {
-                    const int comp = e / Lp, x = e - comp * Lp;
-                    a.coefL[((size_t)comp * N1 + m + 1) * Lp + x] = S.newc[e];
-                }
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    __threadfence();
-                    st_release_u32(pa.pub, (unsigned)(step * N1 + m + 2));
-                    S.misc[MS_ERR_C] = ld_relaxed_int(a.status) != 0;
-                }
-            }
-            pr.mark(PR_CLOSE);
-            cl.sync();  // #3: coefficient m+1 is in CTA 0's newc
-            pr.mark(PR_X3);
-            stop = misc0[MS_ERR_C] != 0;
-            if (stop) break;
-            pull_newest(S, a, cl, true);
-            if (threadIdx.x < 3 && rank != 0) {
-                S.expT[threadIdx.x * N1 + m + 1] = misc0[MS_HE + threadIdx.x];
-                S.flgT[threadIdx.x * N1 + m + 1] = misc0[MS_HF + threadIdx.x];
+                pr.mark(PR_STAGE);
             }
             __syncthreads();
+            int e, f;
+            const bool ok = close_bracket(S, a, G, win, width, lo, dvm, S.newc, e, f);
+            pr.mark(PR_CLOSE);
+            if (!ok) return;
+            if (threadIdx.x == 0) {
+                S.misc[MS_NEWE] = e;
+                S.misc[MS_NEWE + 1] = f;
+            }
+            for (int x = threadIdx.x; x < Lp; x += PT) a.coefL[((size_t)c * N1 + m + 1) * Lp + x] = S.newc[x];
+            if (c == 0 && m + 2 < a.N) {
+                // window table of the inner sums of index m+2 without its two
+                // newest pairs: pairs (a, m+2-a), a = 2..m
+                long long lo3[2] = {LLONG_MAX, LLONG_MAX}, hi3[2] = {LLONG_MIN, LLONG_MIN};
+                for (int aa = 2 + threadIdx.x; aa <= m; aa += PT) {
+                    const int b = m + 2 - aa;
+                    if (!(S.flgT[aa] & F_NZ)) continue;
+                    for (int tg = 0; tg < 2; tg++) {
+                        const int crow = (tg == 0 ? 2 : 1) * N1 + b;
+                        if (!(S.flgT[crow] & F_NZ)) continue;
+                        const long long lp = (long long)S.expT[aa] + S.expT[crow] - 2LL * G.L;
+                        lo3[tg] = min(lo3[tg], lp);
+                        hi3[tg] = max(hi3[tg], lp + 2LL * Lp + 2);
+                    }
+                }
+                long long *red = (long long *)(S.misc + MS_RED);
+                const long long r0 = block_min_ll(lo3[0], red), r1 = block_max_ll(hi3[0], red);
+                const long long r2 = block_min_ll(lo3[1], red), r3 = block_max_ll(hi3[1], red);
+                if (threadIdx.x == 0) {
+                    long long *mid = pa.imid + (size_t)((g + 2) % PIPE_SETS) * 4;
+                    mid[0] = r0;
+                    mid[1] = r1;
+                    mid[2] = r2;
+                    mid[3] = r3;
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                a.coefE[c * N1 + m + 1] = e;
+                a.coefF[c * N1 + m + 1] = f;
+                red_release_add_u32(pa.pub, 1u);
+            }
+            pr.mark(PR_X3);
+            // coefficient m+1: all three components
+            if (!wait_geq(S, a, pa.pub, (unsigned)(3 * (step * N1 + m + 2)))) return;
             pr.mark(PR_X4);
+            if (threadIdx.x < 3) {
+                const int idx = threadIdx.x * N1 + m + 1;
+                S.expT[idx] = __ldcg(&a.coefE[idx]);
+                S.flgT[idx] = __ldcg(&a.coefF[idx]);
+            }
+            if (threadIdx.x >= 32 && threadIdx.x < 36 && m + 1 >= 2 && m + 1 < a.N) {
+                // inner-window table of index m+1 (written with coefficient m-1's alpha)
+                ((long long *)(S.misc + MS_IMID))[threadIdx.x - 32] =
+                    __ldcg(&pa.imid[(size_t)((g + 1) % PIPE_SETS) * 4 + threadIdx.x - 32]);
+            }
+            for (int e2 = threadIdx.x; e2 < 3 * Lp; e2 += PT) {
+                const int comp = e2 / Lp, x = e2 - comp * Lp;
+                S.raw[e2] = comp == c ? S.newc[x] : __ldcg(&a.coefL[((size_t)comp * N1 + m + 1) * Lp + x]);
+            }
+            __syncthreads();
+            pr.mark(PR_X5);
         }
-        if (stop) break;
-        // Horner (Eq. (2)), one component per CTA (ranks 0..2), no cluster
-        // barrier inside: h_N = c_N, h_i = trunc_L(tau h_{i+1} + c_i)
+        // Horner (Eq. (2)) for this CTA's component
         Prof ph(a, prof_on, S.misc);
-        if (threadIdx.x == 0) S.misc[MS_HERR] = 0;
-        __syncthreads();
-        if (rank < 3) horner_component(S, a, rank, step, ph);
+        if (!horner_component(S, a, G, c, step, ph)) return;
         __syncthreads();
         ph.mark(PR_HORNER);
-        cl.sync();  // the new state is in global memory
-        {
-            // stop if any component failed (each CTA reads the same three flags)
-            int bad = 0;
-            for (int r = 0; r < 3; r++) bad |= cl.map_shared_rank(S.misc, r)[MS_HERR];
-            stop = bad != 0;
-        }
-        cl.sync();  // flags read; the next step may reuse them
     }
-    cl.sync();  // the only way out of the closer
 }
 
-__global__ void __launch_bounds__(NT, 1) pipe_kernel(KArgs a, PArgs pa)
+__global__ void __launch_bounds__(PT, 1) pipe_kernel(KArgs a, PArgs pa)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    const Geo G(a.L, a.Lp, a.N, a.Wcap);
     PSmem S;
-    pipe_layout(a.Lp, a.N, a.Wcap, a.tb, pa.umax, &S, smem_raw);
-    const bool prof_cta = blockIdx.x == 0 || blockIdx.x == gridDim.x - 1;
+    pipe_layout(G, a.N, pa.tb, &S, smem_raw);
+    const bool prof_cta = blockIdx.x == 1 || blockIdx.x == gridDim.x - 1;
     if (threadIdx.x < PROF_SLOTS) ((long long *)(S.misc + MS_PROF))[threadIdx.x] = 0;
+    if (threadIdx.x == 0) S.misc[MS_STATUS] = 0;
     __syncthreads();
     Prof tot(a, prof_cta, S.misc);
-    if (blockIdx.x < (unsigned)CP_C)
-        closer_loop(S, a, pa);
+    if (blockIdx.x < (unsigned)NCL)
+        closer_loop(S, a, pa, G);
     else
-        worker_loop(S, a, pa);
+        worker_loop(S, a, pa, G);
     tot.mark(PR_TOTAL);
     if (a.prof && prof_cta && threadIdx.x == 0) {
-        long long *dst = a.prof + (blockIdx.x == 0 ? 0 : PROF_SLOTS);
+        long long *dst = a.prof + (blockIdx.x == 1 ? 0 : PROF_SLOTS);
         for (int k = 0; k < PROF_SLOTS; k++) dst[k] += ((long long *)(S.misc + MS_PROF))[k];
     }
 }
 
 }  // namespace
 
-size_t pipe_smem_bytes(int Lp, int N, int Wcap, int tb, int umax)
+size_t pipe_smem_bytes(int L, int Lp, int N, int Wcap, int tb)
 {
-    return pipe_layout(Lp, N, Wcap, tb, umax, nullptr, nullptr);
+    const Geo G(L, Lp, N, Wcap);
+    return pipe_layout(G, N, tb, nullptr, nullptr);
 }
 
-static cudaLaunchConfig_t pipe_config(int grid, int C, size_t smem, cudaStream_t st,
-                                      cudaLaunchAttribute *attrs, bool coop)
-{
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(NT);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = st;
-    attrs[0].id = cudaLaunchAttributeClusterDimension;
-    attrs[0].val.clusterDim.x = C;
-    attrs[0].val.clusterDim.y = 1;
-    attrs[0].val.clusterDim.z = 1;
-    cfg.attrs = attrs;
-    cfg.numAttrs = 1;
-    if (coop) {
-        attrs[1].id = cudaLaunchAttributeCooperative;
-        attrs[1].val.cooperative = 1;
-        cfg.numAttrs = 2;
-    }
-    return cfg;
-}
+int pipe_tb_max() { return TB_MAX; }
+int pipe_closer_ctas() { return NCL; }
 
-int pipe_max_clusters(int C, size_t smem)
+int pipe_max_ctas(size_t smem)
 {
+    int dev = 0, sms = 0, per = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
     if (cudaFuncSetAttribute(pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess)
         return 0;
-    if (C > 8 &&
-        cudaFuncSetAttribute(pipe_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
-            cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, pipe_kernel, PT, smem) != cudaSuccess)
         return 0;
-    cudaLaunchAttribute attrs[2];
-    cudaLaunchConfig_t cfg = pipe_config(C, C, smem, 0, attrs, false);
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, (void *)pipe_kernel, &cfg) != cudaSuccess) return 0;
-    return n;
+    return per * sms;
 }
 
 cudaError_t launch_pipe(const KArgs &a, const PArgs &pa, int grid, size_t smem, cudaStream_t st)
@@ -1209,17 +1188,10 @@ cudaError_t launch_pipe(const KArgs &a, const PArgs &pa, int grid, size_t smem, 
     cudaError_t e = cudaFuncSetAttribute(pipe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    cudaLaunchAttribute attrs[2];
-    cudaLaunchConfig_t cfg = pipe_config(grid, pa.C, smem, st, attrs, true);
-    e = cudaLaunchKernelEx(&cfg, pipe_kernel, a, pa);
-    if (e != cudaSuccess) {
-        (void)cudaGetLastError();
-        // clusters without the cooperative guarantee: the grid is sized to the
-        // device's active-cluster limit, and every wait is bounded
-        cfg = pipe_config(grid, pa.C, smem, st, attrs, false);
-        e = cudaLaunchKernelEx(&cfg, pipe_kernel, a, pa);
-    }
-    return e;
+    KArgs ca = a;
+    PArgs cpa = pa;
+    void *args[] = {&ca, &cpa};
+    return cudaLaunchCooperativeKernel((const void *)pipe_kernel, dim3(grid), dim3(PT), args, smem, st);
 }
 
 }  // namespace mpt
