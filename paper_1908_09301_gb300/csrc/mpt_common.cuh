@@ -104,15 +104,22 @@ __host__ __device__ __forceinline__ uint32_t mod_inv(uint32_t n, const Divisor &
 // with c_{(qW + k - jW - u) mod M} in column k; chunks j <= q land in block
 // 0 and chunks j > q in block 1 (the limbs that wrap into the zero padding
 // between the two contribute nothing, so the split may be made per chunk).
-// gA = j, gC0 = (q - j) mod (P+1), gC1 = (q - j - 1) mod (P+1) are limb groups.
-__device__ __forceinline__ void chunk_mac(const uint32_t *A, const uint32_t *C, int gA, int gC0,
-                                          int gC1, uint32_t (&c0)[W], uint32_t (&c1)[W],
-                                          uint32_t (&c2)[W])
+// sA, sC are shared-memory addresses of A' and C; gA = j,
+// gC0 = (q - j) mod (P+1), gC1 = (q - j - 1) mod (P+1) are limb groups.
+__device__ __forceinline__ uint4 lds128(unsigned addr)
 {
-    const uint4 *pa = reinterpret_cast<const uint4 *>(A + gA * GS);
-    const uint4 *pb = reinterpret_cast<const uint4 *>(C + gC0 * GS);
-    const uint4 *pn = reinterpret_cast<const uint4 *>(C + gC1 * GS);
-    const uint4 a_lo = pa[0], a_hi = pa[1], b_lo = pb[0], b_hi = pb[1], n_lo = pn[0], n_hi = pn[1];
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(addr));
+    return v;
+}
+__device__ __forceinline__ void chunk_mac(unsigned sA, unsigned sC, int gA, int gC0, int gC1,
+                                          uint32_t (&c0)[W], uint32_t (&c1)[W], uint32_t (&c2)[W])
+{
+    const unsigned pa = sA + gA * GS * 4, pb = sC + gC0 * GS * 4, pn = sC + gC1 * GS * 4;
+    const uint4 a_lo = lds128(pa), a_hi = lds128(pa + 16), b_lo = lds128(pb), b_hi = lds128(pb + 16);
+    const uint4 n_lo = lds128(pn), n_hi = lds128(pn + 16);
     const uint32_t av[W] = {a_lo.x, a_lo.y, a_lo.z, a_lo.w, a_hi.x, a_hi.y, a_hi.z, a_hi.w};
     const uint32_t bw[W] = {b_lo.x, b_lo.y, b_lo.z, b_lo.w, b_hi.x, b_hi.y, b_hi.z, b_hi.w};
     const uint32_t bn[W] = {n_lo.x, n_lo.y, n_lo.z, n_lo.w, n_hi.x, n_hi.y, n_hi.z, n_hi.w};
@@ -124,6 +131,10 @@ __device__ __forceinline__ void chunk_mac(const uint32_t *A, const uint32_t *C, 
             mac_cc(av[u], b, c0[k], c1[k], c2[k]);
         }
     }
+}
+__device__ __forceinline__ unsigned smem_addr(const void *p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
 }
 
 // int64 digit t (t < W+2) of the 96-bit columns (c0, c1, c2)[k]: the column

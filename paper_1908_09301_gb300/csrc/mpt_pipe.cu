@@ -222,13 +222,82 @@ __device__ bool wait_geq(PSmem &S, const KArgs &a, const unsigned *flag, unsigne
 
 // ------------------------------------------------------------------ unit products
 
+// The walk of one thread: share r of Re of unit q's (term, chunk) sequence,
+// in which every term's block-0 chunks (j <= q) come before any block-1 chunk.
+// a = the sums of all its products, x = their block-0 part; strad: the share
+// straddles the block switch; b1only: it lies in block 1.
+__device__ __forceinline__ void unit_walk(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase,
+                                          int s0, int n, int q, int r, int Re, uint32_t (&a0)[W],
+                                          uint32_t (&a1)[W], uint32_t (&a2)[W], uint32_t (&x0)[W],
+                                          uint32_t (&x1)[W], uint32_t (&x2)[W], bool &strad,
+                                          bool &b1only)
+{
+    const int I = n * G.P1;
+    const int i0 = I * r / Re, i1 = I * (r + 1) / Re;
+    const int nA = n * (q + 1);  // block-0 items: chunks 0..q of every term
+    strad = i0 < nA && i1 > nA;
+    b1only = i0 >= nA;
+    const int lenB = G.P - q;    // block-1 chunks per term
+    int t, j, ph;
+    if (i0 < nA) {
+        ph = 0;
+        t = i0 / (q + 1);
+        j = i0 - t * (q + 1);
+    } else {
+        ph = 1;
+        const int ib = i0 - nA;
+        t = ib / lenB;
+        j = q + 1 + ib - t * lenB;
+    }
+    const unsigned sAb = smem_addr(Abase), sCb = smem_addr(Cbase), slot = G.VW * 4;
+    unsigned sA = sAb + (s0 + t) * slot, sC = sCb + (s0 + t) * slot;
+    for (int it = i0; it < i1; it++) {
+        const bool sw = (it == nA);  // first block-1 item: keep the block-0 sums
+        if (__any_sync(__activemask(), sw)) {
+#pragma unroll
+            for (int k = 0; k < W; k++) {
+                x0[k] = sw ? a0[k] : x0[k];
+                x1[k] = sw ? a1[k] : x1[k];
+                x2[k] = sw ? a2[k] : x2[k];
+            }
+        }
+        int gc0 = q - j;
+        if (gc0 < 0) gc0 += G.P1;
+        const int gc1 = gc0 == 0 ? G.P : gc0 - 1;
+        chunk_mac(sA, sC, j, gc0, gc1, a0, a1, a2);
+        // next item, without branches: the end of a term's block-0 run moves to
+        // the next term (or, after the last, to block 1 of the first term); the
+        // end of a block-1 run moves to the next term
+        j++;
+        const bool endA = (ph == 0) & (j > q);
+        const bool endB = (ph != 0) & (j == G.P1);
+        t += (endA | endB) ? 1 : 0;
+        const bool toB = endA & (t == n);
+        j = endB ? q + 1 : (endA ? (toB ? q + 1 : 0) : j);
+        t = toB ? 0 : t;
+        ph = toB ? 1 : ph;
+        const unsigned off = (unsigned)(s0 + t) * slot;
+        sA = sAb + off;
+        sC = sCb + off;
+    }
+    if (i1 <= nA) {
+#pragma unroll
+        for (int k = 0; k < W; k++) {
+            x0[k] = a0[k];
+            x1[k] = a1[k];
+            x2[k] = a2[k];
+        }
+    }
+}
+
 // Sum over the n terms in slots [s0, s0+n) of A'_s * C_s (A'_s = Abase + s VW,
-// C_s = Cbase + s VW), exact, added into win[coff + c], c < 2M+2.  With `tinfo`, slots flagged negative hold the
-// complement of the shifted first factor over its Lp limbs, and the
-// complement's correction
+// C_s = Cbase + s VW), exact, added into win[coff + c], c < 2M+2.  With
+// `tinfo`, slots flagged negative hold the complement of the shifted first
+// factor over its Lp limbs, and the complement's correction
 // (+C 2^(32 d) + ~C 2^(32 (d+Lp)) + 2^(32 (d+Lp)) - 2^(32 (d+2Lp))) is added
 // as well.  neg_all negates the whole sum.  Every thread of the CTA calls
-// this; it starts and ends with __syncthreads.
+// this; it starts and ends with __syncthreads.  For many terms (a worker's
+// batch): R threads per unit, shares summed through shared memory.
 __device__ void group_products(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
                                int n, const int *tinfo, bool neg_all, long long *stage,
                                long long *win, int coff)
@@ -239,74 +308,12 @@ __device__ void group_products(const Geo &G, const uint32_t *Abase, const uint32
     for (int k = 0; k < W; k++) a0[k] = a1[k] = a2[k] = x0[k] = x1[k] = x2[k] = 0u;
     int key = -1;
     bool strad = false, b1only = false;  // share straddles the block switch / lies in block 1
-    // threads per unit
-    const int Re = G.R;
+    const int Re = G.R;  // threads per unit
     __syncthreads();
     if (tid < G.P1 * Re && n > 0) {
         const int q = tid / Re, r = tid - q * Re;
         key = q;
-        const int I = n * G.P1;
-        const int i0 = I * r / Re, i1 = I * (r + 1) / Re;
-        const int nA = n * (q + 1);  // block-0 items: chunks 0..q of every term
-        strad = i0 < nA && i1 > nA;
-        b1only = i0 >= nA;
-        const int lenB = G.P - q;    // block-1 chunks per term
-        int t, j, ph;
-        if (i0 < nA) {
-            ph = 0;
-            t = i0 / (q + 1);
-            j = i0 - t * (q + 1);
-        } else {
-            ph = 1;
-            const int ib = i0 - nA;
-            t = ib / lenB;
-            j = q + 1 + ib - t * lenB;
-        }
-        const uint32_t *Ap = Abase + (size_t)(s0 + t) * G.VW, *Cp = Cbase + (size_t)(s0 + t) * G.VW;
-        for (int it = i0; it < i1; it++) {
-            const bool sw = (it == nA);  // first block-1 item: keep the block-0 sums
-            if (__any_sync(__activemask(), sw)) {
-#pragma unroll
-                for (int k = 0; k < W; k++) {
-                    x0[k] = sw ? a0[k] : x0[k];
-                    x1[k] = sw ? a1[k] : x1[k];
-                    x2[k] = sw ? a2[k] : x2[k];
-                }
-            }
-            int gc0 = q - j;
-            if (gc0 < 0) gc0 += G.P1;
-            const int gc1 = gc0 == 0 ? G.P : gc0 - 1;
-            chunk_mac(Ap, Cp, j, gc0, gc1, a0, a1, a2);
-            j++;
-            bool next = false;
-            if (ph == 0) {
-                if (j > q) {
-                    j = 0;
-                    next = true;
-                    if (++t == n) {
-                        ph = 1;
-                        t = 0;
-                        j = q + 1;
-                    }
-                }
-            } else if (j == G.P1) {
-                j = q + 1;
-                t++;
-                next = true;
-            }
-            if (next) {
-                Ap = Abase + (size_t)(s0 + t) * G.VW;
-                Cp = Cbase + (size_t)(s0 + t) * G.VW;
-            }
-        }
-        if (i1 <= nA) {
-#pragma unroll
-            for (int k = 0; k < W; k++) {
-                x0[k] = a0[k];
-                x1[k] = a1[k];
-                x2[k] = a2[k];
-            }
-        }
+        unit_walk(G, Abase, Cbase, s0, n, q, r, Re, a0, a1, a2, x0, x1, x2, strad, b1only);
     }
     // Each thread's share lies in block 0, in block 1, or straddles the switch
     // once (at most one thread per unit).  A thread stores the digits of its
@@ -379,6 +386,85 @@ __device__ void group_products(const Geo &G, const uint32_t *Abase, const uint32
             }
         }
         if (s) win[coff + c] += neg_all ? -s : s;
+    }
+    __syncthreads();
+}
+
+
+// The same sum for a few terms (a bracket's products, a Horner step): RS = 8
+// threads per unit, always inside one warp, so their shares are summed with
+// three shuffle steps; each unit's first thread stores the unit's digits, and
+// one thread per window column adds them (with the complement corrections).
+// Only the first 8 (P+1) threads walk.  `stage` holds (P+1) 2 (W+2) long
+// longs.  Starts and ends with __syncthreads.
+constexpr int RS = 8;
+__device__ void small_products(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
+                               int n, const int *tinfo, bool neg_all, long long *stage,
+                               long long *win, int coff)
+{
+    constexpr int ND = W + 2;
+    const int tid = threadIdx.x;
+    __syncthreads();
+    if (tid < ((G.P1 * RS + 31) & ~31) && n > 0) {
+        uint32_t a0[W], a1[W], a2[W], x0[W], x1[W], x2[W];
+#pragma unroll
+        for (int k = 0; k < W; k++) a0[k] = a1[k] = a2[k] = x0[k] = x1[k] = x2[k] = 0u;
+        bool strad = false, b1only = false;
+        const int q = tid / RS, r = tid - q * RS;
+        if (q < G.P1) unit_walk(G, Abase, Cbase, s0, n, q, r, RS, a0, a1, a2, x0, x1, x2, strad, b1only);
+        long long v0[ND], v1[ND];
+#pragma unroll
+        for (int t = 0; t < ND; t++) {
+            const long long bx = col_digit(x0, x1, x2, t), ba = col_digit(a0, a1, a2, t);
+            v0[t] = b1only ? 0 : bx;
+            v1[t] = b1only ? ba : (strad ? ba - bx : 0);
+        }
+#pragma unroll
+        for (int off = 1; off < RS; off <<= 1) {
+#pragma unroll
+            for (int t = 0; t < ND; t++) {
+                v0[t] += __shfl_xor_sync(FULL, v0[t], off);
+                v1[t] += __shfl_xor_sync(FULL, v1[t], off);
+            }
+        }
+        if (r == 0 && q < G.P1) {
+            long long *d = stage + (size_t)q * 2 * ND;
+#pragma unroll
+            for (int t = 0; t < ND; t++) {
+                d[t] = v0[t];
+                d[ND + t] = v1[t];
+            }
+        }
+    }
+    __syncthreads();
+    if (n > 0) {
+        for (int c = tid; c < G.GW; c += PT) {
+            long long s = 0;
+            if (c < G.M + 2) {
+                const int u = c / W;
+                if (u <= G.P) s += stage[(u * 2) * ND + c - u * W];
+                if (u >= 1 && c - (u - 1) * W < ND) s += stage[((u - 1) * 2) * ND + c - (u - 1) * W];
+            }
+            const int c1 = c - G.M;
+            if (c1 >= 0) {
+                const int u = c1 / W;
+                if (u <= G.P) s += stage[(u * 2 + 1) * ND + c1 - u * W];
+                if (u >= 1 && c1 - (u - 1) * W < ND) s += stage[((u - 1) * 2 + 1) * ND + c1 - (u - 1) * W];
+            }
+            if (tinfo) {
+                for (int sl = s0; sl < s0 + n; sl++) {
+                    const int *ti = tinfo + sl * TI;
+                    if (!ti[1]) continue;
+                    const int y = c - ti[2];
+                    const uint32_t *Cs = Cbase + (size_t)sl * G.VW;
+                    if (y >= 0 && y < G.Lp) s += Cs[gpos(y)];
+                    else if (y >= G.Lp && y < 2 * G.Lp) s += (uint32_t)~Cs[gpos(y - G.Lp)];
+                    if (y == G.Lp) s += 1;
+                    if (y == 2 * G.Lp) s -= 1;
+                }
+            }
+            if (s) win[coff + c] += neg_all ? -s : s;
+        }
     }
     __syncthreads();
 }
@@ -901,7 +987,7 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
             width = (int)(hi - lo);
         }
         if (prod)
-            group_products(G, hA, tauC, 0, 1, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.stage, win,
+            small_products(G, hA, tauC, 0, 1, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.stage, win,
                            (int)(lpp - lo));
         pr.mark(PR_HMAC);
         if (lone) {
@@ -1043,7 +1129,7 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             const int nrun = S.misc[MS_NRUN];
             for (int rr = 0; rr < nrun; rr++) {
                 const int rs = S.misc[MS_RUN + rr], re = S.misc[MS_RUNE + rr];
-                group_products(G, S.vA, S.vC, rs, re - rs, S.tinfo, false, S.stage, win,
+                small_products(G, S.vA, S.vC, rs, re - rs, S.tinfo, false, S.stage, win,
                                S.tinfo[rs * TI + 3] * W);
             }
             pr.mark(PR_MAC);
