@@ -519,19 +519,19 @@ __device__ void inner_window(const KArgs &a, const long long mid[4], const int *
 __device__ void issue_loads(PSmem &S, const KArgs &a, const Geo &G, int TB, int buf, int m, int tb0,
                             int nb, int mode)
 {
-    const int Lp = G.Lp, q4 = Lp / 4, per = 2 * q4;
-    for (int e = threadIdx.x; e < nb * per; e += PT) {
-        const int sl = e / per, r = e - sl * per;
+    const int Lp = G.Lp, q4 = Lp / 4, lane = threadIdx.x & 31;
+    for (int sl = threadIdx.x >> 5; sl < nb; sl += NWARPS) {  // one warp per slot
         int tg, arow, crow, aa;
         inner_term(m, tb0 + sl, G.N1, tg, arow, crow, aa);
         const bool late = (aa == m - 1) || (aa == 1);
         if ((mode == 1 && late) || (mode == 2 && !late)) continue;
-        if (r < q4) {
-            cp_async16(S.araw + ((size_t)buf * TB + sl) * Lp + 4 * r, a.coefL + (size_t)arow * Lp + 4 * r);
-        } else {
-            const int x4 = r - q4, g = x4 >> 1, h = x4 & 1;
-            cp_async16(S.cc + ((size_t)buf * TB + sl) * G.VW + g * GS + 4 * h,
-                       a.coefL + (size_t)crow * Lp + 8 * g + 4 * h);
+        uint32_t *ar = S.araw + ((size_t)buf * TB + sl) * Lp;
+        uint32_t *cr = S.cc + ((size_t)buf * TB + sl) * G.VW;
+        const uint32_t *ga = a.coefL + (size_t)arow * Lp, *gc = a.coefL + (size_t)crow * Lp;
+        for (int x = lane; x < q4; x += 32) {
+            cp_async16(ar + 4 * x, ga + 4 * x);
+            const int g = x >> 1, h = x & 1;
+            cp_async16(cr + g * GS + 4 * h, gc + 8 * g + 4 * h);
         }
     }
 }
@@ -573,14 +573,14 @@ __device__ void prepare_batch(PSmem &S, const KArgs &a, const Geo &G, int TB, in
         if (lane == 0) S.misc[MS_NRUN] = __popc(Sm);
     }
     __syncthreads();
-    for (int sl = 0; sl < nb; sl++) {
+    for (int sl = threadIdx.x >> 5; sl < nb; sl += NWARPS) {  // one warp per slot
         const int *ti = S.tinfo + sl * TI;
         if (ti[4] < 0) continue;
         const int dl = ti[2];
         const uint32_t inv = ti[1] ? 0xffffffffu : 0u;
         const uint32_t *src = S.araw + ((size_t)buf * TB + sl) * G.Lp;
         uint32_t *dst = S.ash + (size_t)sl * G.VW;
-        for (int x = threadIdx.x; x < G.M; x += PT) {
+        for (int x = threadIdx.x & 31; x < G.M; x += 32) {
             const int y = x - dl;
             dst[gpos(x)] = (y >= 0 && y < G.Lp) ? (src[y] ^ inv) : 0u;
         }
@@ -624,12 +624,13 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 const int idx = threadIdx.x * N1 + m - 1;
                 S.expT[idx] = __ldcg(&a.coefE[idx]);
                 S.flgT[idx] = __ldcg(&a.coefF[idx]);
+            } else if (threadIdx.x >= 32 && threadIdx.x < 36) {
+                ((long long *)(S.misc + MS_BK))[threadIdx.x - 32] = __ldcg(&pa.imid[(size_t)set * 4 + threadIdx.x - 32]);
             }
             __syncthreads();
             if (threadIdx.x == 0) {
-                long long lo[2], hi[2], mid[4];
-                for (int k = 0; k < 4; k++) mid[k] = __ldcg(&pa.imid[(size_t)set * 4 + k]);
-                inner_window(a, mid, S.expT, S.flgT, m, lo, hi);
+                long long lo[2], hi[2];
+                inner_window(a, (const long long *)(S.misc + MS_BK), S.expT, S.flgT, m, lo, hi);
                 for (int tg = 0; tg < 2; tg++) {
                     int width = 0;
                     if (hi[tg] > lo[tg]) {
