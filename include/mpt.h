@@ -166,11 +166,14 @@ int mpt_set_wait_limit(mpt_ctx *ctx, int64_t polls);
 /*
  * Per-phase cycle profile (a device-side stats block; not part of the
  * paper).  With profiling on, every launch accumulates SM clock cycles per
- * phase for the first and the last CTA; mpt_get_profile copies up to n
- * counters (layout: [cta][slot], 16 slots per CTA: 0 window placement,
- * 1 operand staging, 2 limb products, 3 accumulator flush, 4 grid barrier,
- * 5 close (normalise + divide), 6 Horner, 7 Horner products, 8 Horner
- * close, 9 whole launch) of the last launch.  Off by default.
+ * phase; mpt_get_profile copies up to n counters of the last launch.
+ * Layout: rows of 16 slots (0 window placement, 1 operand staging, 2 limb
+ * products, 3 accumulator flush, 4 wait, 5 close (normalise + divide),
+ * 6 Horner, 7 Horner products, 8 Horner close, 9 whole launch, 10-15 finer
+ * marks of the pipelined kernel).  Row 0 is the first CTA (the pipelined
+ * kernel: its beta' bracket CTA), row 1 the last CTA; the pipelined kernel
+ * adds one row per CTA of the launch (row 2 + CTA index), up to 2 + the
+ * device's SM count rows in all.  Off by default.
  */
 int mpt_set_profiling(mpt_ctx *ctx, int on);
 int mpt_get_profile(mpt_ctx *ctx, int64_t *cycles, int n);

@@ -84,9 +84,9 @@ struct mpt_ctx {
     bool pending = false;  // steps queued by mpt_launch, not yet waited for
     long long *prof = nullptr;  // per-phase cycle counters when profiling is on
     long long spin_limit = mpt::DEFAULT_SPIN_LIMIT;
-    // pipelined kernel (closer cluster + workers)
+    // pipelined kernel (bracket and outer-pair CTAs + workers)
     int kind_req = 0;           // 0 auto, 1 lockstep, 2 pipelined
-    int pipe_C = 3;             // bracket CTAs of the pipelined kernel (fixed by the kernel)
+    int pipe_C = 5;             // CTAs with fixed roles in the pipelined kernel (fixed by the kernel)
     int pipe_max_grid = 0;      // co-resident CTAs of the pipelined kernel
     int pipe_tb = 0;
     size_t pipe_smem = 0;
@@ -100,8 +100,11 @@ struct mpt_ctx {
 
 namespace {
 
+// profile counters: the first and the last CTA, then one row per SM
+size_t prof_len(const mpt_ctx *c) { return (size_t)(2 + c->sms) * mpt::PROF_SLOTS; }
+
 // which kernel runs a launch: the pipelined one for large L x N, when the
-// device fits a closer cluster and at least one worker cluster
+// device fits its fixed-role CTAs and at least one worker
 int kind_for(const mpt_ctx *c)
 {
     if (c->kind_req == 1) return 1;
@@ -320,7 +323,7 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
             ptb--;
         c->pipe_tb = ptb;
         c->pipe_smem = mpt::pipe_smem_bytes(L, c->Lp, c->N, c->Wcap, ptb);
-        c->pipe_C = mpt::pipe_closer_ctas();
+        c->pipe_C = mpt::pipe_fixed_ctas();
         c->pipe_max_grid = 0;
         if (c->pipe_smem <= (size_t)smem_optin) {
             c->pipe_max_grid = mpt::pipe_max_ctas(c->pipe_smem);
@@ -344,7 +347,7 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
     if (ce == cudaSuccess) ce = dalloc(&c->status, 1);
     if (ce == cudaSuccess) ce = dalloc(&c->pub, 1);
     if (ce == cudaSuccess) ce = dalloc(&c->done, mpt::PIPE_SETS);
-    if (ce == cudaSuccess) ce = dalloc(&c->gin, (size_t)mpt::PIPE_SETS * 2 * c->Wcap);
+    if (ce == cudaSuccess) ce = dalloc(&c->gin, (size_t)mpt::PIPE_SETS * 4 * c->Wcap);
     if (ce == cudaSuccess) ce = dalloc(&c->imid, (size_t)mpt::PIPE_SETS * 4);
     if (ce != cudaSuccess) {
         free_all(c);
@@ -545,7 +548,7 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
     a.prof = c->prof;
     a.spin_limit = c->spin_limit;
     if (c->prof) {
-        ce = cudaMemsetAsync(c->prof, 0, sizeof(long long) * 2 * mpt::PROF_SLOTS, c->st);
+        ce = cudaMemsetAsync(c->prof, 0, sizeof(long long) * prof_len(c), c->st);
         if (ce != cudaSuccess) return cuda_fail(ce, "profile reset");
     }
     if (kind_for(c) == 2) {
@@ -559,7 +562,7 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
         ce = cudaMemsetAsync(c->pub, 0, sizeof(unsigned), c->st);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(c->done, 0, sizeof(unsigned) * mpt::PIPE_SETS, c->st);
         if (ce == cudaSuccess)
-            ce = cudaMemsetAsync(c->gin, 0, sizeof(long long) * mpt::PIPE_SETS * 2 * c->Wcap, c->st);
+            ce = cudaMemsetAsync(c->gin, 0, sizeof(long long) * mpt::PIPE_SETS * 4 * c->Wcap, c->st);
         if (ce == cudaSuccess) ce = mpt::launch_pipe(a, pa, pipe_grid_for(c), c->pipe_smem, c->st);
     } else {
         ce = mpt::launch_integrate(a, grid_for(c), c->smem, c->st);
@@ -643,8 +646,8 @@ int mpt_set_profiling(mpt_ctx *c, int on)
     if (!c) return fail(MPT_EINVAL, "null context");
     DeviceGuard g(c->dev);
     if (on && !c->prof) {
-        cudaError_t ce = dalloc(&c->prof, 2 * mpt::PROF_SLOTS);
-        if (ce == cudaSuccess) ce = cudaMemset(c->prof, 0, sizeof(long long) * 2 * mpt::PROF_SLOTS);
+        cudaError_t ce = dalloc(&c->prof, prof_len(c));
+        if (ce == cudaSuccess) ce = cudaMemset(c->prof, 0, sizeof(long long) * prof_len(c));
         if (ce != cudaSuccess) return cuda_fail(ce, "profile buffer");
     } else if (!on && c->prof) {
         cudaStreamSynchronize(c->st);
@@ -659,11 +662,13 @@ int mpt_get_profile(mpt_ctx *c, int64_t *cycles, int n)
     if (!c || !cycles) return fail(MPT_EINVAL, "null argument");
     if (!c->prof) return fail(MPT_EINVAL, "profiling is off");
     DeviceGuard g(c->dev);
-    long long h[2 * mpt::PROF_SLOTS];
-    cudaError_t ce = cudaMemcpyAsync(h, c->prof, sizeof h, cudaMemcpyDeviceToHost, c->st);
+    const size_t len = prof_len(c);
+    std::vector<long long> h(len);
+    cudaError_t ce = cudaMemcpyAsync(h.data(), c->prof, sizeof(long long) * len,
+                                     cudaMemcpyDeviceToHost, c->st);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
     if (ce != cudaSuccess) return cuda_fail(ce, "profile download");
-    for (int i = 0; i < n && i < 2 * mpt::PROF_SLOTS; i++) cycles[i] = h[i];
+    for (int i = 0; i < n && (size_t)i < len; i++) cycles[i] = h[i];
     return MPT_OK;
 }
 

@@ -68,21 +68,23 @@ enum ProfSlot {
     PROF_SLOTS = 16
 };
 
-// pipelined kernel: closer cluster + workers
+// pipelined kernel: bracket CTAs, outer-pair CTAs and workers
 constexpr int PIPE_SETS = 8;  // rotating global accumulator sets / completion counters
 
 struct PArgs {
     unsigned *pub;    // [1] component publications of the launch (monotone, 3 per coefficient)
-    unsigned *done;   // [PIPE_SETS] workers finished with an index (monotone)
-    long long *gin;   // [PIPE_SETS][2][Wcap] inner Cauchy sums (targets beta', gamma')
-    long long *imid;  // [PIPE_SETS][4] inner-sum windows without the two newest pairs
-    int C;            // bracket CTAs (pipe_closer_ctas())
+    unsigned *done;   // [PIPE_SETS] non-bracket CTAs finished with an index (monotone)
+    long long *gin;   // [PIPE_SETS][2 targets][2 parts][Wcap] Cauchy sums (targets beta',
+                      // gamma'; parts: middle pairs, outer pairs)
+    long long *imid;  // [PIPE_SETS][4] middle-pair windows without their two newest pairs
+    int C;            // CTAs with fixed roles (pipe_fixed_ctas())
     int tb;           // worker term slots per batch (<= pipe_tb_max())
 };
 
 size_t pipe_smem_bytes(int L, int Lp, int N, int Wcap, int tb);
 int pipe_tb_max();
-int pipe_closer_ctas();
+// CTAs with fixed roles (brackets, outer pairs); a launch needs at least one more
+int pipe_fixed_ctas();
 // co-resident CTAs of the pipelined kernel (one per SM at most; 0 on error)
 int pipe_max_ctas(size_t smem);
 cudaError_t launch_pipe(const KArgs &a, const PArgs &pa, int grid, size_t smem, cudaStream_t st);

@@ -1,28 +1,33 @@
 // mpt_pipe.cu -- pipelined multiple-precision Taylor step (Sec. 2 of Dimova
 // et al., arXiv 1908.09301) for large L x N: one persistent cooperative
-// launch, one CTA per SM, two roles.
+// launch, one CTA per SM, three roles.  Eq. (3)'s Cauchy sums of index m,
+//     Y_m = -sum_{a=1}^{m-1} alpha_a gamma_{m-a},  Z_m = sum_{a=1}^{m-1} alpha_a beta_{m-a},
+// are split by the newest coefficient they need, so that each part starts as
+// early as it can:
 //
-//  * Workers (every CTA but the first three) compute the inner part of
-//    Eq. (3)'s Cauchy sums of index m,
-//        Y_m = -sum_{a=1}^{m-1} alpha_a gamma_{m-a},  Z_m = sum_{a=1}^{m-1} alpha_a beta_{m-a},
-//    which needs coefficients up to m-1 only, while the bracket CTAs are
-//    still finishing coefficient m.  A worker takes a contiguous range of the
-//    2(m-1) terms.  All of its terms of one target are summed in one frame:
-//    a term whose lowest limb lies d = 8 d_hi + d_lo limbs above the window
-//    base has its first factor staged shifted up by d_lo limbs (and
-//    complemented when the term is negative; the complement's correction is
-//    added separately), so the terms with equal d_hi share columns and are
-//    accumulated in the same registers.  The CTA's window is added into a
-//    global window set and the worker counts itself done.
+//  * Workers (CTAs 5 and up) take the middle pairs a = 2..m-2, which need
+//    coefficients up to m-2 only, so they run while the bracket CTAs are
+//    still finishing coefficients m-1 and m.  A worker takes a contiguous
+//    range of the 2(m-3) terms.  All of its terms of one target are summed in
+//    one frame: a term whose lowest limb lies d = 8 d_hi + d_lo limbs above
+//    the window base has its first factor staged shifted up by d_lo limbs
+//    (and complemented when the term is negative; the complement's
+//    correction is added separately), so the terms with equal d_hi share
+//    columns and are accumulated in the same registers.
+//  * The outer-pair CTAs 3 (target Y) and 4 (target Z) take the pairs a = 1
+//    and a = m-1 as soon as coefficient m-1 is out.
 //  * The bracket CTAs 0, 1, 2 own Eq. (3)'s brackets alpha', beta', gamma'.
 //    Each forms its products of the newest coefficient m with numbers fixed
 //    for the step (beta': alpha_m gamma_0, gamma_m alpha_0; gamma':
 //    alpha_m beta_0, beta_m alpha_0, gamma_m b) as one term group, adds its
-//    one-limb and lone terms and the workers' inner sums, normalises,
-//    divides by (m+1) and publishes its component of coefficient m+1; the
-//    three exchange components through global memory.  After index N-1 each
-//    runs the Horner chain of Eq. (2) for its component,
+//    one-limb and lone terms and the other CTAs' sums, normalises, divides by
+//    (m+1) and publishes its component of coefficient m+1; the three
+//    exchange components through global memory.  After index N-1 each runs
+//    the Horner chain of Eq. (2) for its component,
 //    h_i = trunc_L(tau h_{i+1} + c_i).
+//
+// Workers and outer-pair CTAs add their windows into a global window set
+// (one part each) and count themselves done.
 //
 // Limb products use units: unit q of a product A' * C (A' of M = (P+1)W
 // limbs, C of Lp limbs) owns columns qW..qW+W-1 of two blocks (block 1 is M
@@ -47,9 +52,11 @@ namespace mpt {
 namespace {
 
 constexpr int NCL = 3;           // bracket CTAs
-constexpr int NA = 4;            // A' slots of a bracket CTA: 3 product terms, Horner's h
-constexpr int NC = 4;            // C slots: 3 fixed factors, tau
+constexpr int NOUT = 2;          // outer-pair CTAs (one per target: beta', gamma')
+constexpr int NFIX = NCL + NOUT; // CTAs with fixed roles; workers follow
 constexpr int NTERM = 3;         // product terms of a bracket
+constexpr int NA = NTERM + 1;    // A' slots of a bracket CTA: product terms, Horner's h
+constexpr int NC = NTERM + 1;    // C slots: fixed factors, tau
 constexpr int TI = 8;            // ints of term info per slot
 constexpr int TB_MAX = 32;       // worker slots per batch (one warp finds the groups)
 
@@ -61,32 +68,34 @@ enum {
     MS_NEWE = 2,    // [2] exponent and flags of this CTA's newest number
     MS_PSCAL = 8,   // [3][2] sigma, R, b: single non-zero limb index (or -1), value
     MS_WLO = 16,    // [4] long long window bases (ints 16..23)
-    MS_WID = 24,    // [4] window widths (workers); bracket CTAs: [4] long long inner-window
+    MS_WID = 24,    // [4] window widths (workers); bracket CTAs: [4] long long workers-window
                     // table of the next index (ints 24..31, MS_IMID)
     MS_IMID = 24,
-    MS_BK = 32,     // [32] bracket setup (ints 32..63)
-    MS_RED = 64,    // [RED_LL] long long scratch of the block routines (ints 64..255)
-    MS_RUN = 256,   // [TB_MAX] group starts
-    MS_RUNE = 288,  // [TB_MAX] group ends
-    MS_PROF = 320,  // [PROF_SLOTS] long long (ints 320..351)
-    MISC_INTS = 352
+    MS_BK = 32,     // [48] bracket setup (ints 32..79)
+    MS_RED = 80,    // [RED_LL] long long scratch of the block routines (ints 80..271)
+    MS_RUN = 272,   // [TB_MAX] group starts
+    MS_RUNE = 304,  // [TB_MAX] group ends
+    MS_PROF = 336,  // [PROF_SLOTS] long long (ints 336..367)
+    MISC_INTS = 368
 };
 
-// bracket setup (ints at MS_BK): lo (long long), width, simple parts, terms, inner sums
+// bracket setup (ints at MS_BK): lo (long long), width, simple parts, terms, the workers' sums
 enum {
     BK_LO = 0,      // long long (2 ints)
     BK_WIDTH = 2,
     BK_NSIMPLE = 3,
     BK_SIMPLE = 4,  // [2][4]: kind (1 lone, 2 scaled), neg, offset, component
     BK_SV = 12,     // [2] scaled: the parameter's limb
-    BK_INNER = 14,  // offset of the inner sums (or -1)
+    BK_INNER = 14,  // offset of the workers' sums (or -1)
     BK_IWIDTH = 15,
     BK_TERM = 16,   // [NTERM][4]: present, component of A, neg, d
+    BK_OINNER = 28, // offset of the outer-pair sums (or -1)
+    BK_OWIDTH = 29,
 };
 
 // Geometry of the unit walk (host and device)
 struct Geo {
-    int L, Lp, P, P1, M, VW, R, WW, GW, N1;
+    int L, Lp, P, P1, M, VW, R, RS, WW, GW, N1;
     __host__ __device__ Geo(int L_, int Lp_, int N, int Wcap)
     {
         L = L_;
@@ -97,6 +106,8 @@ struct Geo {
         VW = vwords(M);
         R = PT / P1;
         if (R < 1) R = 1;
+        RS = 8;   // lanes per unit of the few-term products: a power of two, units within warps
+        while (RS > 1 && RS * P1 > PT) RS >>= 1;
         WW = Wcap + 4 * W;
         GW = 2 * M + 2;
         N1 = N + 1;
@@ -107,14 +118,15 @@ struct PSmem {
     int *expT, *flgT;  // [3][N+1]
     int *misc;         // [MISC_INTS]
     int *tinfo;        // [TB_MAX][TI] term info
-    long long *stage;  // [P1 (R + 3)][W+2] unit digit sums
     long long *win;    // [2][WW] windows
     uint32_t *dig;     // [WW] normalised digits
     // workers
+    long long *stage;  // [P1 (R + 3)][W+2] unit digit sums
     uint32_t *araw;    // [2][TB][Lp] first factors as loaded
     uint32_t *cc;      // [2][TB][VW] second factors (cyclic, zero above Lp)
     uint32_t *ash;     // [TB][VW] first factors shifted / complemented
     // bracket CTAs (same bytes as the workers' part)
+    long long *bstage; // [P1 2][W+2] unit digit sums of the few-term products
     uint32_t *vA;      // [NA][VW]
     uint32_t *vC;      // [NC][VW]
     uint32_t *raw;     // [3][Lp] limbs of the current coefficient; [2] also Horner's h
@@ -141,13 +153,13 @@ __host__ __device__ inline size_t pipe_layout(const Geo &G, int N, int TB, PSmem
     if (S) S->misc = (int *)p;
     p = take(sizeof(int) * TB_MAX * TI);
     if (S) S->tinfo = (int *)p;
-    p = take(sizeof(long long) * (size_t)G.P1 * (G.R + 3) * (W + 2));
-    if (S) S->stage = (long long *)p;
     p = take(sizeof(long long) * 2 * (size_t)G.WW);
     if (S) S->win = (long long *)p;
     p = take(sizeof(uint32_t) * (size_t)G.WW);
     if (S) S->dig = (uint32_t *)p;
     const size_t u0 = o;
+    p = take(sizeof(long long) * (size_t)G.P1 * (G.R + 3) * (W + 2));
+    if (S) S->stage = (long long *)p;
     p = take(sizeof(uint32_t) * 2 * (size_t)TB * G.Lp);
     if (S) S->araw = (uint32_t *)p;
     p = take(sizeof(uint32_t) * 2 * (size_t)TB * G.VW);
@@ -156,6 +168,8 @@ __host__ __device__ inline size_t pipe_layout(const Geo &G, int N, int TB, PSmem
     if (S) S->ash = (uint32_t *)p;
     const size_t worker_end = o;
     o = u0;
+    p = take(sizeof(long long) * (size_t)G.P1 * 2 * (W + 2));
+    if (S) S->bstage = (long long *)p;
     p = take(sizeof(uint32_t) * NA * (size_t)G.VW);
     if (S) S->vA = (uint32_t *)p;
     p = take(sizeof(uint32_t) * NC * (size_t)G.VW);
@@ -391,19 +405,19 @@ __device__ void group_products(const Geo &G, const uint32_t *Abase, const uint32
 }
 
 
-// The same sum for a few terms (a bracket's products, a Horner step): RS = 8
-// threads per unit, always inside one warp, so their shares are summed with
-// three shuffle steps; each unit's first thread stores the unit's digits, and
-// one thread per window column adds them (with the complement corrections).
-// Only the first 8 (P+1) threads walk.  `stage` holds (P+1) 2 (W+2) long
-// longs.  Starts and ends with __syncthreads.
-constexpr int RS = 8;
+// The same sum for a few terms (a bracket's products, a Horner step): G.RS
+// threads per unit (a power of two, at most 8, with RS (P+1) <= PT), always
+// inside one warp, so their shares are summed with log2(RS) shuffle steps;
+// each unit's first thread stores the unit's digits, and one thread per
+// window column adds them (with the complement corrections).  Only the first
+// RS (P+1) threads walk.  `stage` holds (P+1) 2 (W+2) long longs.  Starts and
+// ends with __syncthreads.
 __device__ void small_products(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
                                int n, const int *tinfo, bool neg_all, long long *stage,
                                long long *win, int coff)
 {
     constexpr int ND = W + 2;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, RS = G.RS;
     __syncthreads();
     if (tid < ((G.P1 * RS + 31) & ~31) && n > 0) {
         uint32_t a0[W], a1[W], a2[W], x0[W], x1[W], x2[W];
@@ -471,26 +485,32 @@ __device__ void small_products(const Geo &G, const uint32_t *Abase, const uint32
 
 // ------------------------------------------------------------------ workers
 
-// term t of index m: Y (tg 0) for t < m-1 with a = t+1 and second factor
-// gamma_{m-a}; Z (tg 1) after, a = t-(m-1)+1, beta_{m-a}.  Rows of coefL.
-__device__ __forceinline__ void inner_term(int m, int t, int N1, int &tg, int &arow, int &crow,
-                                           int &a)
+// Term t of index m for a CTA of role `role`.  Role 0, the workers: the
+// middle pairs a = 2..m-2 of the Cauchy sums (coefficients up to m-2),
+// 2(m-3) terms; Y (tg 0) for t < m-3 with a = t+2 and second factor
+// gamma_{m-a}, Z (tg 1) after, a = t-(m-3)+2, beta_{m-a}.  Role 1 + tg, the
+// outer-pair CTA of target tg: the pairs a = 1 and a = m-1 (coefficients up
+// to m-1), one term when m = 2, else two.  Rows of coefL.
+__device__ __forceinline__ void inner_term(int role, int m, int t, int N1, int &tg, int &arow,
+                                           int &crow, int &a)
 {
-    if (t < m - 1) {
+    if (role != 0) {
+        tg = role - 1;
+        a = t == 0 ? 1 : m - 1;
+    } else if (t < m - 3) {
         tg = 0;
-        a = t + 1;
-        crow = 2 * N1 + (m - a);
+        a = t + 2;
     } else {
         tg = 1;
-        a = t - (m - 1) + 1;
-        crow = N1 + (m - a);
+        a = t - (m - 3) + 2;
     }
+    crow = (tg == 0 ? 2 : 1) * N1 + (m - a);
     arow = a;
 }
 
-// Window of the inner sums of index m (targets Y, Z): the pairs a = 2..m-2
-// come from the table the closer filled one period earlier, the two extreme
-// pairs (a = 1 and a = m-1, which involve coefficient m-1) are added here.
+// Window of the workers' part of index m (targets Y, Z): the pairs
+// a = 3..m-3 come from the table filled with coefficient m-2's publication,
+// the pairs a = 2 and a = m-2 (which involve coefficient m-2) are added here.
 __device__ void inner_window(const KArgs &a, const long long mid[4], const int *expT,
                              const int *flgT, int m, long long lo[2], long long hi[2])
 {
@@ -499,8 +519,8 @@ __device__ void inner_window(const KArgs &a, const long long mid[4], const int *
     hi[0] = mid[1];
     lo[1] = mid[2];
     hi[1] = mid[3];
-    const int ends[2] = {1, m - 1};
-    for (int e = 0; e < (m - 1 == 1 ? 1 : 2); e++) {
+    const int ends[2] = {2, m - 2};
+    for (int e = 0; e < (m - 2 == 2 ? 1 : 2); e++) {
         const int aa = ends[e];
         for (int tg = 0; tg < 2; tg++) {
             const int crow = (tg == 0 ? 2 : 1) * N1 + (m - aa);
@@ -512,18 +532,37 @@ __device__ void inner_window(const KArgs &a, const long long mid[4], const int *
     }
 }
 
+// Window of the outer pairs a = 1 and a = m-1 of index m >= 2 for target tg
+// (0: Y, second factors gamma; 1: Z, beta); empty: lo > hi.
+__device__ void outer_window(const KArgs &a, const int *expT, const int *flgT, int m, int tg,
+                             long long &lo, long long &hi)
+{
+    const int N1 = a.N + 1;
+    lo = LLONG_MAX;
+    hi = LLONG_MIN;
+    const int ends[2] = {1, m - 1};
+    for (int e = 0; e < (m - 1 == 1 ? 1 : 2); e++) {
+        const int aa = ends[e];
+        const int crow = (tg == 0 ? 2 : 1) * N1 + (m - aa);
+        if (!(flgT[aa] & F_NZ) || !(flgT[crow] & F_NZ)) continue;
+        const long long lp = (long long)expT[aa] + expT[crow] - 2LL * a.L;
+        lo = min(lo, lp);
+        hi = max(hi, lp + 2LL * a.Lp + 2);
+    }
+}
+
 // cp.async the factors of slots [0, nb) of the batch (m, tb0) into buffer
 // buf, 16 bytes a copy (the first factor plain, the second into its cyclic
 // layout: a group of W limbs is two 16-byte pieces); mode 0 every slot, 1 all
-// but the late ones, 2 only the late ones (late: a factor is coefficient m-1)
-__device__ void issue_loads(PSmem &S, const KArgs &a, const Geo &G, int TB, int buf, int m, int tb0,
-                            int nb, int mode)
+// but the late ones, 2 only the late ones (late: a factor is coefficient m-2)
+__device__ void issue_loads(PSmem &S, const KArgs &a, const Geo &G, int TB, int buf, int role, int m,
+                            int tb0, int nb, int mode)
 {
     const int Lp = G.Lp, q4 = Lp / 4, lane = threadIdx.x & 31;
     for (int sl = threadIdx.x >> 5; sl < nb; sl += NWARPS) {  // one warp per slot
         int tg, arow, crow, aa;
-        inner_term(m, tb0 + sl, G.N1, tg, arow, crow, aa);
-        const bool late = (aa == m - 1) || (aa == 1);
+        inner_term(role, m, tb0 + sl, G.N1, tg, arow, crow, aa);
+        const bool late = (aa == m - 2) || (aa == 2);
         if ((mode == 1 && late) || (mode == 2 && !late)) continue;
         uint32_t *ar = S.araw + ((size_t)buf * TB + sl) * Lp;
         uint32_t *cr = S.cc + ((size_t)buf * TB + sl) * G.VW;
@@ -538,8 +577,8 @@ __device__ void issue_loads(PSmem &S, const KArgs &a, const Geo &G, int TB, int 
 
 // term info (warp 0), staged first factors and term groups of the batch in
 // buffer buf
-__device__ void prepare_batch(PSmem &S, const KArgs &a, const Geo &G, int TB, int buf, int m,
-                              int tb0, int nb)
+__device__ void prepare_batch(PSmem &S, const KArgs &a, const Geo &G, int TB, int buf, int role,
+                              int m, int tb0, int nb)
 {
     (void)a;
     if (threadIdx.x < 32) {
@@ -548,7 +587,7 @@ __device__ void prepare_batch(PSmem &S, const KArgs &a, const Geo &G, int TB, in
         int key = -1;
         if (lane < nb) {
             int tg, arow, crow, aa;
-            inner_term(m, tb0 + lane, G.N1, tg, arow, crow, aa);
+            inner_term(role, m, tb0 + lane, G.N1, tg, arow, crow, aa);
             const int fa = S.flgT[arow], fc = S.flgT[crow];
             const int neg = (tg == 0 ? 1 : 0) ^ (((fa ^ fc) & F_NEG) ? 1 : 0);
             int d = 0;
@@ -588,12 +627,16 @@ __device__ void prepare_batch(PSmem &S, const KArgs &a, const Geo &G, int TB, in
     __syncthreads();
 }
 
+// Workers (role 0) and outer-pair CTAs (role 1 + target).
 __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &G)
 {
     const int N1 = G.N1, Lp = G.Lp, TB = pa.tb;
-    const int nw = gridDim.x - NCL;
-    const int w = blockIdx.x - NCL;
-    const bool prof_on = (blockIdx.x == gridDim.x - 1);
+    const int role = blockIdx.x < (unsigned)NFIX ? 1 + (int)blockIdx.x - NCL : 0;
+    const int nw = gridDim.x - NFIX;
+    const int w = blockIdx.x - NFIX;
+    // index m waits for coefficient m-2 (workers) or m-1 (outer pairs)
+    const int lag = role ? 1 : 2;
+    const bool prof_on = true;
     // zero padding of the second factors stays zero; windows start empty
     for (int e = threadIdx.x; e < 2 * TB * G.M; e += PT) {
         const int s = e / G.M, x = e - s * G.M;
@@ -610,27 +653,34 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
         for (int m = 0; m < a.N; m++) {
             const long long g = step * a.N + m;
             const int set = (int)(g % PIPE_SETS);
-            if (m < 2) {  // no inner terms; keep the completion counts uniform
+            if (m < (role ? 2 : 4)) {  // no pairs; keep the completion counts uniform
                 if (threadIdx.x == 0) atomicAdd(&pa.done[set], 1u);
                 continue;
             }
             Prof pr(a, prof_on, S.misc);
-            if (!wait_geq(S, a, pa.pub, (unsigned)(3 * (step * N1 + m)))) {
+            if (!wait_geq(S, a, pa.pub, (unsigned)(3 * (step * N1 + m + 1 - lag)))) {
                 cp_async_wait<0>();
                 return;
             }
             pr.mark(PR_BARRIER);
             if (threadIdx.x < 3) {
-                const int idx = threadIdx.x * N1 + m - 1;
+                const int idx = threadIdx.x * N1 + m - lag;
                 S.expT[idx] = __ldcg(&a.coefE[idx]);
                 S.flgT[idx] = __ldcg(&a.coefF[idx]);
-            } else if (threadIdx.x >= 32 && threadIdx.x < 36) {
+            } else if (role == 0 && threadIdx.x >= 32 && threadIdx.x < 36) {
                 ((long long *)(S.misc + MS_BK))[threadIdx.x - 32] = __ldcg(&pa.imid[(size_t)set * 4 + threadIdx.x - 32]);
             }
             __syncthreads();
             if (threadIdx.x == 0) {
                 long long lo[2], hi[2];
-                inner_window(a, (const long long *)(S.misc + MS_BK), S.expT, S.flgT, m, lo, hi);
+                if (role == 0) {
+                    inner_window(a, (const long long *)(S.misc + MS_BK), S.expT, S.flgT, m, lo, hi);
+                } else {
+                    const int tg = role - 1;
+                    outer_window(a, S.expT, S.flgT, m, tg, lo[tg], hi[tg]);
+                    lo[1 - tg] = 0;
+                    hi[1 - tg] = 0;
+                }
                 for (int tg = 0; tg < 2; tg++) {
                     int width = 0;
                     if (hi[tg] > lo[tg]) {
@@ -651,14 +701,18 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 cp_async_wait<0>();
                 return;
             }
-            const int T = 2 * (m - 1);
-            const int tA = (int)((long long)T * w / nw), tB = (int)((long long)T * (w + 1) / nw);
+            int tA = 0, tB = m == 2 ? 1 : 2;  // outer pairs: all of them
+            if (role == 0) {
+                const int T = 2 * (m - 3);
+                tA = (int)((long long)T * w / nw);
+                tB = (int)((long long)T * (w + 1) / nw);
+            }
             for (int tb0 = tA; tb0 < tB; tb0 += TB) {
                 const int nb = min(TB, tB - tb0);
                 const int buf = bcount & 1;
                 const bool was_pf = pf && pf_step == step && pf_m == m && pf_tb0 == tb0;
-                if (!was_pf) issue_loads(S, a, G, TB, buf, m, tb0, nb, 0);
-                else if (pf_late) issue_loads(S, a, G, TB, buf, m, tb0, nb, 2);
+                if (!was_pf) issue_loads(S, a, G, TB, buf, role, m, tb0, nb, 0);
+                else if (pf_late) issue_loads(S, a, G, TB, buf, role, m, tb0, nb, 2);
                 cp_async_commit();
                 // prefetch the next batch: the rest of this index, or the first
                 // batch of index m+1 without its late terms
@@ -669,9 +723,9 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                     pf_step = step;
                     pf_m = m;
                     pf_tb0 = tb0 + TB;
-                    issue_loads(S, a, G, TB, buf ^ 1, m, pf_tb0, min(TB, tB - pf_tb0), 0);
-                } else if (m + 1 < a.N) {
-                    const int T2 = 2 * m;
+                    issue_loads(S, a, G, TB, buf ^ 1, role, m, pf_tb0, min(TB, tB - pf_tb0), 0);
+                } else if (role == 0 && m + 1 < a.N) {
+                    const int T2 = 2 * (m - 2);
                     const int tA2 = (int)((long long)T2 * w / nw), tB2 = (int)((long long)T2 * (w + 1) / nw);
                     if (tB2 > tA2) {
                         pf = true;
@@ -679,7 +733,7 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                         pf_step = step;
                         pf_m = m + 1;
                         pf_tb0 = tA2;
-                        issue_loads(S, a, G, TB, buf ^ 1, m + 1, tA2, min(TB, tB2 - tA2), 1);
+                        issue_loads(S, a, G, TB, buf ^ 1, role, m + 1, tA2, min(TB, tB2 - tA2), 1);
                     }
                 }
                 cp_async_commit();
@@ -687,7 +741,7 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 cp_async_wait<1>();
                 __syncthreads();
                 pr.mark(PR_STAGE);
-                prepare_batch(S, a, G, TB, buf, m, tb0, nb);
+                prepare_batch(S, a, G, TB, buf, role, m, tb0, nb);
                 pr.mark(PR_FLUSH);
                 const int nrun = S.misc[MS_NRUN];
                 for (int rr = 0; rr < nrun; rr++) {
@@ -703,7 +757,7 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             for (int tg = 0; tg < 2; tg++) {
                 const int wd = S.misc[MS_WID + tg];
                 long long *src = S.win + (size_t)tg * G.WW;
-                long long *dst = pa.gin + ((size_t)set * 2 + tg) * a.Wcap;
+                long long *dst = pa.gin + (((size_t)set * 2 + tg) * 2 + (role ? 1 : 0)) * a.Wcap;
                 for (int c = threadIdx.x; c < wd; c += PT) {
                     const long long v = src[c];
                     if (v) {
@@ -733,8 +787,9 @@ __device__ __forceinline__ void to_slot(uint32_t *dst, const uint32_t *src, int 
 
 // Setup of bracket c at index m (thread 0): the simple parts (a lone number,
 // a number times a one-limb parameter), the product terms (a component of
-// coefficient m times the fixed number in C slot k) and the inner sums; the
-// window (base, width) and each part's offset in it; the term groups.
+// coefficient m, or of m-1 for the outer pairs, times the fixed number in C
+// slot k) and the workers' middle sums; the window (base, width) and each
+// part's offset in it; the term groups.
 // Returns false (status set) when the window is wider than Wcap.
 __device__ bool bracket_setup(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &G, int c, int m,
                               int set)
@@ -750,8 +805,8 @@ __device__ bool bracket_setup(PSmem &S, const KArgs &a, const PArgs &pa, const G
     int sk[2] = {0, 0}, sneg[2] = {0, 0}, scomp[2] = {0, 0};
     uint32_t sv[2] = {0u, 0u};
     long long slp[2] = {0, 0};
-    int tp[NTERM] = {0, 0, 0}, tcomp[NTERM] = {0, 0, 0}, tneg[NTERM] = {0, 0, 0};
-    long long tlp[NTERM] = {0, 0, 0};
+    int tp[NTERM] = {}, tcomp[NTERM] = {}, tneg[NTERM] = {};
+    long long tlp[NTERM] = {};
     int ns = 0;
     // parameter p times component comp of coefficient m (exponent e, flags f)
     auto param = [&](int p, int comp, int e, int f, int neg, int tslot) {
@@ -810,8 +865,9 @@ __device__ bool bracket_setup(PSmem &S, const KArgs &a, const PArgs &pa, const G
             lo = min(lo, tlp[k]);
             hi = max(hi, tlp[k] + 2LL * Lp + 2);
         }
-    long long ilo = 0, ihi = 0;
-    if (c > 0 && m >= 2) {
+    // the middle pairs (workers) and the outer pairs (outer-pair CTAs)
+    long long ilo = 0, ihi = 0, olo = 0, ohi = 0;
+    if (c > 0 && m >= 4) {
         long long l2[2], h2[2];
         inner_window(a, (const long long *)(S.misc + MS_IMID), S.expT, S.flgT, m, l2, h2);
         ilo = l2[c - 1];
@@ -819,6 +875,13 @@ __device__ bool bracket_setup(PSmem &S, const KArgs &a, const PArgs &pa, const G
         if (ihi > ilo) {
             lo = min(lo, ilo);
             hi = max(hi, ihi);
+        }
+    }
+    if (c > 0 && m >= 2) {
+        outer_window(a, S.expT, S.flgT, m, c - 1, olo, ohi);
+        if (ohi > olo) {
+            lo = min(lo, olo);
+            hi = max(hi, ohi);
         }
     }
     int width = 0;
@@ -841,9 +904,12 @@ __device__ bool bracket_setup(PSmem &S, const KArgs &a, const PArgs &pa, const G
         bk[BK_SIMPLE + 4 * k + 3] = scomp[k];
         bk[BK_SV + k] = (int)sv[k];
     }
-    const bool inner = c > 0 && m >= 2 && ihi > ilo;
+    const bool inner = c > 0 && m >= 4 && ihi > ilo;
     bk[BK_INNER] = inner ? (int)(ilo - lo) : -1;
     bk[BK_IWIDTH] = inner ? (int)(ihi - ilo) : 0;
+    const bool outer = c > 0 && m >= 2 && ohi > olo;
+    bk[BK_OINNER] = outer ? (int)(olo - lo) : -1;
+    bk[BK_OWIDTH] = outer ? (int)(ohi - olo) : 0;
     int nrun = 0, prev_dhi = -1;
     for (int k = 0; k < NTERM; k++) {
         const int d = tp[k] ? (int)(tlp[k] - lo) : 0;
@@ -938,8 +1004,8 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
                                  Prof &pr)
 {
     const int N1 = G.N1, Lp = G.Lp, L = G.L;
-    uint32_t *hA = S.vA + 3 * (size_t)G.VW;        // h as first factor (slot 3)
-    const uint32_t *tauC = S.vC + 3 * (size_t)G.VW; // tau (slot 3)
+    uint32_t *hA = S.vA + NTERM * (size_t)G.VW;        // h as first factor (last slot)
+    const uint32_t *tauC = S.vC + NTERM * (size_t)G.VW; // tau (last slot)
     uint32_t *hp = S.raw + 2 * (size_t)Lp;     // h, plain limbs
     long long *win = S.win;
     const int tauE = __ldg(&a.parE[P_TAU]), tauF = __ldg(&a.parF[P_TAU]);
@@ -988,7 +1054,7 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
             width = (int)(hi - lo);
         }
         if (prod)
-            small_products(G, hA, tauC, 0, 1, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.stage, win,
+            small_products(G, hA, tauC, 0, 1, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.bstage, win,
                            (int)(lpp - lo));
         pr.mark(PR_HMAC);
         if (lone) {
@@ -1039,7 +1105,7 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
 {
     const int c = blockIdx.x;
     const int N1 = G.N1, Lp = G.Lp;
-    const bool prof_on = (c == 1);
+    const bool prof_on = true;
     for (int e = threadIdx.x; e < NA * G.VW; e += PT) S.vA[e] = 0u;
     for (int e = threadIdx.x; e < NC * G.VW; e += PT) S.vC[e] = 0u;
     for (int e = threadIdx.x; e < 3 * Lp; e += PT) S.raw[e] = 0u;
@@ -1069,7 +1135,7 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
     }
     if (c == 1) to_slot(S.vC + 2 * (size_t)G.VW, a.parL + (size_t)P_R * Lp, Lp);
     if (c == 2) to_slot(S.vC + 2 * (size_t)G.VW, a.parL + (size_t)P_B * Lp, Lp);
-    to_slot(S.vC + 3 * (size_t)G.VW, a.parL + (size_t)P_TAU * Lp, Lp);
+    to_slot(S.vC + NTERM * (size_t)G.VW, a.parL + (size_t)P_TAU * Lp, Lp);
     __syncthreads();
     for (long long step = 0; step < a.nsteps; step++) {
         // the state is coefficient 0 (Sec. 2): publish this CTA's component,
@@ -1115,10 +1181,11 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             // first factors of the product terms: component shifted by d_lo,
             // complemented when the term is negative
             for (int k = 0; k < NTERM; k++) {
-                if (!bk[BK_TERM + 4 * k]) continue;
-                const uint32_t *src = S.raw + (size_t)bk[BK_TERM + 4 * k + 1] * Lp;
-                const uint32_t inv = bk[BK_TERM + 4 * k + 2] ? 0xffffffffu : 0u;
-                const int dl = bk[BK_TERM + 4 * k + 3] & 7;
+                const int *bt = bk + BK_TERM + 4 * k;
+                if (!bt[0]) continue;
+                const uint32_t *src = S.raw + (size_t)bt[1] * Lp;
+                const uint32_t inv = bt[2] ? 0xffffffffu : 0u;
+                const int dl = bt[3] & 7;
                 uint32_t *dst = S.vA + (size_t)k * G.VW;
                 for (int x = threadIdx.x; x < G.M; x += PT) {
                     const int y = x - dl;
@@ -1130,26 +1197,38 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             const int nrun = S.misc[MS_NRUN];
             for (int rr = 0; rr < nrun; rr++) {
                 const int rs = S.misc[MS_RUN + rr], re = S.misc[MS_RUNE + rr];
-                small_products(G, S.vA, S.vC, rs, re - rs, S.tinfo, false, S.stage, win,
+                small_products(G, S.vA, S.vC, rs, re - rs, S.tinfo, false, S.bstage, win,
                                S.tinfo[rs * TI + 3] * W);
             }
             pr.mark(PR_MAC);
-            if (bk[BK_INNER] >= 0) {
-                // every worker has added its inner sums of index m
+            if (bk[BK_INNER] >= 0 || bk[BK_OINNER] >= 0) {
+                // every worker and outer-pair CTA has added its sums of index m
                 const unsigned target = (unsigned)((g / PIPE_SETS + 1) * (long long)(gridDim.x - NCL));
                 if (!wait_geq(S, a, pa.done + set, target)) return;
                 pr.mark(PR_BARRIER);
-                long long *gg = pa.gin + ((size_t)set * 2 + (c - 1)) * a.Wcap;
-                const int off = bk[BK_INNER], iw = bk[BK_IWIDTH];
+                // both parts of this target (middle pairs, outer pairs); a
+                // thread owns window columns cc = threadIdx.x mod PT
+                long long *gm = pa.gin + ((size_t)set * 2 + (c - 1)) * 2 * a.Wcap, *go = gm + a.Wcap;
+                const int offm = bk[BK_INNER], wm = bk[BK_IWIDTH];
+                const int offo = bk[BK_OINNER], wo = bk[BK_OWIDTH];
                 for (int cc = threadIdx.x; cc < width; cc += PT) {
-                    const int y = cc - off;
-                    if (y >= 0 && y < iw) {
-                        const long long v = __ldcg(&gg[y]);
-                        if (v) {
-                            win[cc] += v;
-                            gg[y] = 0;
+                    long long v = 0;
+                    const int ym = cc - offm, yo = cc - offo;
+                    if (offm >= 0 && ym >= 0 && ym < wm) {
+                        const long long u = __ldcg(&gm[ym]);
+                        if (u) {
+                            v += u;
+                            gm[ym] = 0;
                         }
                     }
+                    if (offo >= 0 && yo >= 0 && yo < wo) {
+                        const long long u = __ldcg(&go[yo]);
+                        if (u) {
+                            v += u;
+                            go[yo] = 0;
+                        }
+                    }
+                    if (v) win[cc] += v;
                 }
                 pr.mark(PR_STAGE);
             }
@@ -1163,12 +1242,12 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 S.misc[MS_NEWE + 1] = f;
             }
             for (int x = threadIdx.x; x < Lp; x += PT) a.coefL[((size_t)c * N1 + m + 1) * Lp + x] = S.newc[x];
-            if (c == 0 && m + 2 < a.N) {
-                // window table of the inner sums of index m+2 without its two
-                // newest pairs: pairs (a, m+2-a), a = 2..m
+            if (c == 0 && m + 3 < a.N) {
+                // window table of the workers' part of index m+3 without its
+                // two newest pairs: pairs (a, m+3-a), a = 3..m
                 long long lo3[2] = {LLONG_MAX, LLONG_MAX}, hi3[2] = {LLONG_MIN, LLONG_MIN};
-                for (int aa = 2 + threadIdx.x; aa <= m; aa += PT) {
-                    const int b = m + 2 - aa;
+                for (int aa = 3 + threadIdx.x; aa <= m; aa += PT) {
+                    const int b = m + 3 - aa;
                     if (!(S.flgT[aa] & F_NZ)) continue;
                     for (int tg = 0; tg < 2; tg++) {
                         const int crow = (tg == 0 ? 2 : 1) * N1 + b;
@@ -1182,7 +1261,7 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 const long long r0 = block_min_ll(lo3[0], red), r1 = block_max_ll(hi3[0], red);
                 const long long r2 = block_min_ll(lo3[1], red), r3 = block_max_ll(hi3[1], red);
                 if (threadIdx.x == 0) {
-                    long long *mid = pa.imid + (size_t)((g + 2) % PIPE_SETS) * 4;
+                    long long *mid = pa.imid + (size_t)((g + 3) % PIPE_SETS) * 4;
                     mid[0] = r0;
                     mid[1] = r1;
                     mid[2] = r2;
@@ -1204,8 +1283,9 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 S.expT[idx] = __ldcg(&a.coefE[idx]);
                 S.flgT[idx] = __ldcg(&a.coefF[idx]);
             }
-            if (threadIdx.x >= 32 && threadIdx.x < 36 && m + 1 >= 2 && m + 1 < a.N) {
-                // inner-window table of index m+1 (written with coefficient m-1's alpha)
+            if (threadIdx.x >= 32 && threadIdx.x < 36 && m + 1 >= 4 && m + 1 < a.N) {
+                // window table of the workers' part of index m+1 (written with
+                // coefficient m-1)
                 ((long long *)(S.misc + MS_IMID))[threadIdx.x - 32] =
                     __ldcg(&pa.imid[(size_t)((g + 1) % PIPE_SETS) * 4 + threadIdx.x - 32]);
             }
@@ -1230,7 +1310,7 @@ __global__ void __launch_bounds__(PT, 1) pipe_kernel(KArgs a, PArgs pa)
     const Geo G(a.L, a.Lp, a.N, a.Wcap);
     PSmem S;
     pipe_layout(G, a.N, pa.tb, &S, smem_raw);
-    const bool prof_cta = blockIdx.x == 1 || blockIdx.x == gridDim.x - 1;
+    const bool prof_cta = true;
     if (threadIdx.x < PROF_SLOTS) ((long long *)(S.misc + MS_PROF))[threadIdx.x] = 0;
     if (threadIdx.x == 0) S.misc[MS_STATUS] = 0;
     __syncthreads();
@@ -1240,9 +1320,15 @@ __global__ void __launch_bounds__(PT, 1) pipe_kernel(KArgs a, PArgs pa)
     else
         worker_loop(S, a, pa, G);
     tot.mark(PR_TOTAL);
-    if (a.prof && prof_cta && threadIdx.x == 0) {
-        long long *dst = a.prof + (blockIdx.x == 1 ? 0 : PROF_SLOTS);
-        for (int k = 0; k < PROF_SLOTS; k++) dst[k] += ((long long *)(S.misc + MS_PROF))[k];
+    if (a.prof && threadIdx.x == 0) {
+        // rows 0 and 1: the beta' bracket CTA and the last worker; then one row per CTA
+        const long long *src = (const long long *)(S.misc + MS_PROF);
+        long long *row = a.prof + (size_t)(2 + blockIdx.x) * PROF_SLOTS;
+        for (int k = 0; k < PROF_SLOTS; k++) row[k] += src[k];
+        if (blockIdx.x == 1 || blockIdx.x == gridDim.x - 1) {
+            long long *dst = a.prof + (blockIdx.x == 1 ? 0 : PROF_SLOTS);
+            for (int k = 0; k < PROF_SLOTS; k++) dst[k] += src[k];
+        }
     }
 }
 
@@ -1255,7 +1341,7 @@ size_t pipe_smem_bytes(int L, int Lp, int N, int Wcap, int tb)
 }
 
 int pipe_tb_max() { return TB_MAX; }
-int pipe_closer_ctas() { return NCL; }
+int pipe_fixed_ctas() { return NFIX; }
 
 int pipe_max_ctas(size_t smem)
 {

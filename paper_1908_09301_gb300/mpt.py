@@ -231,12 +231,15 @@ class Context:
 
     def profile(self):
         """Per-phase SM cycles of the last launch: {cta: {phase: cycles}} for
-        the first and the last CTA."""
-        buf = np.zeros(32, np.int64)
-        _check(lib().mpt_get_profile(self._h, _ptr(buf), 32))
+        the first and the last CTA, and under "ctas" one row of raw counters
+        per CTA (pipelined kernel; zeros otherwise)."""
+        rows = 2 + self.launch()
+        buf = np.zeros(16 * rows, np.int64)
+        _check(lib().mpt_get_profile(self._h, _ptr(buf), int(buf.size)))
         out = {}
         for k, cta in enumerate(("first", "last")):
             out[cta] = {n: int(buf[16 * k + j]) for j, n in enumerate(self.PROFILE_SLOTS)}
+        out["ctas"] = buf[32:].reshape(-1, 16)
         return out
 
     def set_launch(self, ctas: int):

@@ -28,6 +28,8 @@ def gpu_ctx(mpt, L, N, par=(O.SIGMA, O.R, O.B, O.TAU), x0=O.X0, ctas=0, kind=0):
         c.set_launch(ctas)
     if kind:
         c.set_kernel(kind)
+        if kind == 2 and N >= 3:
+            assert c.kernel() == 2, "the pipelined kernel must run this case"
     return c
 
 
@@ -68,7 +70,7 @@ def test_parameters_match_oracle(mpt):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("L,N", [(1, 5), (2, 7), (3, 20), (11, 60), (13, 25), (21, 40), (53, 30),
-                                 (8, 9), (9, 64)])
+                                 (8, 9), (9, 64), (130, 12), (250, 9), (600, 8), (1024, 6)])
 def test_one_step_coefficients(mpt, L, N, kind):
     """Eq. (3) coefficients alpha_0..alpha_N etc. and the Horner state, bit for bit."""
     c = gpu_ctx(mpt, L, N, kind=kind)
@@ -81,8 +83,8 @@ def test_one_step_coefficients(mpt, L, N, kind):
     c.close()
 
 
-@pytest.mark.parametrize("kind,ctas", [(1, 1), (1, 2), (1, 3), (1, 5), (1, 17), (2, 16), (2, 24),
-                                       (2, 64), (2, 0)])
+@pytest.mark.parametrize("kind,ctas", [(1, 1), (1, 2), (1, 3), (1, 5), (1, 17), (2, 6), (2, 7),
+                                       (2, 16), (2, 24), (2, 64), (2, 0)])
 def test_launch_shape_invariance(mpt, kind, ctas):
     """The exact sums make the result independent of how the GPU splits them."""
     L, N = 21, 90
