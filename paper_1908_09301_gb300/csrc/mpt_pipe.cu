@@ -405,19 +405,48 @@ __device__ void group_products(const Geo &G, const uint32_t *Abase, const uint32
 }
 
 
-// The same sum for a few terms (a bracket's products, a Horner step): G.RS
-// threads per unit (a power of two, at most 8, with RS (P+1) <= PT), always
-// inside one warp, so their shares are summed with log2(RS) shuffle steps;
-// each unit's first thread stores the unit's digits, and one thread per
-// window column adds them (with the complement corrections).  Only the first
-// RS (P+1) threads walk.  `stage` holds (P+1) 2 (W+2) long longs.  Starts and
-// ends with __syncthreads.
-__device__ void small_products(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
-                               int n, const int *tinfo, bool neg_all, long long *stage,
-                               long long *win, int coff)
+// Reduce-scatter of NV values over the 2^LOG lanes r = 0.. of an aligned lane
+// group: lane r ends with NV >> LOG sums, of the values base .. base +
+// (NV >> LOG) - 1; returns base.  Each step swaps half of the values with
+// the partner lane (xor offset) and keeps the other half.
+template <int NV, int LOG>
+__device__ __forceinline__ int reduce_scatter(long long (&v)[NV], int r)
+{
+    int base = 0;
+#pragma unroll
+    for (int k = 0; k < LOG; k++) {
+        const int o = 1 << (LOG - 1 - k);
+        const int half = NV >> (k + 1);
+        const bool up = (r & o) != 0;  // keep the upper half
+#pragma unroll
+        for (int i = 0; i < NV / 2; i++) {
+            if (i < half) {
+                const long long send = up ? v[i] : v[half + i];
+                const long long keep = up ? v[half + i] : v[i];
+                v[i] = keep + __shfl_xor_sync(FULL, send, o);
+            }
+        }
+        base += up ? half : 0;
+    }
+    return base;
+}
+
+// The same sum for a few terms (a bracket's products, a Horner step): RS =
+// 2^LOG threads per unit (RS (P+1) <= PT), always inside one warp, so their
+// shares are combined by a reduce-scatter of the unit's 2 (W+2) digits
+// (block 0, block 1) and each lane stores its part; then one thread per
+// window column adds the column (with the complement corrections).  Only the
+// first RS (P+1) threads walk.  `stage` holds (P+1) 2 (W+2) long longs.
+// Starts and ends with __syncthreads.
+template <int LOG>
+__device__ void small_products_t(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
+                                 int n, const int *tinfo, bool neg_all, long long *stage,
+                                 long long *win, int coff)
 {
     constexpr int ND = W + 2;
-    const int tid = threadIdx.x, RS = G.RS;
+    constexpr int RS = 1 << LOG;
+    constexpr int NV = ((2 * ND + RS - 1) / RS) * RS;  // the digits, padded to a multiple of RS
+    const int tid = threadIdx.x;
     __syncthreads();
     if (tid < ((G.P1 * RS + 31) & ~31) && n > 0) {
         uint32_t a0[W], a1[W], a2[W], x0[W], x1[W], x2[W];
@@ -426,28 +455,21 @@ __device__ void small_products(const Geo &G, const uint32_t *Abase, const uint32
         bool strad = false, b1only = false;
         const int q = tid / RS, r = tid - q * RS;
         if (q < G.P1) unit_walk(G, Abase, Cbase, s0, n, q, r, RS, a0, a1, a2, x0, x1, x2, strad, b1only);
-        long long v0[ND], v1[ND];
+        long long v[NV];
 #pragma unroll
         for (int t = 0; t < ND; t++) {
             const long long bx = col_digit(x0, x1, x2, t), ba = col_digit(a0, a1, a2, t);
-            v0[t] = b1only ? 0 : bx;
-            v1[t] = b1only ? ba : (strad ? ba - bx : 0);
+            v[t] = b1only ? 0 : bx;
+            v[ND + t] = b1only ? ba : (strad ? ba - bx : 0);
         }
 #pragma unroll
-        for (int off = 1; off < RS; off <<= 1) {
-#pragma unroll
-            for (int t = 0; t < ND; t++) {
-                v0[t] += __shfl_xor_sync(FULL, v0[t], off);
-                v1[t] += __shfl_xor_sync(FULL, v1[t], off);
-            }
-        }
-        if (r == 0 && q < G.P1) {
+        for (int t = 2 * ND; t < NV; t++) v[t] = 0;
+        const int base = reduce_scatter<NV, LOG>(v, r);
+        if (q < G.P1) {
             long long *d = stage + (size_t)q * 2 * ND;
 #pragma unroll
-            for (int t = 0; t < ND; t++) {
-                d[t] = v0[t];
-                d[ND + t] = v1[t];
-            }
+            for (int i = 0; i < NV / RS; i++)
+                if (base + i < 2 * ND) d[base + i] = v[i];
         }
     }
     __syncthreads();
@@ -481,6 +503,17 @@ __device__ void small_products(const Geo &G, const uint32_t *Abase, const uint32
         }
     }
     __syncthreads();
+}
+
+__device__ void small_products(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
+                               int n, const int *tinfo, bool neg_all, long long *stage,
+                               long long *win, int coff)
+{
+    switch (G.RS) {
+    case 8: small_products_t<3>(G, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
+    case 4: small_products_t<2>(G, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
+    default: small_products_t<1>(G, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
+    }
 }
 
 // ------------------------------------------------------------------ workers
@@ -636,6 +669,22 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
     const int w = blockIdx.x - NFIX;
     // index m waits for coefficient m-2 (workers) or m-1 (outer pairs)
     const int lag = role ? 1 : 2;
+    // with two workers or more, the first half takes the Y terms and the
+    // rest the Z terms, so that no worker's range straddles the two targets
+    const bool wsplit = nw >= 2;
+    const int wtg = w < nw / 2 ? 0 : 1;
+    const int wl = wtg ? w - nw / 2 : w, wn = wtg ? nw - nw / 2 : nw / 2;
+    // this worker's terms [ta, tb) of index mm (mm >= 4)
+    auto range_of = [&](int mm, int &ta, int &tb) {
+        const int Tt = mm - 3;  // terms per target
+        if (wsplit) {
+            ta = wtg * Tt + (int)((long long)Tt * wl / wn);
+            tb = wtg * Tt + (int)((long long)Tt * (wl + 1) / wn);
+        } else {
+            ta = (int)((long long)2 * Tt * w / nw);
+            tb = (int)((long long)2 * Tt * (w + 1) / nw);
+        }
+    };
     const bool prof_on = true;
     // zero padding of the second factors stays zero; windows start empty
     for (int e = threadIdx.x; e < 2 * TB * G.M; e += PT) {
@@ -675,6 +724,10 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 long long lo[2], hi[2];
                 if (role == 0) {
                     inner_window(a, (const long long *)(S.misc + MS_BK), S.expT, S.flgT, m, lo, hi);
+                    if (wsplit) {  // only this worker's target
+                        lo[1 - wtg] = 0;
+                        hi[1 - wtg] = 0;
+                    }
                 } else {
                     const int tg = role - 1;
                     outer_window(a, S.expT, S.flgT, m, tg, lo[tg], hi[tg]);
@@ -702,11 +755,7 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 return;
             }
             int tA = 0, tB = m == 2 ? 1 : 2;  // outer pairs: all of them
-            if (role == 0) {
-                const int T = 2 * (m - 3);
-                tA = (int)((long long)T * w / nw);
-                tB = (int)((long long)T * (w + 1) / nw);
-            }
+            if (role == 0) range_of(m, tA, tB);
             for (int tb0 = tA; tb0 < tB; tb0 += TB) {
                 const int nb = min(TB, tB - tb0);
                 const int buf = bcount & 1;
@@ -725,8 +774,8 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                     pf_tb0 = tb0 + TB;
                     issue_loads(S, a, G, TB, buf ^ 1, role, m, pf_tb0, min(TB, tB - pf_tb0), 0);
                 } else if (role == 0 && m + 1 < a.N) {
-                    const int T2 = 2 * (m - 2);
-                    const int tA2 = (int)((long long)T2 * w / nw), tB2 = (int)((long long)T2 * (w + 1) / nw);
+                    int tA2, tB2;
+                    range_of(m + 1, tA2, tB2);
                     if (tB2 > tA2) {
                         pf = true;
                         pf_late = true;
@@ -744,6 +793,10 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 prepare_batch(S, a, G, TB, buf, role, m, tb0, nb);
                 pr.mark(PR_FLUSH);
                 const int nrun = S.misc[MS_NRUN];
+                if (pr.p) {  // counts: term groups (slot PR_X2), terms (slot PR_X6)
+                    pr.p[PR_X2] += nrun;
+                    pr.p[PR_X6] += nb;
+                }
                 for (int rr = 0; rr < nrun; rr++) {
                     const int rs = S.misc[MS_RUN + rr], re = S.misc[MS_RUNE + rr];
                     const int *ti = S.tinfo + rs * TI;
