@@ -31,11 +31,11 @@
 //
 // Limb products use units: unit q of a product A' * C (A' of M = (P+1)W
 // limbs, C of Lp limbs) owns columns qW..qW+W-1 of two blocks (block 1 is M
-// columns up); R threads share a unit, each taking a contiguous share of its
-// (term, chunk) sequence, in which every term's block-0 chunks come before
-// any block-1 chunk, so a thread switches blocks at most once.  The shares
-// are summed through shared memory per (unit, block, digit), then added into
-// the window one column per thread.
+// columns up); a group of RS lanes of one warp shares a unit, each taking a
+// contiguous share of its (term, chunk) sequence, in which every term's
+// block-0 chunks come before any block-1 chunk, so a lane switches blocks at
+// most once.  The shares are combined by a reduce-scatter within the lane
+// group, then added into the window one column per thread.
 //
 // Hand-over: a monotone "published" counter (release/acquire, 3 per
 // coefficient) and per-set monotone completion counters; every wait is
@@ -95,7 +95,7 @@ enum {
 
 // Geometry of the unit walk (host and device)
 struct Geo {
-    int L, Lp, P, P1, M, VW, R, RS, WW, GW, N1;
+    int L, Lp, P, P1, M, VW, RS, RSW, WW, GW, N1;
     __host__ __device__ Geo(int L_, int Lp_, int N, int Wcap)
     {
         L = L_;
@@ -104,10 +104,12 @@ struct Geo {
         P1 = P + 1;
         M = P1 * W;
         VW = vwords(M);
-        R = PT / P1;
-        if (R < 1) R = 1;
-        RS = 8;   // lanes per unit of the few-term products: a power of two, units within warps
-        while (RS > 1 && RS * P1 > PT) RS >>= 1;
+        // lanes per unit of the few-term products (brackets, Horner) and of
+        // the workers' batches: powers of two, units within warps
+        RS = 8;
+        while (RS > 2 && RS * P1 > PT) RS >>= 1;
+        RSW = 16;
+        while (RSW > 2 && RSW * P1 > PT) RSW >>= 1;
         WW = Wcap + 4 * W;
         GW = 2 * M + 2;
         N1 = N + 1;
@@ -121,7 +123,7 @@ struct PSmem {
     long long *win;    // [2][WW] windows
     uint32_t *dig;     // [WW] normalised digits
     // workers
-    long long *stage;  // [P1 (R + 3)][W+2] unit digit sums
+    long long *stage;  // [P1 2][W+2] unit digit sums
     uint32_t *araw;    // [2][TB][Lp] first factors as loaded
     uint32_t *cc;      // [2][TB][VW] second factors (cyclic, zero above Lp)
     uint32_t *ash;     // [TB][VW] first factors shifted / complemented
@@ -158,7 +160,7 @@ __host__ __device__ inline size_t pipe_layout(const Geo &G, int N, int TB, PSmem
     p = take(sizeof(uint32_t) * (size_t)G.WW);
     if (S) S->dig = (uint32_t *)p;
     const size_t u0 = o;
-    p = take(sizeof(long long) * (size_t)G.P1 * (G.R + 3) * (W + 2));
+    p = take(sizeof(long long) * (size_t)G.P1 * 2 * (W + 2));
     if (S) S->stage = (long long *)p;
     p = take(sizeof(uint32_t) * 2 * (size_t)TB * G.Lp);
     if (S) S->araw = (uint32_t *)p;
@@ -304,107 +306,6 @@ __device__ __forceinline__ void unit_walk(const Geo &G, const uint32_t *Abase, c
     }
 }
 
-// Sum over the n terms in slots [s0, s0+n) of A'_s * C_s (A'_s = Abase + s VW,
-// C_s = Cbase + s VW), exact, added into win[coff + c], c < 2M+2.  With
-// `tinfo`, slots flagged negative hold the complement of the shifted first
-// factor over its Lp limbs, and the complement's correction
-// (+C 2^(32 d) + ~C 2^(32 (d+Lp)) + 2^(32 (d+Lp)) - 2^(32 (d+2Lp))) is added
-// as well.  neg_all negates the whole sum.  Every thread of the CTA calls
-// this; it starts and ends with __syncthreads.  For many terms (a worker's
-// batch): R threads per unit, shares summed through shared memory.
-__device__ void group_products(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
-                               int n, const int *tinfo, bool neg_all, long long *stage,
-                               long long *win, int coff)
-{
-    const int tid = threadIdx.x;
-    uint32_t a0[W], a1[W], a2[W], x0[W], x1[W], x2[W];
-#pragma unroll
-    for (int k = 0; k < W; k++) a0[k] = a1[k] = a2[k] = x0[k] = x1[k] = x2[k] = 0u;
-    int key = -1;
-    bool strad = false, b1only = false;  // share straddles the block switch / lies in block 1
-    const int Re = G.R;  // threads per unit
-    __syncthreads();
-    if (tid < G.P1 * Re && n > 0) {
-        const int q = tid / Re, r = tid - q * Re;
-        key = q;
-        unit_walk(G, Abase, Cbase, s0, n, q, r, Re, a0, a1, a2, x0, x1, x2, strad, b1only);
-    }
-    // Each thread's share lies in block 0, in block 1, or straddles the switch
-    // once (at most one thread per unit).  A thread stores the digits of its
-    // block (block 0 when straddling, whose block-1 digits go to a slot of
-    // the unit), the shares are summed per (unit, block, digit), and one
-    // thread per window column adds the column.
-    constexpr int ND = W + 2;
-    long long *st0 = stage;                                // [P1 Re][ND]
-    long long *st1 = st0 + (size_t)G.P1 * G.R * ND;        // [P1][ND] straddlers' block 1
-    long long *tot = st1 + (size_t)G.P1 * ND;              // [P1][2][ND]
-    if (key >= 0) {
-        long long *dst = st0 + (size_t)tid * ND;
-        long long *dst1 = st1 + (size_t)key * ND;
-#pragma unroll
-        for (int t = 0; t < ND; t++) {
-            const long long bx = col_digit(x0, x1, x2, t), ba = col_digit(a0, a1, a2, t);
-            dst[t] = b1only ? ba : bx;
-            if (strad) dst1[t] = ba - bx;
-        }
-    }
-    __syncthreads();
-    for (int e = tid; e < G.P1 * 2 * ND; e += PT) {
-        const int u = e / (2 * ND), rem = e - u * 2 * ND, b = rem / ND, t = rem - b * ND;
-        const int I = n * G.P1, nAu = n * (u + 1);
-        // rs: the last thread whose share starts at or below the switch
-        int rs = Re;
-        bool sS = false;
-        if (nAu < I) {
-            rs = ((nAu + 1) * Re + I - 1) / I - 1;
-            sS = (I * rs / Re) < nAu;
-        }
-        const long long *src = st0 + (size_t)u * Re * ND + t;
-        long long sum = 0;
-        if (b == 0) {
-            const int r1 = sS ? rs + 1 : rs;
-            for (int r = 0; r < r1; r++) sum += src[(size_t)r * ND];
-        } else if (rs < Re) {
-            for (int r = sS ? rs + 1 : rs; r < Re; r++) sum += src[(size_t)r * ND];
-            if (sS) sum += st1[(size_t)u * ND + t];
-        }
-        tot[e] = sum;
-    }
-    __syncthreads();
-    for (int c = tid; c < G.GW; c += PT) {
-        long long s = 0;
-        if (n > 0) {
-            if (c < G.M + 2) {
-                const int u = c / W;
-                if (u <= G.P) s += tot[(u * 2) * ND + c - u * W];
-                if (u >= 1 && c - (u - 1) * W < ND) s += tot[((u - 1) * 2) * ND + c - (u - 1) * W];
-            }
-            const int c1 = c - G.M;
-            if (c1 >= 0) {
-                const int u = c1 / W;
-                if (u <= G.P) s += tot[(u * 2 + 1) * ND + c1 - u * W];
-                if (u >= 1 && c1 - (u - 1) * W < ND) s += tot[((u - 1) * 2 + 1) * ND + c1 - (u - 1) * W];
-            }
-        }
-        if (tinfo) {
-            // complement corrections of the negative terms
-            for (int sl = s0; sl < s0 + n; sl++) {
-                const int *ti = tinfo + sl * TI;
-                if (!ti[1]) continue;
-                const int y = c - ti[2];
-                const uint32_t *Cs = Cbase + (size_t)sl * G.VW;
-                if (y >= 0 && y < G.Lp) s += Cs[gpos(y)];
-                else if (y >= G.Lp && y < 2 * G.Lp) s += (uint32_t)~Cs[gpos(y - G.Lp)];
-                if (y == G.Lp) s += 1;
-                if (y == 2 * G.Lp) s -= 1;
-            }
-        }
-        if (s) win[coff + c] += neg_all ? -s : s;
-    }
-    __syncthreads();
-}
-
-
 // Reduce-scatter of NV values over the 2^LOG lanes r = 0.. of an aligned lane
 // group: lane r ends with NV >> LOG sums, of the values base .. base +
 // (NV >> LOG) - 1; returns base.  Each step swaps half of the values with
@@ -431,13 +332,18 @@ __device__ __forceinline__ int reduce_scatter(long long (&v)[NV], int r)
     return base;
 }
 
-// The same sum for a few terms (a bracket's products, a Horner step): RS =
-// 2^LOG threads per unit (RS (P+1) <= PT), always inside one warp, so their
-// shares are combined by a reduce-scatter of the unit's 2 (W+2) digits
-// (block 0, block 1) and each lane stores its part; then one thread per
-// window column adds the column (with the complement corrections).  Only the
-// first RS (P+1) threads walk.  `stage` holds (P+1) 2 (W+2) long longs.
-// Starts and ends with __syncthreads.
+// Sum over the n terms in slots [s0, s0+n) of A'_s * C_s (A'_s = Abase + s VW,
+// C_s = Cbase + s VW), exact, added into win[coff + c], c < 2M+2.  With
+// `tinfo`, slots flagged negative hold the complement of the shifted first
+// factor over its Lp limbs, and the complement's correction
+// (+C 2^(32 d) + ~C 2^(32 (d+Lp)) + 2^(32 (d+Lp)) - 2^(32 (d+2Lp))) is added
+// as well.  neg_all negates the whole sum.  Every thread of the CTA calls
+// this.  RS = 2^LOG threads share a unit (RS (P+1) <= PT), always
+// inside one warp, so their shares are combined by a reduce-scatter of the
+// unit's 2 (W+2) digits (block 0, block 1) and each lane stores its part;
+// then one thread per window column adds the column (with the complement
+// corrections).  Only the first RS (P+1) threads walk.  `stage` holds
+// (P+1) 2 (W+2) long longs.  Starts and ends with __syncthreads.
 template <int LOG>
 __device__ void small_products_t(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
                                  int n, const int *tinfo, bool neg_all, long long *stage,
@@ -453,7 +359,7 @@ __device__ void small_products_t(const Geo &G, const uint32_t *Abase, const uint
 #pragma unroll
         for (int k = 0; k < W; k++) a0[k] = a1[k] = a2[k] = x0[k] = x1[k] = x2[k] = 0u;
         bool strad = false, b1only = false;
-        const int q = tid / RS, r = tid - q * RS;
+        const int q = tid >> LOG, r = tid & (RS - 1);
         if (q < G.P1) unit_walk(G, Abase, Cbase, s0, n, q, r, RS, a0, a1, a2, x0, x1, x2, strad, b1only);
         long long v[NV];
 #pragma unroll
@@ -505,11 +411,13 @@ __device__ void small_products_t(const Geo &G, const uint32_t *Abase, const uint
     __syncthreads();
 }
 
-__device__ void small_products(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
-                               int n, const int *tinfo, bool neg_all, long long *stage,
+// RS threads per unit: a power of two from 2 to 16 with RS (P+1) <= PT
+__device__ void small_products(const Geo &G, int RS, const uint32_t *Abase, const uint32_t *Cbase,
+                               int s0, int n, const int *tinfo, bool neg_all, long long *stage,
                                long long *win, int coff)
 {
-    switch (G.RS) {
+    switch (RS) {
+    case 16: small_products_t<4>(G, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
     case 8: small_products_t<3>(G, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
     case 4: small_products_t<2>(G, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
     default: small_products_t<1>(G, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
@@ -800,7 +708,7 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 for (int rr = 0; rr < nrun; rr++) {
                     const int rs = S.misc[MS_RUN + rr], re = S.misc[MS_RUNE + rr];
                     const int *ti = S.tinfo + rs * TI;
-                    group_products(G, S.ash, S.cc + (size_t)buf * TB * G.VW, rs, re - rs, S.tinfo,
+                    small_products(G, G.RSW, S.ash, S.cc + (size_t)buf * TB * G.VW, rs, re - rs, S.tinfo,
                                    false, S.stage, S.win + (size_t)ti[0] * G.WW, ti[3] * W);
                 }
                 pr.mark(PR_MAC);
@@ -1107,7 +1015,7 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
             width = (int)(hi - lo);
         }
         if (prod)
-            small_products(G, hA, tauC, 0, 1, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.bstage, win,
+            small_products(G, G.RS, hA, tauC, 0, 1, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.bstage, win,
                            (int)(lpp - lo));
         pr.mark(PR_HMAC);
         if (lone) {
@@ -1250,7 +1158,7 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             const int nrun = S.misc[MS_NRUN];
             for (int rr = 0; rr < nrun; rr++) {
                 const int rs = S.misc[MS_RUN + rr], re = S.misc[MS_RUNE + rr];
-                small_products(G, S.vA, S.vC, rs, re - rs, S.tinfo, false, S.bstage, win,
+                small_products(G, G.RS, S.vA, S.vC, rs, re - rs, S.tinfo, false, S.bstage, win,
                                S.tinfo[rs * TI + 3] * W);
             }
             pr.mark(PR_MAC);
