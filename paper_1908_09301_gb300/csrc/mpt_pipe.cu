@@ -582,15 +582,16 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
     const bool wsplit = nw >= 2;
     const int wtg = w < nw / 2 ? 0 : 1;
     const int wl = wtg ? w - nw / 2 : w, wn = wtg ? nw - nw / 2 : nw / 2;
-    // this worker's terms [ta, tb) of index mm (mm >= 4)
+    // this worker's terms [ta, tb) of index mm (mm >= 4); 32-bit arithmetic
+    // (2 N * gridDim < 2^31), a 64-bit division being a long software routine
     auto range_of = [&](int mm, int &ta, int &tb) {
-        const int Tt = mm - 3;  // terms per target
+        const unsigned Tt = (unsigned)(mm - 3);  // terms per target
         if (wsplit) {
-            ta = wtg * Tt + (int)((long long)Tt * wl / wn);
-            tb = wtg * Tt + (int)((long long)Tt * (wl + 1) / wn);
+            ta = wtg * (int)Tt + (int)(Tt * (unsigned)wl / (unsigned)wn);
+            tb = wtg * (int)Tt + (int)(Tt * (unsigned)(wl + 1) / (unsigned)wn);
         } else {
-            ta = (int)((long long)2 * Tt * w / nw);
-            tb = (int)((long long)2 * Tt * (w + 1) / nw);
+            ta = (int)(2u * Tt * (unsigned)w / (unsigned)nw);
+            tb = (int)(2u * Tt * (unsigned)(w + 1) / (unsigned)nw);
         }
     };
     const bool prof_on = true;
@@ -628,6 +629,7 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 ((long long *)(S.misc + MS_BK))[threadIdx.x - 32] = __ldcg(&pa.imid[(size_t)set * 4 + threadIdx.x - 32]);
             }
             __syncthreads();
+            pr.mark(PR_X4);
             if (threadIdx.x == 0) {
                 long long lo[2], hi[2];
                 if (role == 0) {
@@ -671,6 +673,7 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 if (!was_pf) issue_loads(S, a, G, TB, buf, role, m, tb0, nb, 0);
                 else if (pf_late) issue_loads(S, a, G, TB, buf, role, m, tb0, nb, 2);
                 cp_async_commit();
+                pr.mark(PR_X3);
                 // prefetch the next batch: the rest of this index, or the first
                 // batch of index m+1 without its late terms
                 pf = false;
