@@ -59,6 +59,16 @@ constexpr int NA = NTERM + 1;    // A' slots of a bracket CTA: product terms, Ho
 constexpr int NC = NTERM + 1;    // C slots: fixed factors, tau
 constexpr int TI = 8;            // ints of term info per slot
 constexpr int TB_MAX = 32;       // worker slots per batch (one warp finds the groups)
+// a worker CTA's two groups: control warps (waits, loads, staging, flushes)
+// and compute warps (products), handing batches over through two buffers
+constexpr int CW = 2;            // control warps
+constexpr int CT = 32 * CW;      // control threads
+constexpr int KT = PT - CT;      // compute threads
+// named barriers: FULL + b (a batch in buffer b is ready), EMPTY + b (the
+// compute group is through buffer b), the compute group's, the control group's
+enum { BAR_FULL = 1, BAR_EMPTY = 3, BAR_KT = 5, BAR_CT = 6 };
+// batch descriptor: exit flag, term groups, window parity, group starts and ends
+enum { DS_EXIT = 0, DS_NRUN = 1, DS_PAR = 2, DS_RUN = 4, DS_RUNE = 4 + TB_MAX, DESC_INTS = 4 + 2 * TB_MAX };
 
 enum { P_SIGMA = 0, P_R = 1, P_B = 2, P_TAU = 3 };
 
@@ -68,8 +78,8 @@ enum {
     MS_NEWE = 2,    // [2] exponent and flags of this CTA's newest number
     MS_PSCAL = 8,   // [3][2] sigma, R, b: single non-zero limb index (or -1), value
     MS_WLO = 16,    // [4] long long window bases (ints 16..23)
-    MS_WID = 24,    // [4] window widths (workers); bracket CTAs: [4] long long workers-window
-                    // table of the next index (ints 24..31, MS_IMID)
+    MS_WID = 24,    // [2][2] window widths by parity and target (workers); bracket CTAs:
+                    // [4] long long workers-window table of the next index (ints 24..31, MS_IMID)
     MS_IMID = 24,
     MS_BK = 32,     // [48] bracket setup (ints 32..79)
     MS_RED = 80,    // [RED_LL] long long scratch of the block routines (ints 80..271)
@@ -109,7 +119,7 @@ struct Geo {
         RS = 8;
         while (RS > 2 && RS * P1 > PT) RS >>= 1;
         RSW = 16;
-        while (RSW > 2 && RSW * P1 > PT) RSW >>= 1;
+        while (RSW > 2 && RSW * P1 > KT) RSW >>= 1;
         WW = Wcap + 4 * W;
         GW = 2 * M + 2;
         N1 = N + 1;
@@ -119,14 +129,15 @@ struct Geo {
 struct PSmem {
     int *expT, *flgT;  // [3][N+1]
     int *misc;         // [MISC_INTS]
-    int *tinfo;        // [TB_MAX][TI] term info
-    long long *win;    // [2][WW] windows
+    int *tinfo;        // [2][TB_MAX][TI] term info (by buffer)
+    int *desc;         // [2][DESC_INTS] batch descriptors (workers)
+    long long *win;    // [4][WW] windows (workers: by parity and target)
     uint32_t *dig;     // [WW] normalised digits
     // workers
     long long *stage;  // [P1 2][W+2] unit digit sums
-    uint32_t *araw;    // [2][TB][Lp] first factors as loaded
+    uint32_t *araw;    // [TB][Lp] first factors as loaded
     uint32_t *cc;      // [2][TB][VW] second factors (cyclic, zero above Lp)
-    uint32_t *ash;     // [TB][VW] first factors shifted / complemented
+    uint32_t *ash;     // [2][TB][VW] first factors shifted / complemented
     // bracket CTAs (same bytes as the workers' part)
     long long *bstage; // [P1 2][W+2] unit digit sums of the few-term products
     uint32_t *vA;      // [NA][VW]
@@ -153,20 +164,22 @@ __host__ __device__ inline size_t pipe_layout(const Geo &G, int N, int TB, PSmem
     if (S) S->flgT = (int *)p;
     p = take(sizeof(int) * MISC_INTS);
     if (S) S->misc = (int *)p;
-    p = take(sizeof(int) * TB_MAX * TI);
+    p = take(sizeof(int) * 2 * TB_MAX * TI);
     if (S) S->tinfo = (int *)p;
-    p = take(sizeof(long long) * 2 * (size_t)G.WW);
+    p = take(sizeof(int) * 2 * DESC_INTS);
+    if (S) S->desc = (int *)p;
+    p = take(sizeof(long long) * 4 * (size_t)G.WW);
     if (S) S->win = (long long *)p;
     p = take(sizeof(uint32_t) * (size_t)G.WW);
     if (S) S->dig = (uint32_t *)p;
     const size_t u0 = o;
     p = take(sizeof(long long) * (size_t)G.P1 * 2 * (W + 2));
     if (S) S->stage = (long long *)p;
-    p = take(sizeof(uint32_t) * 2 * (size_t)TB * G.Lp);
+    p = take(sizeof(uint32_t) * (size_t)TB * G.Lp);
     if (S) S->araw = (uint32_t *)p;
     p = take(sizeof(uint32_t) * 2 * (size_t)TB * G.VW);
     if (S) S->cc = (uint32_t *)p;
-    p = take(sizeof(uint32_t) * (size_t)TB * G.VW);
+    p = take(sizeof(uint32_t) * 2 * (size_t)TB * G.VW);
     if (S) S->ash = (uint32_t *)p;
     const size_t worker_end = o;
     o = u0;
@@ -186,16 +199,16 @@ __host__ __device__ inline size_t pipe_layout(const Geo &G, int N, int TB, PSmem
 
 __device__ __forceinline__ long long &ll_at(int *misc, int slot) { return ((long long *)(misc + slot))[0]; }
 
-// Per-phase cycle counters of thread 0 of one closer CTA and of the last
-// worker, accumulated in shared memory and written out at the end.
+// Per-phase cycle counters of one thread (`who`) of a CTA, accumulated in
+// shared memory and written out at the end.
 struct Prof {
     long long *p;
     long long t;
-    __device__ Prof(const KArgs &a, bool on, int *misc)
+    __device__ Prof(const KArgs &a, bool on, int *misc, int who = 0)
     {
         p = nullptr;
         t = 0;
-        if (a.prof && on && threadIdx.x == 0) {
+        if (a.prof && on && threadIdx.x == (unsigned)who) {
             p = (long long *)(misc + MS_PROF);
             t = clock64();
         }
@@ -306,6 +319,27 @@ __device__ __forceinline__ void unit_walk(const Geo &G, const uint32_t *Abase, c
     }
 }
 
+// A thread group of the CTA: the whole CTA (bar 0, __syncthreads) or a set of
+// whole warps synchronised by named barrier `bar`; t is the thread's index in
+// the group, n the group's size.
+struct Grp {
+    int t, n, bar;
+};
+__device__ __forceinline__ void named_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void grp_sync(const Grp &g)
+{
+    if (g.bar == 0) __syncthreads();
+    else named_sync(g.bar, g.n);
+}
+__device__ __forceinline__ Grp whole_cta() { return Grp{(int)threadIdx.x, PT, 0}; }
+
 // Reduce-scatter of NV values over the 2^LOG lanes r = 0.. of an aligned lane
 // group: lane r ends with NV >> LOG sums, of the values base .. base +
 // (NV >> LOG) - 1; returns base.  Each step swaps half of the values with
@@ -337,23 +371,24 @@ __device__ __forceinline__ int reduce_scatter(long long (&v)[NV], int r)
 // `tinfo`, slots flagged negative hold the complement of the shifted first
 // factor over its Lp limbs, and the complement's correction
 // (+C 2^(32 d) + ~C 2^(32 (d+Lp)) + 2^(32 (d+Lp)) - 2^(32 (d+2Lp))) is added
-// as well.  neg_all negates the whole sum.  Every thread of the CTA calls
-// this.  RS = 2^LOG threads share a unit (RS (P+1) <= PT), always
+// as well.  neg_all negates the whole sum.  Every thread of group g calls
+// this (its first thread is a warp's first).  RS = 2^LOG threads share a
+// unit (RS (P+1) <= g.n), always
 // inside one warp, so their shares are combined by a reduce-scatter of the
 // unit's 2 (W+2) digits (block 0, block 1) and each lane stores its part;
 // then one thread per window column adds the column (with the complement
 // corrections).  Only the first RS (P+1) threads walk.  `stage` holds
-// (P+1) 2 (W+2) long longs.  Starts and ends with __syncthreads.
+// (P+1) 2 (W+2) long longs.  Starts and ends with a barrier of the group.
 template <int LOG>
-__device__ void small_products_t(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
-                                 int n, const int *tinfo, bool neg_all, long long *stage,
-                                 long long *win, int coff)
+__device__ void small_products_t(const Geo &G, const Grp &gr, const uint32_t *Abase,
+                                 const uint32_t *Cbase, int s0, int n, const int *tinfo,
+                                 bool neg_all, long long *stage, long long *win, int coff)
 {
     constexpr int ND = W + 2;
     constexpr int RS = 1 << LOG;
     constexpr int NV = ((2 * ND + RS - 1) / RS) * RS;  // the digits, padded to a multiple of RS
-    const int tid = threadIdx.x;
-    __syncthreads();
+    const int tid = gr.t;
+    grp_sync(gr);
     if (tid < ((G.P1 * RS + 31) & ~31) && n > 0) {
         uint32_t a0[W], a1[W], a2[W], x0[W], x1[W], x2[W];
 #pragma unroll
@@ -378,9 +413,9 @@ __device__ void small_products_t(const Geo &G, const uint32_t *Abase, const uint
                 if (base + i < 2 * ND) d[base + i] = v[i];
         }
     }
-    __syncthreads();
+    grp_sync(gr);
     if (n > 0) {
-        for (int c = tid; c < G.GW; c += PT) {
+        for (int c = tid; c < G.GW; c += gr.n) {
             long long s = 0;
             if (c < G.M + 2) {
                 const int u = c / W;
@@ -408,19 +443,19 @@ __device__ void small_products_t(const Geo &G, const uint32_t *Abase, const uint
             if (s) win[coff + c] += neg_all ? -s : s;
         }
     }
-    __syncthreads();
+    grp_sync(gr);
 }
 
-// RS threads per unit: a power of two from 2 to 16 with RS (P+1) <= PT
-__device__ void small_products(const Geo &G, int RS, const uint32_t *Abase, const uint32_t *Cbase,
-                               int s0, int n, const int *tinfo, bool neg_all, long long *stage,
-                               long long *win, int coff)
+// RS threads per unit: a power of two from 2 to 16 with RS (P+1) <= gr.n
+__device__ void small_products(const Geo &G, int RS, const Grp &gr, const uint32_t *Abase,
+                               const uint32_t *Cbase, int s0, int n, const int *tinfo, bool neg_all,
+                               long long *stage, long long *win, int coff)
 {
     switch (RS) {
-    case 16: small_products_t<4>(G, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
-    case 8: small_products_t<3>(G, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
-    case 4: small_products_t<2>(G, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
-    default: small_products_t<1>(G, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
+    case 16: small_products_t<4>(G, gr, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
+    case 8: small_products_t<3>(G, gr, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
+    case 4: small_products_t<2>(G, gr, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
+    default: small_products_t<1>(G, gr, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff); break;
     }
 }
 
@@ -492,20 +527,18 @@ __device__ void outer_window(const KArgs &a, const int *expT, const int *flgT, i
     }
 }
 
-// cp.async the factors of slots [0, nb) of the batch (m, tb0) into buffer
-// buf, 16 bytes a copy (the first factor plain, the second into its cyclic
-// layout: a group of W limbs is two 16-byte pieces); mode 0 every slot, 1 all
-// but the late ones, 2 only the late ones (late: a factor is coefficient m-2)
-__device__ void issue_loads(PSmem &S, const KArgs &a, const Geo &G, int TB, int buf, int role, int m,
-                            int tb0, int nb, int mode)
+// cp.async the factors of slots [0, nb) of the batch (m, tb0), 16 bytes a
+// copy: the first factors plain into araw, the second factors into their
+// cyclic layout in cc[buf] (a group of W limbs is two 16-byte pieces).
+// Control group, one warp per slot.
+__device__ void ctl_issue_loads(PSmem &S, const KArgs &a, const Geo &G, int TB, int buf, int role,
+                                int m, int tb0, int nb, int ct)
 {
-    const int Lp = G.Lp, q4 = Lp / 4, lane = threadIdx.x & 31;
-    for (int sl = threadIdx.x >> 5; sl < nb; sl += NWARPS) {  // one warp per slot
+    const int Lp = G.Lp, q4 = Lp / 4, lane = ct & 31;
+    for (int sl = ct >> 5; sl < nb; sl += CW) {
         int tg, arow, crow, aa;
         inner_term(role, m, tb0 + sl, G.N1, tg, arow, crow, aa);
-        const bool late = (aa == m - 2) || (aa == 2);
-        if ((mode == 1 && late) || (mode == 2 && !late)) continue;
-        uint32_t *ar = S.araw + ((size_t)buf * TB + sl) * Lp;
+        uint32_t *ar = S.araw + (size_t)sl * Lp;
         uint32_t *cr = S.cc + ((size_t)buf * TB + sl) * G.VW;
         const uint32_t *ga = a.coefL + (size_t)arow * Lp, *gc = a.coefL + (size_t)crow * Lp;
         for (int x = lane; x < q4; x += 32) {
@@ -516,15 +549,18 @@ __device__ void issue_loads(PSmem &S, const KArgs &a, const Geo &G, int TB, int 
     }
 }
 
-// term info (warp 0), staged first factors and term groups of the batch in
-// buffer buf
-__device__ void prepare_batch(PSmem &S, const KArgs &a, const Geo &G, int TB, int buf, int role,
-                              int m, int tb0, int nb)
+// Term info and term groups of the batch (control warp 0), then the first
+// factors shifted by d_lo (complemented when negative) into ash[buf]; the
+// batch's descriptor.  Window bases at MS_WLO.  Control group; the loads of
+// the batch have landed.
+__device__ void ctl_prepare(PSmem &S, const Geo &G, int TB, int buf, int role, int m, int tb0,
+                            int nb, int par, int ct)
 {
-    (void)a;
-    if (threadIdx.x < 32) {
+    int *desc = S.desc + buf * DESC_INTS;
+    int *tinfo = S.tinfo + buf * TB_MAX * TI;
+    if (ct < 32) {
         const long long *wlo = (const long long *)(S.misc + MS_WLO);
-        const int lane = threadIdx.x;
+        const int lane = ct;
         int key = -1;
         if (lane < nb) {
             int tg, arow, crow, aa;
@@ -536,7 +572,7 @@ __device__ void prepare_batch(PSmem &S, const KArgs &a, const Geo &G, int TB, in
                 d = (int)((long long)S.expT[arow] + S.expT[crow] - 2LL * G.L - wlo[tg]);
                 key = (tg << 20) | (d >> 3);
             }
-            int *ti = S.tinfo + lane * TI;
+            int *ti = tinfo + lane * TI;
             ti[0] = tg;
             ti[1] = neg;
             ti[2] = d & 7;
@@ -548,30 +584,70 @@ __device__ void prepare_batch(PSmem &S, const KArgs &a, const Geo &G, int TB, in
         const bool en = key >= 0 && (lane == 31 || knext != key);
         const unsigned Sm = __ballot_sync(FULL, st), Em = __ballot_sync(FULL, en);
         const unsigned lt = (1u << lane) - 1u;
-        if (st) S.misc[MS_RUN + __popc(Sm & lt)] = lane;
-        if (en) S.misc[MS_RUNE + __popc(Em & lt)] = lane + 1;
-        if (lane == 0) S.misc[MS_NRUN] = __popc(Sm);
+        if (st) desc[DS_RUN + __popc(Sm & lt)] = lane;
+        if (en) desc[DS_RUNE + __popc(Em & lt)] = lane + 1;
+        if (lane == 0) {
+            desc[DS_EXIT] = 0;
+            desc[DS_NRUN] = __popc(Sm);
+            desc[DS_PAR] = par;
+        }
     }
-    __syncthreads();
-    for (int sl = threadIdx.x >> 5; sl < nb; sl += NWARPS) {  // one warp per slot
-        const int *ti = S.tinfo + sl * TI;
+    named_sync(BAR_CT, CT);
+    for (int sl = ct >> 5; sl < nb; sl += CW) {  // one warp per slot
+        const int *ti = tinfo + sl * TI;
         if (ti[4] < 0) continue;
         const int dl = ti[2];
         const uint32_t inv = ti[1] ? 0xffffffffu : 0u;
-        const uint32_t *src = S.araw + ((size_t)buf * TB + sl) * G.Lp;
-        uint32_t *dst = S.ash + (size_t)sl * G.VW;
-        for (int x = threadIdx.x & 31; x < G.M; x += 32) {
+        const uint32_t *src = S.araw + (size_t)sl * G.Lp;
+        uint32_t *dst = S.ash + ((size_t)buf * TB + sl) * G.VW;
+        for (int x = ct & 31; x < G.M; x += 32) {
             const int y = x - dl;
             dst[gpos(x)] = (y >= 0 && y < G.Lp) ? (src[y] ^ inv) : 0u;
         }
     }
-    __syncthreads();
+    named_sync(BAR_CT, CT);
 }
 
-// Workers (role 0) and outer-pair CTAs (role 1 + target).
-__device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &G)
+// bounded wait of the control group until *flag >= target (its first thread
+// polls); false (group-uniform) when the launch must stop.  The compute
+// warps keep running meanwhile, so the poll is a relaxed load (an acquire
+// load may invalidate the SM's L1 on every poll) with one acquire at the end.
+__device__ bool ctl_wait_geq(PSmem &S, const KArgs &a, const unsigned *flag, unsigned target, int ct)
 {
-    const int N1 = G.N1, Lp = G.Lp, TB = pa.tb;
+    if (ct == 0) {
+        int st = 0;
+        long long it = 0;
+        while ((int)(ld_relaxed_u32(flag) - target) < 0) {
+            if (++it > a.spin_limit) {
+                atomicCAS(a.status, 0, DEV_TIMEOUT);
+                st = DEV_TIMEOUT;
+                break;
+            }
+            if ((it & 63) == 0) {
+                st = ld_relaxed_int(a.status);
+                if (st) break;
+            }
+            __nanosleep(64);
+        }
+        (void)ld_acquire_u32(flag);  // pairs with the publisher's release
+        if (!st) st = ld_relaxed_int(a.status);
+        S.misc[MS_STATUS] = st;
+    }
+    named_sync(BAR_CT, CT);
+    return S.misc[MS_STATUS] == 0;
+}
+
+// The control group of a worker or outer-pair CTA (roles 0 and 1 + target):
+// per index it waits for the coefficient its terms need, places the window,
+// loads and stages each batch of terms into the free buffer and hands it to
+// the compute group, and once the compute group is through an index's last
+// batch, adds that window into the global set and counts the CTA done.
+// Consecutive indices with terms alternate between two windows, so that the
+// flush of one overlaps the products of the next.
+__device__ void worker_control(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &G)
+{
+    const int ct = threadIdx.x - KT;
+    const int N1 = G.N1, TB = pa.tb;
     const int role = blockIdx.x < (unsigned)NFIX ? 1 + (int)blockIdx.x - NCL : 0;
     const int nw = gridDim.x - NFIX;
     const int w = blockIdx.x - NFIX;
@@ -594,43 +670,81 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             tb = (int)(2u * Tt * (unsigned)(w + 1) / (unsigned)nw);
         }
     };
-    const bool prof_on = true;
-    // zero padding of the second factors stays zero; windows start empty
-    for (int e = threadIdx.x; e < 2 * TB * G.M; e += PT) {
-        const int s = e / G.M, x = e - s * G.M;
-        if (x >= Lp) S.cc[(size_t)s * G.VW + gpos(x)] = 0u;
-    }
-    for (int e = threadIdx.x; e < 2 * G.WW; e += PT) S.win[e] = 0;
-    __syncthreads();
-    int bcount = 0;        // batches so far (buffer = parity)
-    bool pf = false;       // the batch at (pf_step, pf_m, pf_tb0) is loading
-    bool pf_late = false;  // ... without its late terms
-    long long pf_step = -1;
-    int pf_m = -1, pf_tb0 = -1;
-    for (long long step = 0; step < a.nsteps; step++) {
+    Prof pr(a, true, S.misc, KT);
+    long long k = 0, kdone = 0;  // batches handed over; batches the compute group is through
+    auto consumed = [&](long long upto) {
+        while (kdone < upto) {
+            named_sync(BAR_EMPTY + (int)(kdone & 1), PT);
+            kdone++;
+        }
+    };
+    auto flush = [&](int set, int par) {
+        for (int tg = 0; tg < 2; tg++) {
+            const int wd = S.misc[MS_WID + 2 * par + tg];
+            long long *src = S.win + (size_t)(2 * par + tg) * G.WW;
+            long long *dst = pa.gin + (((size_t)set * 2 + tg) * 2 + (role ? 1 : 0)) * a.Wcap;
+            for (int c = ct; c < wd; c += CT) {
+                const long long v = src[c];
+                if (v) {
+                    atomicAdd((unsigned long long *)&dst[c], (unsigned long long)v);
+                    src[c] = 0;
+                }
+            }
+        }
+        named_sync(BAR_CT, CT);
+        if (ct == 0) {
+            __threadfence();
+            atomicAdd(&pa.done[set], 1u);
+        }
+    };
+    bool pend = false;  // an index (global number pend_g) whose window awaits its flush
+    int pend_set = 0, pend_par = 0, wpar = 0;
+    long long pend_last = 0, pend_g = 0;
+    auto flush_pending = [&]() {
+        consumed(pend_last + 1);
+        flush(pend_set, pend_par);
+        pend = false;
+        pr.mark(PR_CLOSE);
+    };
+    bool ok = true;
+    for (long long step = 0; step < a.nsteps && ok; step++) {
         for (int m = 0; m < a.N; m++) {
             const long long g = step * a.N + m;
             const int set = (int)(g % PIPE_SETS);
             if (m < (role ? 2 : 4)) {  // no pairs; keep the completion counts uniform
-                if (threadIdx.x == 0) atomicAdd(&pa.done[set], 1u);
+                if (ct == 0) atomicAdd(&pa.done[set], 1u);
                 continue;
             }
-            Prof pr(a, prof_on, S.misc);
-            if (!wait_geq(S, a, pa.pub, (unsigned)(3 * (step * N1 + m + 1 - lag)))) {
-                cp_async_wait<0>();
-                return;
+            // the coefficient awaited, m - lag, comes out of the brackets'
+            // index g - lag - 1, which needs the windows of every index up to
+            // that one: a pending one among them is flushed first
+            if (pend && pend_g <= g - lag - 1) flush_pending();
+            // every index waits for its coefficient, so that no CTA runs more
+            // than a few indices ahead of the brackets (the sets are reused)
+            if (!ctl_wait_geq(S, a, pa.pub, (unsigned)(3 * (step * N1 + m + 1 - lag)), ct)) {
+                ok = false;
+                break;
             }
-            pr.mark(PR_BARRIER);
-            if (threadIdx.x < 3) {
-                const int idx = threadIdx.x * N1 + m - lag;
+            pr.mark(PR_X1);
+            int tA = 0, tB = m == 2 ? 1 : 2;  // outer pairs: all of them
+            if (role == 0) range_of(m, tA, tB);
+            // the exponents of the new coefficient, needed by later indices
+            // even when this one has no terms here
+            if (ct < 3) {
+                const int idx = ct * N1 + m - lag;
                 S.expT[idx] = __ldcg(&a.coefE[idx]);
                 S.flgT[idx] = __ldcg(&a.coefF[idx]);
-            } else if (role == 0 && threadIdx.x >= 32 && threadIdx.x < 36) {
-                ((long long *)(S.misc + MS_BK))[threadIdx.x - 32] = __ldcg(&pa.imid[(size_t)set * 4 + threadIdx.x - 32]);
+            } else if (role == 0 && ct >= 32 && ct < 36 && tB > tA) {
+                ((long long *)(S.misc + MS_BK))[ct - 32] = __ldcg(&pa.imid[(size_t)set * 4 + ct - 32]);
             }
-            __syncthreads();
-            pr.mark(PR_X4);
-            if (threadIdx.x == 0) {
+            if (tB <= tA) {  // no terms here: nothing to add
+                if (ct == 0) atomicAdd(&pa.done[set], 1u);
+                continue;
+            }
+            const int par = wpar;
+            wpar ^= 1;
+            named_sync(BAR_CT, CT);
+            if (ct == 0) {
                 long long lo[2], hi[2];
                 if (role == 0) {
                     inner_window(a, (const long long *)(S.misc + MS_BK), S.expT, S.flgT, m, lo, hi);
@@ -655,90 +769,91 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                         }
                     }
                     ll_at(S.misc, MS_WLO + 2 * tg) = hi[tg] > lo[tg] ? lo[tg] : 0;
-                    S.misc[MS_WID + tg] = width;
+                    S.misc[MS_WID + 2 * par + tg] = width;
                 }
             }
-            __syncthreads();
+            named_sync(BAR_CT, CT);
             pr.mark(PR_PLACE);
             if (S.misc[MS_STATUS] != 0) {
-                cp_async_wait<0>();
-                return;
+                ok = false;
+                break;
             }
-            int tA = 0, tB = m == 2 ? 1 : 2;  // outer pairs: all of them
-            if (role == 0) range_of(m, tA, tB);
+            bool first = true;
             for (int tb0 = tA; tb0 < tB; tb0 += TB) {
                 const int nb = min(TB, tB - tb0);
-                const int buf = bcount & 1;
-                const bool was_pf = pf && pf_step == step && pf_m == m && pf_tb0 == tb0;
-                if (!was_pf) issue_loads(S, a, G, TB, buf, role, m, tb0, nb, 0);
-                else if (pf_late) issue_loads(S, a, G, TB, buf, role, m, tb0, nb, 2);
-                cp_async_commit();
-                pr.mark(PR_X3);
-                // prefetch the next batch: the rest of this index, or the first
-                // batch of index m+1 without its late terms
-                pf = false;
-                if (tb0 + TB < tB) {
-                    pf = true;
-                    pf_late = false;
-                    pf_step = step;
-                    pf_m = m;
-                    pf_tb0 = tb0 + TB;
-                    issue_loads(S, a, G, TB, buf ^ 1, role, m, pf_tb0, min(TB, tB - pf_tb0), 0);
-                } else if (role == 0 && m + 1 < a.N) {
-                    int tA2, tB2;
-                    range_of(m + 1, tA2, tB2);
-                    if (tB2 > tA2) {
-                        pf = true;
-                        pf_late = true;
-                        pf_step = step;
-                        pf_m = m + 1;
-                        pf_tb0 = tA2;
-                        issue_loads(S, a, G, TB, buf ^ 1, role, m + 1, tA2, min(TB, tB2 - tA2), 1);
-                    }
-                }
-                cp_async_commit();
-                pr.mark(PR_X1);
-                cp_async_wait<1>();
-                __syncthreads();
+                const int buf = (int)(k & 1);
+                consumed(k - 1);  // the buffer's previous batch is through
                 pr.mark(PR_STAGE);
-                prepare_batch(S, a, G, TB, buf, role, m, tb0, nb);
+                ctl_issue_loads(S, a, G, TB, buf, role, m, tb0, nb, ct);
+                cp_async_commit();
+                cp_async_wait<0>();
+                named_sync(BAR_CT, CT);
+                ctl_prepare(S, G, TB, buf, role, m, tb0, nb, par, ct);
+                named_arrive(BAR_FULL + buf, PT);
+                k++;
                 pr.mark(PR_FLUSH);
-                const int nrun = S.misc[MS_NRUN];
-                if (pr.p) {  // counts: term groups (slot PR_X2), terms (slot PR_X6)
-                    pr.p[PR_X2] += nrun;
-                    pr.p[PR_X6] += nb;
-                }
-                for (int rr = 0; rr < nrun; rr++) {
-                    const int rs = S.misc[MS_RUN + rr], re = S.misc[MS_RUNE + rr];
-                    const int *ti = S.tinfo + rs * TI;
-                    small_products(G, G.RSW, S.ash, S.cc + (size_t)buf * TB * G.VW, rs, re - rs, S.tinfo,
-                                   false, S.stage, S.win + (size_t)ti[0] * G.WW, ti[3] * W);
-                }
-                pr.mark(PR_MAC);
-                bcount++;
+                if (first && pend) flush_pending();  // the previous window (other parity)
+                first = false;
             }
-            // the CTA's windows into the global set
-            for (int tg = 0; tg < 2; tg++) {
-                const int wd = S.misc[MS_WID + tg];
-                long long *src = S.win + (size_t)tg * G.WW;
-                long long *dst = pa.gin + (((size_t)set * 2 + tg) * 2 + (role ? 1 : 0)) * a.Wcap;
-                for (int c = threadIdx.x; c < wd; c += PT) {
-                    const long long v = src[c];
-                    if (v) {
-                        atomicAdd((unsigned long long *)&dst[c], (unsigned long long)v);
-                        src[c] = 0;
-                    }
-                }
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                __threadfence();
-                atomicAdd(&pa.done[set], 1u);
-            }
-            pr.mark(PR_CLOSE);
+            pend = true;
+            pend_set = set;
+            pend_par = par;
+            pend_last = k - 1;
+            pend_g = g;
         }
     }
+    if (ok && pend) flush_pending();
+    // hand the compute group its exit
+    consumed(k - 1);
+    if (ct == 0) S.desc[(k & 1) * DESC_INTS + DS_EXIT] = 1;
+    named_arrive(BAR_FULL + (int)(k & 1), PT);
     cp_async_wait<0>();
+}
+
+// The compute group: the products of each batch handed over, into the
+// window of its parity.
+__device__ void worker_compute(PSmem &S, const Geo &G, const PArgs &pa, const KArgs &a)
+{
+    const Grp gr{(int)threadIdx.x, KT, BAR_KT};
+    const int TB = pa.tb;
+    Prof pr(a, true, S.misc, 0);
+    for (long long k = 0;; k++) {
+        const int b = (int)(k & 1);
+        named_sync(BAR_FULL + b, PT);
+        pr.mark(PR_BARRIER);
+        const int *desc = S.desc + b * DESC_INTS;
+        if (desc[DS_EXIT]) break;
+        const int nrun = desc[DS_NRUN], par = desc[DS_PAR];
+        const int *tinfo = S.tinfo + b * TB_MAX * TI;
+        if (pr.p) {  // counts: term groups (slot PR_X2)
+            pr.p[PR_X2] += nrun;
+        }
+        for (int rr = 0; rr < nrun; rr++) {
+            const int rs = desc[DS_RUN + rr], re = desc[DS_RUNE + rr];
+            const int *ti = tinfo + rs * TI;
+            if (pr.p) pr.p[PR_X6] += re - rs;
+            small_products(G, G.RSW, gr, S.ash + (size_t)b * TB * G.VW, S.cc + (size_t)b * TB * G.VW,
+                           rs, re - rs, tinfo, false, S.stage, S.win + (size_t)(2 * par + ti[0]) * G.WW,
+                           ti[3] * W);
+        }
+        named_arrive(BAR_EMPTY + b, PT);
+        pr.mark(PR_MAC);
+    }
+}
+
+__device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &G)
+{
+    // zero padding of the second factors stays zero; windows start empty
+    for (int e = threadIdx.x; e < 2 * pa.tb * G.M; e += PT) {
+        const int s = e / G.M, x = e - s * G.M;
+        if (x >= G.Lp) S.cc[(size_t)s * G.VW + gpos(x)] = 0u;
+    }
+    for (int e = threadIdx.x; e < 4 * G.WW; e += PT) S.win[e] = 0;
+    __syncthreads();
+    if (threadIdx.x < (unsigned)KT)
+        worker_compute(S, G, pa, a);
+    else
+        worker_control(S, a, pa, G);
 }
 
 // ------------------------------------------------------------------ bracket CTAs
@@ -1018,7 +1133,7 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
             width = (int)(hi - lo);
         }
         if (prod)
-            small_products(G, G.RS, hA, tauC, 0, 1, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.bstage, win,
+            small_products(G, G.RS, whole_cta(), hA, tauC, 0, 1, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.bstage, win,
                            (int)(lpp - lo));
         pr.mark(PR_HMAC);
         if (lone) {
@@ -1161,7 +1276,7 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             const int nrun = S.misc[MS_NRUN];
             for (int rr = 0; rr < nrun; rr++) {
                 const int rs = S.misc[MS_RUN + rr], re = S.misc[MS_RUNE + rr];
-                small_products(G, G.RS, S.vA, S.vC, rs, re - rs, S.tinfo, false, S.bstage, win,
+                small_products(G, G.RS, whole_cta(), S.vA, S.vC, rs, re - rs, S.tinfo, false, S.bstage, win,
                                S.tinfo[rs * TI + 3] * W);
             }
             pr.mark(PR_MAC);
@@ -1283,6 +1398,7 @@ __global__ void __launch_bounds__(PT, 1) pipe_kernel(KArgs a, PArgs pa)
         closer_loop(S, a, pa, G);
     else
         worker_loop(S, a, pa, G);
+    __syncthreads();
     tot.mark(PR_TOTAL);
     if (a.prof && threadIdx.x == 0) {
         // rows 0 and 1: the beta' bracket CTA and the last worker; then one row per CTA
