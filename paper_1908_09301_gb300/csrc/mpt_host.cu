@@ -86,7 +86,7 @@ struct mpt_ctx {
     long long spin_limit = mpt::DEFAULT_SPIN_LIMIT;
     // pipelined kernel (bracket and outer-pair CTAs + workers)
     int kind_req = 0;           // 0 auto, 1 lockstep, 2 pipelined
-    int pipe_C = 5;             // CTAs with fixed roles in the pipelined kernel (fixed by the kernel)
+    int pipe_C = 10;            // CTAs with fixed roles in the pipelined kernel (fixed by the kernel)
     int pipe_max_grid = 0;      // co-resident CTAs of the pipelined kernel
     int pipe_tb = 0;
     size_t pipe_smem = 0;
@@ -347,7 +347,7 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
     if (ce == cudaSuccess) ce = dalloc(&c->status, 1);
     if (ce == cudaSuccess) ce = dalloc(&c->pub, 1);
     if (ce == cudaSuccess) ce = dalloc(&c->done, mpt::PIPE_SETS);
-    if (ce == cudaSuccess) ce = dalloc(&c->gin, (size_t)mpt::PIPE_SETS * 4 * c->Wcap);
+    if (ce == cudaSuccess) ce = dalloc(&c->gin, (size_t)mpt::PIPE_SETS * 9 * c->Wcap);
     if (ce == cudaSuccess) ce = dalloc(&c->imid, (size_t)mpt::PIPE_SETS * 4);
     if (ce != cudaSuccess) {
         free_all(c);
@@ -562,7 +562,7 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
         ce = cudaMemsetAsync(c->pub, 0, sizeof(unsigned), c->st);
         if (ce == cudaSuccess) ce = cudaMemsetAsync(c->done, 0, sizeof(unsigned) * mpt::PIPE_SETS, c->st);
         if (ce == cudaSuccess)
-            ce = cudaMemsetAsync(c->gin, 0, sizeof(long long) * mpt::PIPE_SETS * 4 * c->Wcap, c->st);
+            ce = cudaMemsetAsync(c->gin, 0, sizeof(long long) * mpt::PIPE_SETS * 9 * c->Wcap, c->st);
         if (ce == cudaSuccess) ce = mpt::launch_pipe(a, pa, pipe_grid_for(c), c->pipe_smem, c->st);
     } else {
         ce = mpt::launch_integrate(a, grid_for(c), c->smem, c->st);

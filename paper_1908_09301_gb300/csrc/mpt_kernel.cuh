@@ -68,14 +68,14 @@ enum ProfSlot {
     PROF_SLOTS = 16
 };
 
-// pipelined kernel: bracket CTAs, outer-pair CTAs and workers
+// pipelined kernel: bracket, outer-pair and edge CTAs, and workers
 constexpr int PIPE_SETS = 8;  // rotating global accumulator sets / completion counters
 
 struct PArgs {
     unsigned *pub;    // [1] component publications of the launch (monotone, 3 per coefficient)
     unsigned *done;   // [PIPE_SETS] non-bracket CTAs finished with an index (monotone)
-    long long *gin;   // [PIPE_SETS][2 targets][2 parts][Wcap] Cauchy sums (targets beta',
-                      // gamma'; parts: middle pairs, outer pairs)
+    long long *gin;   // [PIPE_SETS][3 brackets][3 parts][Wcap] sums the other CTAs add to the
+                      // brackets alpha', beta', gamma' (parts: middle pairs, outer pairs, edge terms)
     long long *imid;  // [PIPE_SETS][4] middle-pair windows without their two newest pairs
     int C;            // CTAs with fixed roles (pipe_fixed_ctas())
     int tb;           // worker term slots per batch (<= pipe_tb_max())
@@ -83,7 +83,7 @@ struct PArgs {
 
 size_t pipe_smem_bytes(int L, int Lp, int N, int Wcap, int tb);
 int pipe_tb_max();
-// CTAs with fixed roles (brackets, outer pairs); a launch needs at least one more
+// CTAs with fixed roles (brackets, outer pairs, edge terms); a launch needs at least one more
 int pipe_fixed_ctas();
 // co-resident CTAs of the pipelined kernel (one per SM at most; 0 on error)
 int pipe_max_ctas(size_t smem);

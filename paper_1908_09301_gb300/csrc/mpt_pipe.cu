@@ -1,33 +1,35 @@
 // mpt_pipe.cu -- pipelined multiple-precision Taylor step (Sec. 2 of Dimova
 // et al., arXiv 1908.09301) for large L x N: one persistent cooperative
-// launch, one CTA per SM, three roles.  Eq. (3)'s Cauchy sums of index m,
-//     Y_m = -sum_{a=1}^{m-1} alpha_a gamma_{m-a},  Z_m = sum_{a=1}^{m-1} alpha_a beta_{m-a},
+// launch, one CTA per SM, four roles.  Eq. (3)'s Cauchy sums of index m,
+//     sum_{a=0}^{m} alpha_a gamma_{m-a},  sum_{a=0}^{m} alpha_a beta_{m-a},
 // are split by the newest coefficient they need, so that each part starts as
 // early as it can:
 //
-//  * Workers (CTAs 5 and up) take the middle pairs a = 2..m-2, which need
+//  * Workers (CTAs 10 and up) take the middle pairs a = 2..m-2, which need
 //    coefficients up to m-2 only, so they run while the bracket CTAs are
 //    still finishing coefficients m-1 and m.  A worker takes a contiguous
-//    range of the 2(m-3) terms.  All of its terms of one target are summed in
-//    one frame: a term whose lowest limb lies d = 8 d_hi + d_lo limbs above
-//    the window base has its first factor staged shifted up by d_lo limbs
-//    (and complemented when the term is negative; the complement's
-//    correction is added separately), so the terms with equal d_hi share
-//    columns and are accumulated in the same registers.
-//  * The outer-pair CTAs 3 (target Y) and 4 (target Z) take the pairs a = 1
-//    and a = m-1 as soon as coefficient m-1 is out.
+//    range of one target's m-3 terms.  All of its terms are summed in one
+//    frame: a term whose lowest limb lies d = 8 d_hi + d_lo limbs above the
+//    window base has its first factor staged shifted up by d_lo limbs (and
+//    complemented when the term is negative; the complement's correction is
+//    added separately), so the terms with equal d_hi share columns and are
+//    accumulated in the same registers.  Two warps of a worker (control)
+//    wait, load, stage and flush while the other fourteen (compute) run the
+//    products.
+//  * The outer-pair CTAs 3 (beta') and 4 (gamma') take the pairs a = 1 and
+//    a = m-1 as soon as coefficient m-1 is out.
+//  * The edge CTAs 5..9 take the terms with coefficient m itself (the pairs
+//    a = 0 and a = m, and products with a parameter of more than one limb,
+//    such as b gamma_m), one term each, as soon as coefficient m is out.
 //  * The bracket CTAs 0, 1, 2 own Eq. (3)'s brackets alpha', beta', gamma'.
-//    Each forms its products of the newest coefficient m with numbers fixed
-//    for the step (beta': alpha_m gamma_0, gamma_m alpha_0; gamma':
-//    alpha_m beta_0, beta_m alpha_0, gamma_m b) as one term group, adds its
-//    one-limb and lone terms and the other CTAs' sums, normalises, divides by
-//    (m+1) and publishes its component of coefficient m+1; the three
-//    exchange components through global memory.  After index N-1 each runs
-//    the Horner chain of Eq. (2) for its component,
+//    Each adds its one-limb and lone terms and the other CTAs' sums,
+//    normalises, divides by (m+1) and publishes its component of coefficient
+//    m+1; the three exchange components through global memory.  After index
+//    N-1 each runs the Horner chain of Eq. (2) for its component,
 //    h_i = trunc_L(tau h_{i+1} + c_i).
 //
-// Workers and outer-pair CTAs add their windows into a global window set
-// (one part each) and count themselves done.
+// The non-bracket CTAs add their windows into a global window set (one part
+// per kind) and count themselves done.
 //
 // Limb products use units: unit q of a product A' * C (A' of M = (P+1)W
 // limbs, C of Lp limbs) owns columns qW..qW+W-1 of two blocks (block 1 is M
@@ -53,10 +55,11 @@ namespace {
 
 constexpr int NCL = 3;           // bracket CTAs
 constexpr int NOUT = 2;          // outer-pair CTAs (one per target: beta', gamma')
-constexpr int NFIX = NCL + NOUT; // CTAs with fixed roles; workers follow
-constexpr int NTERM = 3;         // product terms of a bracket
-constexpr int NA = NTERM + 1;    // A' slots of a bracket CTA: product terms, Horner's h
-constexpr int NC = NTERM + 1;    // C slots: fixed factors, tau
+constexpr int NEDGE = 5;         // edge CTAs (products with the newest coefficient)
+constexpr int NFIX = NCL + NOUT + NEDGE;  // CTAs with fixed roles; workers follow
+constexpr int NA = 2;            // A' slots of a bracket / edge CTA (Horner's h: slot 0)
+constexpr int NC = 2;            // C slots (tau: slot 0)
+constexpr int GIN_PARTS = 3;     // parts of a bracket's global window: middle, outer, edge
 constexpr int TI = 8;            // ints of term info per slot
 constexpr int TB_MAX = 32;       // worker slots per batch (one warp finds the groups)
 // a worker CTA's two groups: control warps (waits, loads, staging, flushes)
@@ -74,7 +77,7 @@ enum { P_SIGMA = 0, P_R = 1, P_B = 2, P_TAU = 3 };
 
 enum {
     MS_STATUS = 0,  // CTA-uniform copy of the status word
-    MS_NRUN = 1,    // term groups of the batch / bracket
+    MS_NRUN = 1,    // (unused)
     MS_NEWE = 2,    // [2] exponent and flags of this CTA's newest number
     MS_PSCAL = 8,   // [3][2] sigma, R, b: single non-zero limb index (or -1), value
     MS_WLO = 16,    // [4] long long window bases (ints 16..23)
@@ -98,7 +101,8 @@ enum {
     BK_SV = 12,     // [2] scaled: the parameter's limb
     BK_INNER = 14,  // offset of the workers' sums (or -1)
     BK_IWIDTH = 15,
-    BK_TERM = 16,   // [NTERM][4]: present, component of A, neg, d
+    BK_EINNER = 16, // offset of the edge-term sums (or -1)
+    BK_EWIDTH = 17,
     BK_OINNER = 28, // offset of the outer-pair sums (or -1)
     BK_OWIDTH = 29,
 };
@@ -648,7 +652,7 @@ __device__ void worker_control(PSmem &S, const KArgs &a, const PArgs &pa, const 
 {
     const int ct = threadIdx.x - KT;
     const int N1 = G.N1, TB = pa.tb;
-    const int role = blockIdx.x < (unsigned)NFIX ? 1 + (int)blockIdx.x - NCL : 0;
+    const int role = blockIdx.x < (unsigned)(NCL + NOUT) ? 1 + (int)blockIdx.x - NCL : 0;
     const int nw = gridDim.x - NFIX;
     const int w = blockIdx.x - NFIX;
     // index m waits for coefficient m-2 (workers) or m-1 (outer pairs)
@@ -682,7 +686,7 @@ __device__ void worker_control(PSmem &S, const KArgs &a, const PArgs &pa, const 
         for (int tg = 0; tg < 2; tg++) {
             const int wd = S.misc[MS_WID + 2 * par + tg];
             long long *src = S.win + (size_t)(2 * par + tg) * G.WW;
-            long long *dst = pa.gin + (((size_t)set * 2 + tg) * 2 + (role ? 1 : 0)) * a.Wcap;
+            long long *dst = pa.gin + (((size_t)set * 3 + 1 + tg) * GIN_PARTS + (role ? 1 : 0)) * a.Wcap;
             for (int c = ct; c < wd; c += CT) {
                 const long long v = src[c];
                 if (v) {
@@ -856,73 +860,248 @@ __device__ void worker_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
         worker_control(S, a, pa, G);
 }
 
-// ------------------------------------------------------------------ bracket CTAs
-
 // raw limbs -> operand slot (the zero padding above Lp is never written)
 __device__ __forceinline__ void to_slot(uint32_t *dst, const uint32_t *src, int Lp)
 {
     for (int x = threadIdx.x; x < Lp; x += PT) dst[gpos(x)] = src[x];
 }
 
+// single non-zero limb of sigma, R, b (index and value at MS_PSCAL, index
+// -1 otherwise); whole CTA, ends with __syncthreads
+__device__ void scan_one_limb_params(PSmem &S, const KArgs &a, const Geo &G)
+{
+    if (threadIdx.x < 3) {
+        const int p = threadIdx.x;
+        int cnt = 0, i0 = -1;
+        uint32_t v = 0;
+        for (int x = 0; x < G.Lp; x++) {
+            const uint32_t l = __ldg(&a.parL[(size_t)p * G.Lp + x]);
+            if (l) {
+                cnt++;
+                i0 = x;
+                v = l;
+            }
+        }
+        S.misc[MS_PSCAL + 2 * p] = cnt == 1 ? i0 : -1;
+        S.misc[MS_PSCAL + 2 * p + 1] = (int)v;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ edge terms
+
+// The edge terms of index m: a component of coefficient m times a number
+// fixed for the step, i.e. the pairs a = 0 and a = m of Eq. (3)'s Cauchy
+// sums and the parameter products whose parameter has more than one non-zero
+// limb (a one-limb parameter's product stays a simple part of its bracket).
+// They need coefficient m itself, so they sit on the chain from coefficient m
+// to coefficient m+1; edge CTA e computes EDGE_T[e][0..1] as soon as m is
+// out, in parallel with the others.
+struct EdgeTerm {
+    int tgt;   // bracket (0 alpha', 1 beta', 2 gamma'), -1 none
+    int comp;  // component of coefficient m
+    int fix;   // fixed factor: 0..2 component of coefficient 0, 3 + p parameter p
+    int neg;   // the term enters negated
+    int mpos;  // only for m > 0 (the pair a = m is the pair a = 0 at m = 0)
+};
+__device__ constexpr EdgeTerm EDGE_T[NEDGE][2] = {
+    {{1, 0, 2, 1, 0}, {0, 1, 3 + P_SIGMA, 0, 0}},  // -alpha_m gamma_0;  +sigma beta_m
+    {{1, 2, 0, 1, 1}, {0, 0, 3 + P_SIGMA, 1, 0}},  // -gamma_m alpha_0;  -sigma alpha_m
+    {{2, 0, 1, 0, 0}, {1, 0, 3 + P_R, 0, 0}},      // +alpha_m beta_0;   +R alpha_m
+    {{2, 1, 0, 0, 1}, {-1, 0, 0, 0, 0}},           // +beta_m alpha_0
+    {{2, 2, 3 + P_B, 1, 0}, {-1, 0, 0, 0, 0}},     // -gamma_m b
+};
+
+// term T at index m: present?  Its lowest limb lp (relative to the base of
+// the exact sum) and its sign.  expT/flgT hold coefficients 0 and m; the
+// one-limb parameters are marked at MS_PSCAL.
+__device__ bool edge_term(const PSmem &S, const KArgs &a, const Geo &G, const EdgeTerm &T, int m,
+                          long long &lp, int &neg)
+{
+    if (T.tgt < 0 || (T.mpos && m == 0)) return false;
+    const int eA = S.expT[T.comp * G.N1 + m], fA = S.flgT[T.comp * G.N1 + m];
+    int eF, fF;
+    if (T.fix < 3) {
+        eF = S.expT[T.fix * G.N1];
+        fF = S.flgT[T.fix * G.N1];
+    } else {
+        const int p = T.fix - 3;
+        if (S.misc[MS_PSCAL + 2 * p] >= 0) return false;  // one limb: a simple part
+        eF = __ldg(&a.parE[p]);
+        fF = __ldg(&a.parF[p]);
+    }
+    if (!(fA & F_NZ) || !(fF & F_NZ)) return false;
+    lp = (long long)eA + eF - 2LL * G.L;
+    neg = T.neg ^ (((fA ^ fF) & F_NEG) ? 1 : 0);
+    return true;
+}
+
+// window of bracket c's edge terms at index m (empty: lo > hi)
+__device__ void edge_window(const PSmem &S, const KArgs &a, const Geo &G, int c, int m, long long &lo,
+                            long long &hi)
+{
+    lo = LLONG_MAX;
+    hi = LLONG_MIN;
+    for (int e = 0; e < NEDGE; e++)
+        for (int k = 0; k < 2; k++) {
+            const EdgeTerm T = EDGE_T[e][k];
+            long long lp;
+            int neg;
+            if (T.tgt != c || !edge_term(S, a, G, T, m, lp, neg)) continue;
+            lo = min(lo, lp);
+            hi = max(hi, lp + 2LL * G.Lp + 2);
+        }
+}
+
+// Edge CTA e: at each index m, once coefficient m is out, its terms
+// EDGE_T[e] (a component of coefficient m times a number fixed for the step)
+// into the edge part of their brackets' global windows; then it counts
+// itself done.
+__device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &G)
+{
+    const int e = blockIdx.x - (NCL + NOUT);
+    const int N1 = G.N1, Lp = G.Lp;
+    for (int i = threadIdx.x; i < NA * G.VW; i += PT) S.vA[i] = 0u;
+    for (int i = threadIdx.x; i < NC * G.VW; i += PT) S.vC[i] = 0u;
+    for (int i = threadIdx.x; i < 2 * G.WW; i += PT) S.win[i] = 0;
+    scan_one_limb_params(S, a, G);
+    for (long long step = 0; step < a.nsteps; step++) {
+        for (int m = 0; m < a.N; m++) {
+            Prof pr(a, true, S.misc);
+            const long long g = step * a.N + m;
+            const int set = (int)(g % PIPE_SETS);
+            if (!wait_geq(S, a, pa.pub, (unsigned)(3 * (step * N1 + m + 1)))) return;
+            pr.mark(PR_BARRIER);
+            if (threadIdx.x < 3) {
+                const int idx = threadIdx.x * N1 + m;
+                S.expT[idx] = __ldcg(&a.coefE[idx]);
+                S.flgT[idx] = __ldcg(&a.coefF[idx]);
+            }
+            __syncthreads();
+            if (m == 0) {
+                // the fixed factors of this CTA's terms: coefficient 0 or a parameter
+                for (int k = 0; k < 2; k++) {
+                    const EdgeTerm T = EDGE_T[e][k];
+                    if (T.tgt < 0) continue;
+                    const uint32_t *src = T.fix < 3 ? a.coefL + (size_t)T.fix * N1 * Lp
+                                                    : a.parL + (size_t)(T.fix - 3) * Lp;
+                    for (int x = threadIdx.x; x < Lp; x += PT)
+                        S.vC[(size_t)k * G.VW + gpos(x)] = __ldcg(&src[x]);
+                }
+            }
+            // terms present, their windows (thread 0)
+            if (threadIdx.x == 0) {
+                for (int k = 0; k < 2; k++) {
+                    const EdgeTerm T = EDGE_T[e][k];
+                    long long lp, lo, hi;
+                    int neg, on = 0, d = 0, width = 0;
+                    if (T.tgt >= 0 && edge_term(S, a, G, T, m, lp, neg)) {
+                        edge_window(S, a, G, T.tgt, m, lo, hi);
+                        if (hi - lo > a.Wcap) {
+                            atomicCAS(a.status, 0, DEV_ERANGE);
+                        } else {
+                            on = 1;
+                            d = (int)(lp - lo);
+                            width = (int)(hi - lo);
+                        }
+                    } else {
+                        neg = 0;
+                    }
+                    int *ti = S.tinfo + k * TI;
+                    ti[0] = on;
+                    ti[1] = neg;
+                    ti[2] = d & 7;
+                    ti[3] = d >> 3;
+                    ti[4] = width;
+                }
+            }
+            __syncthreads();
+            pr.mark(PR_PLACE);
+            // first factors: the component shifted by d_lo, complemented when negative
+            for (int k = 0; k < 2; k++) {
+                const int *ti = S.tinfo + k * TI;
+                if (!ti[0]) continue;
+                const EdgeTerm T = EDGE_T[e][k];
+                const uint32_t *src = a.coefL + ((size_t)T.comp * N1 + m) * Lp;
+                const uint32_t inv = ti[1] ? 0xffffffffu : 0u;
+                const int dl = ti[2];
+                uint32_t *dst = S.vA + (size_t)k * G.VW;
+                for (int x = threadIdx.x; x < G.M; x += PT) {
+                    const int y = x - dl;
+                    dst[gpos(x)] = (y >= 0 && y < Lp) ? (__ldcg(&src[y]) ^ inv) : 0u;
+                }
+            }
+            pr.mark(PR_STAGE);
+            for (int k = 0; k < 2; k++) {
+                const int *ti = S.tinfo + k * TI;
+                if (!ti[0]) continue;
+                small_products(G, G.RS, whole_cta(), S.vA, S.vC, k, 1, S.tinfo, false, S.bstage,
+                               S.win + (size_t)k * G.WW, ti[3] * W);
+            }
+            pr.mark(PR_MAC);
+            for (int k = 0; k < 2; k++) {
+                const int *ti = S.tinfo + k * TI;
+                if (!ti[0]) continue;
+                const EdgeTerm T = EDGE_T[e][k];
+                long long *src = S.win + (size_t)k * G.WW;
+                long long *dst = pa.gin + (((size_t)set * 3 + T.tgt) * GIN_PARTS + 2) * a.Wcap;
+                for (int c = threadIdx.x; c < ti[4]; c += PT) {
+                    const long long v = src[c];
+                    if (v) {
+                        atomicAdd((unsigned long long *)&dst[c], (unsigned long long)v);
+                        src[c] = 0;
+                    }
+                }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                __threadfence();
+                atomicAdd(&pa.done[set], 1u);
+            }
+            pr.mark(PR_FLUSH);
+            if (S.misc[MS_STATUS]) return;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ bracket CTAs
+
 // Setup of bracket c at index m (thread 0): the simple parts (a lone number,
-// a number times a one-limb parameter), the product terms (a component of
-// coefficient m, or of m-1 for the outer pairs, times the fixed number in C
-// slot k) and the workers' middle sums; the window (base, width) and each
-// part's offset in it; the term groups.
-// Returns false (status set) when the window is wider than Wcap.
+// a number times a one-limb parameter); the windows of the parts the other
+// CTAs add (edge terms, outer pairs, middle pairs); the bracket's window
+// (base, width) and each part's offset in it.  Returns false (status set)
+// when the window is wider than Wcap.
 __device__ bool bracket_setup(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &G, int c, int m,
                               int set)
 {
+    (void)pa;
+    (void)set;
     const int N1 = G.N1, L = G.L, Lp = G.Lp;
     int *bk = S.misc + MS_BK;
     const int eA = S.expT[m], fA = S.flgT[m];
     const int eB = S.expT[N1 + m], fB = S.flgT[N1 + m];
-    const int eG = S.expT[2 * N1 + m], fG = S.flgT[2 * N1 + m];
-    const int eA0 = S.expT[0], fA0 = S.flgT[0];
-    const int eB0 = S.expT[N1], fB0 = S.flgT[N1];
-    const int eG0 = S.expT[2 * N1], fG0 = S.flgT[2 * N1];
     int sk[2] = {0, 0}, sneg[2] = {0, 0}, scomp[2] = {0, 0};
     uint32_t sv[2] = {0u, 0u};
     long long slp[2] = {0, 0};
-    int tp[NTERM] = {}, tcomp[NTERM] = {}, tneg[NTERM] = {};
-    long long tlp[NTERM] = {};
     int ns = 0;
-    // parameter p times component comp of coefficient m (exponent e, flags f)
-    auto param = [&](int p, int comp, int e, int f, int neg, int tslot) {
+    // one-limb parameter p times component comp of coefficient m (exponent e, flags f)
+    auto param = [&](int p, int comp, int e, int f, int neg) {
         const int pe = __ldg(&a.parE[p]), pf = __ldg(&a.parF[p]);
-        if (!(pf & F_NZ) || !(f & F_NZ)) return;
-        const int nn = neg ^ (((pf ^ f) & F_NEG) ? 1 : 0);
         const int i0 = S.misc[MS_PSCAL + 2 * p];
-        if (i0 >= 0) {
-            sk[ns] = 2;
-            sneg[ns] = nn;
-            scomp[ns] = comp;
-            sv[ns] = (uint32_t)S.misc[MS_PSCAL + 2 * p + 1];
-            slp[ns] = (long long)pe - L + i0 + (long long)e - L;
-            ns++;
-        } else {
-            tp[tslot] = 1;
-            tcomp[tslot] = comp;
-            tneg[tslot] = nn;
-            tlp[tslot] = (long long)pe + e - 2LL * L;
-        }
-    };
-    // component comp of coefficient m times a fixed number (e0, f0)
-    auto term = [&](int tslot, int comp, int e, int f, int e0, int f0, int neg) {
-        if (!(f & F_NZ) || !(f0 & F_NZ)) return;
-        tp[tslot] = 1;
-        tcomp[tslot] = comp;
-        tneg[tslot] = neg ^ (((f ^ f0) & F_NEG) ? 1 : 0);
-        tlp[tslot] = (long long)e + e0 - 2LL * L;
+        if (!(pf & F_NZ) || !(f & F_NZ) || i0 < 0) return;
+        sk[ns] = 2;
+        sneg[ns] = neg ^ (((pf ^ f) & F_NEG) ? 1 : 0);
+        scomp[ns] = comp;
+        sv[ns] = (uint32_t)S.misc[MS_PSCAL + 2 * p + 1];
+        slp[ns] = (long long)pe - L + i0 + (long long)e - L;
+        ns++;
     };
     if (c == 0) {
-        param(P_SIGMA, 1, eB, fB, 0, 0);  // + sigma beta_m   (C slot 0: sigma)
-        param(P_SIGMA, 0, eA, fA, 1, 1);  // - sigma alpha_m  (C slot 1: sigma)
+        param(P_SIGMA, 1, eB, fB, 0);  // + sigma beta_m
+        param(P_SIGMA, 0, eA, fA, 1);  // - sigma alpha_m
     } else if (c == 1) {
-        term(0, 0, eA, fA, eG0, fG0, 1);             // - alpha_m gamma_0  (C slot 0: gamma_0)
-        if (m > 0) term(1, 2, eG, fG, eA0, fA0, 1);  // - gamma_m alpha_0  (C slot 1: alpha_0)
-        param(P_R, 0, eA, fA, 0, 2);                  // + R alpha_m        (C slot 2: R)
-        if (fB & F_NZ) {                              // - beta_m
+        param(P_R, 0, eA, fA, 0);      // + R alpha_m
+        if (fB & F_NZ) {               // - beta_m
             sk[ns] = 1;
             sneg[ns] = 1 ^ ((fB & F_NEG) ? 1 : 0);
             scomp[ns] = 1;
@@ -930,22 +1109,22 @@ __device__ bool bracket_setup(PSmem &S, const KArgs &a, const PArgs &pa, const G
             ns++;
         }
     } else {
-        term(0, 0, eA, fA, eB0, fB0, 0);             // + alpha_m beta_0   (C slot 0: beta_0)
-        if (m > 0) term(1, 1, eB, fB, eA0, fA0, 0);  // + beta_m alpha_0   (C slot 1: alpha_0)
-        term(2, 2, eG, fG, __ldg(&a.parE[P_B]), __ldg(&a.parF[P_B]), 1);  // - gamma_m b (C slot 2: b)
+        const int eG = S.expT[2 * N1 + m], fG = S.flgT[2 * N1 + m];
+        param(P_B, 2, eG, fG, 1);      // - b gamma_m
     }
     long long lo = LLONG_MAX, hi = LLONG_MIN;
     for (int k = 0; k < ns; k++) {
         lo = min(lo, slp[k]);
         hi = max(hi, slp[k] + Lp + 2);
     }
-    for (int k = 0; k < NTERM; k++)
-        if (tp[k]) {
-            lo = min(lo, tlp[k]);
-            hi = max(hi, tlp[k] + 2LL * Lp + 2);
-        }
-    // the middle pairs (workers) and the outer pairs (outer-pair CTAs)
-    long long ilo = 0, ihi = 0, olo = 0, ohi = 0;
+    // the edge terms (edge CTAs), the middle pairs (workers) and the outer
+    // pairs (outer-pair CTAs)
+    long long elo, ehi, ilo = 0, ihi = 0, olo = 0, ohi = 0;
+    edge_window(S, a, G, c, m, elo, ehi);
+    if (ehi > elo) {
+        lo = min(lo, elo);
+        hi = max(hi, ehi);
+    }
     if (c > 0 && m >= 4) {
         long long l2[2], h2[2];
         inner_window(a, (const long long *)(S.misc + MS_IMID), S.expT, S.flgT, m, l2, h2);
@@ -983,38 +1162,15 @@ __device__ bool bracket_setup(PSmem &S, const KArgs &a, const PArgs &pa, const G
         bk[BK_SIMPLE + 4 * k + 3] = scomp[k];
         bk[BK_SV + k] = (int)sv[k];
     }
+    const bool edge = ehi > elo;
+    bk[BK_EINNER] = edge ? (int)(elo - lo) : -1;
+    bk[BK_EWIDTH] = edge ? (int)(ehi - elo) : 0;
     const bool inner = c > 0 && m >= 4 && ihi > ilo;
     bk[BK_INNER] = inner ? (int)(ilo - lo) : -1;
     bk[BK_IWIDTH] = inner ? (int)(ihi - ilo) : 0;
     const bool outer = c > 0 && m >= 2 && ohi > olo;
     bk[BK_OINNER] = outer ? (int)(olo - lo) : -1;
     bk[BK_OWIDTH] = outer ? (int)(ohi - olo) : 0;
-    int nrun = 0, prev_dhi = -1;
-    for (int k = 0; k < NTERM; k++) {
-        const int d = tp[k] ? (int)(tlp[k] - lo) : 0;
-        bk[BK_TERM + 4 * k] = tp[k];
-        bk[BK_TERM + 4 * k + 1] = tcomp[k];
-        bk[BK_TERM + 4 * k + 2] = tneg[k];
-        bk[BK_TERM + 4 * k + 3] = d;
-        int *ti = S.tinfo + k * TI;
-        ti[1] = tneg[k];
-        ti[2] = d & 7;
-        ti[3] = d >> 3;
-        // groups: maximal runs of present terms with equal d_hi
-        if (!tp[k]) {
-            prev_dhi = -1;
-            continue;
-        }
-        if (prev_dhi == (d >> 3)) {
-            S.misc[MS_RUNE + nrun - 1] = k + 1;
-        } else {
-            S.misc[MS_RUN + nrun] = k;
-            S.misc[MS_RUNE + nrun] = k + 1;
-            nrun++;
-        }
-        prev_dhi = d >> 3;
-    }
-    S.misc[MS_NRUN] = nrun;
     return true;
 }
 
@@ -1083,8 +1239,8 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
                                  Prof &pr)
 {
     const int N1 = G.N1, Lp = G.Lp, L = G.L;
-    uint32_t *hA = S.vA + NTERM * (size_t)G.VW;        // h as first factor (last slot)
-    const uint32_t *tauC = S.vC + NTERM * (size_t)G.VW; // tau (last slot)
+    uint32_t *hA = S.vA;         // h as first factor (slot 0)
+    const uint32_t *tauC = S.vC; // tau (slot 0)
     uint32_t *hp = S.raw + 2 * (size_t)Lp;     // h, plain limbs
     long long *win = S.win;
     const int tauE = __ldg(&a.parE[P_TAU]), tauF = __ldg(&a.parF[P_TAU]);
@@ -1190,31 +1346,9 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
     for (int e = threadIdx.x; e < 3 * Lp; e += PT) S.raw[e] = 0u;
     for (int e = threadIdx.x; e < Lp; e += PT) S.newc[e] = 0u;
     for (int e = threadIdx.x; e < 2 * G.WW; e += PT) S.win[e] = 0;
-    if (threadIdx.x < 3) {
-        // single non-zero limb of sigma, R, b (else -1)
-        const int p = threadIdx.x;
-        int cnt = 0, i0 = -1;
-        uint32_t v = 0;
-        for (int x = 0; x < Lp; x++) {
-            const uint32_t l = __ldg(&a.parL[(size_t)p * Lp + x]);
-            if (l) {
-                cnt++;
-                i0 = x;
-                v = l;
-            }
-        }
-        S.misc[MS_PSCAL + 2 * p] = cnt == 1 ? i0 : -1;
-        S.misc[MS_PSCAL + 2 * p + 1] = (int)v;
-    }
-    __syncthreads();
-    // fixed factors: sigma (alpha'), R (beta'), b (gamma'), tau (Horner)
-    if (c == 0) {
-        to_slot(S.vC, a.parL + (size_t)P_SIGMA * Lp, Lp);
-        to_slot(S.vC + G.VW, a.parL + (size_t)P_SIGMA * Lp, Lp);
-    }
-    if (c == 1) to_slot(S.vC + 2 * (size_t)G.VW, a.parL + (size_t)P_R * Lp, Lp);
-    if (c == 2) to_slot(S.vC + 2 * (size_t)G.VW, a.parL + (size_t)P_B * Lp, Lp);
-    to_slot(S.vC + NTERM * (size_t)G.VW, a.parL + (size_t)P_TAU * Lp, Lp);
+    scan_one_limb_params(S, a, G);
+    // tau (Horner's fixed factor)
+    to_slot(S.vC, a.parL + (size_t)P_TAU * Lp, Lp);
     __syncthreads();
     for (long long step = 0; step < a.nsteps; step++) {
         // the state is coefficient 0 (Sec. 2): publish this CTA's component,
@@ -1237,14 +1371,6 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             S.raw[e] = __ldcg(&a.coefL[((size_t)comp * N1) * Lp + x]);
         }
         __syncthreads();
-        if (c == 1) {
-            to_slot(S.vC, S.raw + 2 * (size_t)Lp, Lp);  // gamma_0
-            to_slot(S.vC + G.VW, S.raw, Lp);            // alpha_0
-        } else if (c == 2) {
-            to_slot(S.vC, S.raw + Lp, Lp);              // beta_0
-            to_slot(S.vC + G.VW, S.raw, Lp);            // alpha_0
-        }
-        __syncthreads();
         for (int m = 0; m < a.N; m++) {
             Prof pr(a, prof_on, S.misc);
             const long long g = step * a.N + m;
@@ -1257,54 +1383,35 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             const long long lo = ((const long long *)(bk + BK_LO))[0];
             const int width = bk[BK_WIDTH];
             long long *win = S.win;
-            // first factors of the product terms: component shifted by d_lo,
-            // complemented when the term is negative
-            for (int k = 0; k < NTERM; k++) {
-                const int *bt = bk + BK_TERM + 4 * k;
-                if (!bt[0]) continue;
-                const uint32_t *src = S.raw + (size_t)bt[1] * Lp;
-                const uint32_t inv = bt[2] ? 0xffffffffu : 0u;
-                const int dl = bt[3] & 7;
-                uint32_t *dst = S.vA + (size_t)k * G.VW;
-                for (int x = threadIdx.x; x < G.M; x += PT) {
-                    const int y = x - dl;
-                    dst[gpos(x)] = (y >= 0 && y < Lp) ? (src[y] ^ inv) : 0u;
-                }
-            }
             add_simple_parts(S, G, win, width);
             pr.mark(PR_PLACE);
-            const int nrun = S.misc[MS_NRUN];
-            for (int rr = 0; rr < nrun; rr++) {
-                const int rs = S.misc[MS_RUN + rr], re = S.misc[MS_RUNE + rr];
-                small_products(G, G.RS, whole_cta(), S.vA, S.vC, rs, re - rs, S.tinfo, false, S.bstage, win,
-                               S.tinfo[rs * TI + 3] * W);
-            }
-            pr.mark(PR_MAC);
-            if (bk[BK_INNER] >= 0 || bk[BK_OINNER] >= 0) {
-                // every worker and outer-pair CTA has added its sums of index m
+            if (bk[BK_INNER] >= 0 || bk[BK_OINNER] >= 0 || bk[BK_EINNER] >= 0) {
+                // every other CTA has added its sums of index m
                 const unsigned target = (unsigned)((g / PIPE_SETS + 1) * (long long)(gridDim.x - NCL));
                 if (!wait_geq(S, a, pa.done + set, target)) return;
                 pr.mark(PR_BARRIER);
-                // both parts of this target (middle pairs, outer pairs); a
-                // thread owns window columns cc = threadIdx.x mod PT
-                long long *gm = pa.gin + ((size_t)set * 2 + (c - 1)) * 2 * a.Wcap, *go = gm + a.Wcap;
-                const int offm = bk[BK_INNER], wm = bk[BK_IWIDTH];
-                const int offo = bk[BK_OINNER], wo = bk[BK_OWIDTH];
+                // the three parts of this bracket (middle pairs, outer pairs,
+                // edge terms); a thread owns window columns cc = threadIdx.x mod PT
+                long long *gp = pa.gin + ((size_t)set * 3 + c) * 3 * a.Wcap;
+                int off[3], wd[3];
+                off[0] = bk[BK_INNER];
+                wd[0] = bk[BK_IWIDTH];
+                off[1] = bk[BK_OINNER];
+                wd[1] = bk[BK_OWIDTH];
+                off[2] = bk[BK_EINNER];
+                wd[2] = bk[BK_EWIDTH];
                 for (int cc = threadIdx.x; cc < width; cc += PT) {
                     long long v = 0;
-                    const int ym = cc - offm, yo = cc - offo;
-                    if (offm >= 0 && ym >= 0 && ym < wm) {
-                        const long long u = __ldcg(&gm[ym]);
-                        if (u) {
-                            v += u;
-                            gm[ym] = 0;
-                        }
-                    }
-                    if (offo >= 0 && yo >= 0 && yo < wo) {
-                        const long long u = __ldcg(&go[yo]);
-                        if (u) {
-                            v += u;
-                            go[yo] = 0;
+#pragma unroll
+                    for (int part = 0; part < 3; part++) {
+                        const int y = cc - off[part];
+                        if (off[part] >= 0 && y >= 0 && y < wd[part]) {
+                            long long *q = gp + (size_t)part * a.Wcap + y;
+                            const long long u = __ldcg(q);
+                            if (u) {
+                                v += u;
+                                *q = 0;
+                            }
                         }
                     }
                     if (v) win[cc] += v;
@@ -1396,8 +1503,10 @@ __global__ void __launch_bounds__(PT, 1) pipe_kernel(KArgs a, PArgs pa)
     Prof tot(a, prof_cta, S.misc);
     if (blockIdx.x < (unsigned)NCL)
         closer_loop(S, a, pa, G);
-    else
+    else if (blockIdx.x < (unsigned)(NCL + NOUT) || blockIdx.x >= (unsigned)NFIX)
         worker_loop(S, a, pa, G);
+    else
+        edge_loop(S, a, pa, G);
     __syncthreads();
     tot.mark(PR_TOTAL);
     if (a.prof && threadIdx.x == 0) {

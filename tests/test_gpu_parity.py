@@ -83,7 +83,7 @@ def test_one_step_coefficients(mpt, L, N, kind):
     c.close()
 
 
-@pytest.mark.parametrize("kind,ctas", [(1, 1), (1, 2), (1, 3), (1, 5), (1, 17), (2, 6), (2, 7),
+@pytest.mark.parametrize("kind,ctas", [(1, 1), (1, 2), (1, 3), (1, 5), (1, 17), (2, 11), (2, 12),
                                        (2, 16), (2, 24), (2, 64), (2, 0)])
 def test_launch_shape_invariance(mpt, kind, ctas):
     """The exact sums make the result independent of how the GPU splits them."""
