@@ -86,8 +86,7 @@ enum {
     MS_IMID = 24,
     MS_BK = 32,     // [48] bracket setup (ints 32..79)
     MS_RED = 80,    // [RED_LL] long long scratch of the block routines (ints 80..271)
-    MS_RUN = 272,   // [TB_MAX] group starts
-    MS_RUNE = 304,  // [TB_MAX] group ends
+    MS_PARX = 272,  // [4][2] exponent and flags of sigma, R, b, tau (ints 272..279)
     MS_PROF = 336,  // [PROF_SLOTS] long long (ints 336..367)
     MISC_INTS = 368
 };
@@ -867,7 +866,8 @@ __device__ __forceinline__ void to_slot(uint32_t *dst, const uint32_t *src, int 
 }
 
 // single non-zero limb of sigma, R, b (index and value at MS_PSCAL, index
-// -1 otherwise); whole CTA, ends with __syncthreads
+// -1 otherwise) and the parameters' exponents and flags (MS_PARX); whole
+// CTA, ends with __syncthreads
 __device__ void scan_one_limb_params(PSmem &S, const KArgs &a, const Geo &G)
 {
     if (threadIdx.x < 3) {
@@ -884,6 +884,10 @@ __device__ void scan_one_limb_params(PSmem &S, const KArgs &a, const Geo &G)
         }
         S.misc[MS_PSCAL + 2 * p] = cnt == 1 ? i0 : -1;
         S.misc[MS_PSCAL + 2 * p + 1] = (int)v;
+    } else if (threadIdx.x >= 32 && threadIdx.x < 36) {
+        const int p = threadIdx.x - 32;
+        S.misc[MS_PARX + 2 * p] = __ldg(&a.parE[p]);
+        S.misc[MS_PARX + 2 * p + 1] = __ldg(&a.parF[p]);
     }
     __syncthreads();
 }
@@ -927,8 +931,8 @@ __device__ bool edge_term(const PSmem &S, const KArgs &a, const Geo &G, const Ed
     } else {
         const int p = T.fix - 3;
         if (S.misc[MS_PSCAL + 2 * p] >= 0) return false;  // one limb: a simple part
-        eF = __ldg(&a.parE[p]);
-        fF = __ldg(&a.parF[p]);
+        eF = S.misc[MS_PARX + 2 * p];
+        fF = S.misc[MS_PARX + 2 * p + 1];
     }
     if (!(fA & F_NZ) || !(fF & F_NZ)) return false;
     lp = (long long)eA + eF - 2LL * G.L;
@@ -970,14 +974,64 @@ __device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &
             Prof pr(a, true, S.misc);
             const long long g = step * a.N + m;
             const int set = (int)(g % PIPE_SETS);
-            if (!wait_geq(S, a, pa.pub, (unsigned)(3 * (step * N1 + m + 1)))) return;
-            pr.mark(PR_BARRIER);
-            if (threadIdx.x < 3) {
-                const int idx = threadIdx.x * N1 + m;
-                S.expT[idx] = __ldcg(&a.coefE[idx]);
-                S.flgT[idx] = __ldcg(&a.coefF[idx]);
+            // thread 0 waits for coefficient m, takes its exponents and
+            // places this CTA's terms; one barrier for all of it
+            if (threadIdx.x == 0) {
+                int st = 0;
+                long long it = 0;
+                const unsigned target = (unsigned)(3 * (step * N1 + m + 1));
+                while ((int)(ld_acquire_u32(pa.pub) - target) < 0) {
+                    if (++it > a.spin_limit) {
+                        atomicCAS(a.status, 0, DEV_TIMEOUT);
+                        st = DEV_TIMEOUT;
+                        break;
+                    }
+                    if ((it & 63) == 0) {
+                        st = ld_relaxed_int(a.status);
+                        if (st) break;
+                    }
+                    __nanosleep(20);
+                }
+                if (!st) st = ld_relaxed_int(a.status);
+                S.misc[MS_STATUS] = st;
+                pr.mark(PR_BARRIER);
+                if (!st) {
+                    int ev[3], fv[3];
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        ev[k] = __ldcg(&a.coefE[k * N1 + m]);
+                        fv[k] = __ldcg(&a.coefF[k * N1 + m]);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 3; k++) {
+                        S.expT[k * N1 + m] = ev[k];
+                        S.flgT[k * N1 + m] = fv[k];
+                    }
+                    for (int k = 0; k < 2; k++) {
+                        const EdgeTerm T = EDGE_T[e][k];
+                        long long lp, lo, hi;
+                        int neg = 0, on = 0, d = 0, width = 0;
+                        if (T.tgt >= 0 && edge_term(S, a, G, T, m, lp, neg)) {
+                            edge_window(S, a, G, T.tgt, m, lo, hi);
+                            if (hi - lo > a.Wcap) {
+                                atomicCAS(a.status, 0, DEV_ERANGE);
+                            } else {
+                                on = 1;
+                                d = (int)(lp - lo);
+                                width = (int)(hi - lo);
+                            }
+                        }
+                        int *ti = S.tinfo + k * TI;
+                        ti[0] = on;
+                        ti[1] = neg;
+                        ti[2] = d & 7;
+                        ti[3] = d >> 3;
+                        ti[4] = width;
+                    }
+                }
             }
             __syncthreads();
+            if (S.misc[MS_STATUS]) return;
             if (m == 0) {
                 // the fixed factors of this CTA's terms: coefficient 0 or a parameter
                 for (int k = 0; k < 2; k++) {
@@ -989,33 +1043,6 @@ __device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &
                         S.vC[(size_t)k * G.VW + gpos(x)] = __ldcg(&src[x]);
                 }
             }
-            // terms present, their windows (thread 0)
-            if (threadIdx.x == 0) {
-                for (int k = 0; k < 2; k++) {
-                    const EdgeTerm T = EDGE_T[e][k];
-                    long long lp, lo, hi;
-                    int neg, on = 0, d = 0, width = 0;
-                    if (T.tgt >= 0 && edge_term(S, a, G, T, m, lp, neg)) {
-                        edge_window(S, a, G, T.tgt, m, lo, hi);
-                        if (hi - lo > a.Wcap) {
-                            atomicCAS(a.status, 0, DEV_ERANGE);
-                        } else {
-                            on = 1;
-                            d = (int)(lp - lo);
-                            width = (int)(hi - lo);
-                        }
-                    } else {
-                        neg = 0;
-                    }
-                    int *ti = S.tinfo + k * TI;
-                    ti[0] = on;
-                    ti[1] = neg;
-                    ti[2] = d & 7;
-                    ti[3] = d >> 3;
-                    ti[4] = width;
-                }
-            }
-            __syncthreads();
             pr.mark(PR_PLACE);
             // first factors: the component shifted by d_lo, complemented when negative
             for (int k = 0; k < 2; k++) {
@@ -1059,7 +1086,6 @@ __device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &
                 atomicAdd(&pa.done[set], 1u);
             }
             pr.mark(PR_FLUSH);
-            if (S.misc[MS_STATUS]) return;
         }
     }
 }
@@ -1086,7 +1112,7 @@ __device__ bool bracket_setup(PSmem &S, const KArgs &a, const PArgs &pa, const G
     int ns = 0;
     // one-limb parameter p times component comp of coefficient m (exponent e, flags f)
     auto param = [&](int p, int comp, int e, int f, int neg) {
-        const int pe = __ldg(&a.parE[p]), pf = __ldg(&a.parF[p]);
+        const int pe = S.misc[MS_PARX + 2 * p], pf = S.misc[MS_PARX + 2 * p + 1];
         const int i0 = S.misc[MS_PSCAL + 2 * p];
         if (!(pf & F_NZ) || !(f & F_NZ) || i0 < 0) return;
         sk[ns] = 2;
