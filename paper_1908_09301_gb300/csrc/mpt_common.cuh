@@ -237,8 +237,9 @@ constexpr int RED_LL = 96;   // long longs of scratch the block routines need
 // applied.  One merged reduction gives the lowest non-zero digit and the top
 // digit.  The magnitude is 2^(32 Wn) - D when the value is negative.  `red`
 // holds RED_LL long longs.  Needs |V| < 2^(32 Wn) (else status DEV_INTERNAL).
+// The columns read are left zero.
 template <int KK>
-__device__ Norm block_normalize_k(const long long *col, uint32_t *dig, int Wn, long long *red,
+__device__ Norm block_normalize_k(long long *col, uint32_t *dig, int Wn, long long *red,
                                   int *status)
 {
     Norm r;
@@ -251,6 +252,7 @@ __device__ Norm block_normalize_k(const long long *col, uint32_t *dig, int Wn, l
         d[k] = 0u;
         if (k < nk) {
             const long long v = col[c0 + k] + lc;
+            col[c0 + k] = 0;  // the window is left empty for its next use
             d[k] = (uint32_t)v;
             lc = v >> 32;
         }
@@ -357,7 +359,7 @@ __device__ Norm block_normalize_k(const long long *col, uint32_t *dig, int Wn, l
     return r;
 }
 
-__device__ Norm block_normalize(const long long *col, uint32_t *dig, int Wn, long long *red,
+__device__ Norm block_normalize(long long *col, uint32_t *dig, int Wn, long long *red,
                                 int *status)
 {
     if (Wn <= 0) {
@@ -382,9 +384,10 @@ __device__ Norm block_normalize(const long long *col, uint32_t *dig, int Wn, lon
 // maps are composed with a scan within each warp and one over the warps (in
 // warp 0), then every thread divides its chunk from its incoming remainder.
 // d < 2^16; `red` holds >= 4 NWARPS ints.  Ends with __syncthreads (out is
-// complete).
+// complete).  For d = 1 the limbs also go to out2 (when given) in the
+// grouped operand layout of the limb products.
 __device__ long long block_divide(const uint32_t *dig, int t, long long base, const Divisor &dv,
-                                  int L, uint32_t *out, int *red)
+                                  int L, uint32_t *out, int *red, uint32_t *out2 = nullptr)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long T = base + t + 1;
@@ -401,7 +404,11 @@ __device__ long long block_divide(const uint32_t *dig, int t, long long base, co
     };
     if (d == 1u) {
         for (int j = jhi - 1; j >= jlo; j--)
-            if (j < L) out[j] = X(j);
+            if (j < L) {
+                const uint32_t v = X(j);
+                out[j] = v;
+                if (out2) out2[gpos(j)] = v;
+            }
         __syncthreads();
         return eq;
     }

@@ -1230,7 +1230,8 @@ __device__ void add_simple_parts(const PSmem &S, const Geo &G, long long *win, i
 // zero the window.  Exponent and flags via e, f; false on a range error
 // (status set).
 __device__ bool close_bracket(PSmem &S, const KArgs &a, const Geo &G, long long *win, int width,
-                              long long lo, const Divisor &dv, uint32_t *out, int &e, int &f)
+                              long long lo, const Divisor &dv, uint32_t *out, int &e, int &f,
+                              uint32_t *out2 = nullptr)
 {
     e = 0;
     f = 0;
@@ -1242,7 +1243,7 @@ __device__ bool close_bracket(PSmem &S, const KArgs &a, const Geo &G, long long 
         neg = nr.neg;
     }
     if (top >= 0) {
-        const long long eq = block_divide(S.dig, top, lo, dv, G.L, out, S.misc + MS_RED);
+        const long long eq = block_divide(S.dig, top, lo, dv, G.L, out, S.misc + MS_RED, out2);
         if (eq > (1LL << 30) || eq < -(1LL << 30)) {
             if (threadIdx.x == 0) atomicCAS(a.status, 0, DEV_ERANGE);
             ok = false;
@@ -1251,10 +1252,10 @@ __device__ bool close_bracket(PSmem &S, const KArgs &a, const Geo &G, long long 
             f = F_NZ | (neg ? F_NEG : 0);
         }
     }
-    if (!(f & F_NZ))
+    if (!(f & F_NZ)) {
         for (int x = threadIdx.x; x < G.L; x += PT) out[x] = 0u;
-    for (int c = threadIdx.x; c < width; c += PT) win[c] = 0;
-    __syncthreads();
+        __syncthreads();
+    }
     return ok;
 }
 
@@ -1328,16 +1329,16 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
         }
         __syncthreads();
         int e, f;
-        if (!close_bracket(S, a, G, win, width, lo, one, hp, e, f)) {
+        // h for the next step, plain (hp) and as the product's first factor
+        // (hA; when h is zero, the next step has no product)
+        if (!close_bracket(S, a, G, win, width, lo, one, hp, e, f, hA)) {
             ok = false;
             break;
         }
-        for (int x = threadIdx.x; x < Lp; x += PT) hA[gpos(x)] = x < L ? hp[x] : 0u;
         he = e;
         hf = f;
 #pragma unroll
         for (int r = 0; r < CR; r++) cur[r] = nxt[r];
-        __syncthreads();
         pr.mark(PR_HCLOSE);
     }
     if (!ok) return false;

@@ -133,6 +133,25 @@ def test_edge_cases(mpt, name, L, N, par, x0, kind):
     c.close()
 
 
+# step sizes whose limbs repeat with different periods (1/3: one limb; 2/7:
+# three limbs; 0.1: one limb; 1.01: a head limb, then five; 1/48: a head
+# limb, then one), one with a period too long for the pattern product
+# (0.001: 25 limbs) and a negative one: the Horner chain of Eq. (2) must be
+# bit-exact whichever way the kernel forms tau h
+TAUS = ["1/3", "2/7", "0.1", "1.01", "1/48", "0.001", "-0.01"]
+
+
+@pytest.mark.parametrize("tau", TAUS)
+def test_horner_step_sizes(mpt, tau):
+    L, N = 40, 30
+    par = (O.SIGMA, O.R, O.B, tau)
+    c = gpu_ctx(mpt, L, N, par, kind=2)
+    c.integrate(2)
+    fin, _ = oracle_run(L, N, par, nsteps=2)
+    assert same(c.get_state(), fin), first_mismatch(c.get_state(), fin)
+    c.close()
+
+
 def test_symmetry_bit_exact(mpt):
     """(x, y, z) -> (-x, -y, z) maps GPU runs onto each other exactly."""
     L, N = 11, 60
