@@ -170,6 +170,26 @@ __device__ __forceinline__ long long warp_max_ll(long long v)
 
 // block-wide min (max) of v, returned in every thread; red holds >= NWARPS
 // long longs; two __syncthreads.
+// 32-bit warp min / max: one warp-reduction instruction (sm_80 and later)
+__device__ __forceinline__ int warp_min_i(int v)
+{
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 800
+    return __reduce_min_sync(FULL, v);
+#else
+    for (int o = 16; o; o >>= 1) v = min(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+#endif
+}
+__device__ __forceinline__ int warp_max_i(int v)
+{
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 800
+    return __reduce_max_sync(FULL, v);
+#else
+    for (int o = 16; o; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o));
+    return v;
+#endif
+}
+
 __device__ __forceinline__ long long block_min_ll(long long v, long long *red)
 {
     v = warp_min_ll(v);
@@ -303,7 +323,8 @@ __device__ Norm block_normalize_k(long long *col, uint32_t *dig, int Wn, long lo
     if (lane == 0) ex = CMAP_ID;
     const int din = cmap_apply(cmap_compose(ex, pre[warp]), 0);
     long long cin = lprev + din;
-    long long z = LLONG_MAX, t0 = -1, t1 = -1;
+    // column indices (< 2^31): lowest non-zero digit, top non-zero, top non-all-ones
+    int z = INT_MAX, t0 = -1, t1 = -1;
 #pragma unroll
     for (int k = 0; k < KK; k++) {
         if (k < nk) {
@@ -312,16 +333,16 @@ __device__ Norm block_normalize_k(long long *col, uint32_t *dig, int Wn, long lo
             cin = v >> 32;
             dig[c0 + k] = d[k];
             if (d[k]) {
-                z = min(z, (long long)(c0 + k));
+                z = min(z, c0 + k);
                 t0 = c0 + k;
             }
             if (d[k] != 0xffffffffu) t1 = c0 + k;
         }
     }
     const long long topc = fin[1];
-    z = warp_min_ll(z);
-    t0 = warp_max_ll(t0);
-    t1 = warp_max_ll(t1);
+    z = warp_min_i(z);
+    t0 = warp_max_i(t0);
+    t1 = warp_max_i(t1);
     if (lane == 0) {
         fin[2 + 3 * warp] = z;
         fin[3 + 3 * warp] = t0;
@@ -330,19 +351,19 @@ __device__ Norm block_normalize_k(long long *col, uint32_t *dig, int Wn, long lo
     __syncthreads();
     {
         // the warps' values, reduced across lanes (lane w holds warp w's)
-        long long zz = LLONG_MAX, a0 = -1, a1 = -1;
+        int zz = INT_MAX, a0 = -1, a1 = -1;
         if (lane < NWARPS) {
-            zz = fin[2 + 3 * lane];
-            a0 = fin[3 + 3 * lane];
-            a1 = fin[4 + 3 * lane];
+            zz = (int)fin[2 + 3 * lane];
+            a0 = (int)fin[3 + 3 * lane];
+            a1 = (int)fin[4 + 3 * lane];
         }
-        z = warp_min_ll(zz);
-        t0 = warp_max_ll(a0);
-        t1 = warp_max_ll(a1);
+        z = warp_min_i(zz);
+        t0 = warp_max_i(a0);
+        t1 = warp_max_i(a1);
     }
     if (topc != 0 && topc != -1 && tid == 0) atomicCAS(status, 0, DEV_INTERNAL);
     r.neg = topc < 0;
-    r.top = (int)(r.neg ? max(t1, z) : t0);
+    r.top = r.neg ? (z == INT_MAX ? -1 : max(t1, z)) : t0;
     if (r.neg) {
         // |V| = 2^(32 Wn) - D: digits below the lowest non-zero one stay 0,
         // that one becomes 2^32 - d, the ones above are complemented
