@@ -449,6 +449,117 @@ __device__ void small_products_t(const Geo &G, const Grp &gr, const uint32_t *Ab
     grp_sync(gr);
 }
 
+// One product A'_s0 * C_s0 (a Horner step, an edge term) with the same
+// result as small_products(n = 1), on the whole CTA, RS = 2^LOG lanes per
+// unit: lane r of unit q takes the chunks j = r, r + RS, ... (increasing, so
+// the block-0 part is complete before the first chunk j > q), at most NJ of
+// them (NJ RS >= P+1), in one fully unrolled sequence, with none of the
+// general walk's bookkeeping.
+template <int LOG, int NJ>
+__device__ void single_product_t(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
+                                 const int *tinfo, bool neg_all, long long *stage, long long *win,
+                                 int coff)
+{
+    constexpr int ND = W + 2;
+    constexpr int RS = 1 << LOG;
+    constexpr int NV = ((2 * ND + RS - 1) / RS) * RS;
+    const int tid = threadIdx.x;
+    __syncthreads();
+    if (tid < ((G.P1 * RS + 31) & ~31)) {
+        uint32_t a0[W], a1[W], a2[W], x0[W], x1[W], x2[W];
+#pragma unroll
+        for (int k = 0; k < W; k++) a0[k] = a1[k] = a2[k] = x0[k] = x1[k] = x2[k] = 0u;
+        const int q = tid >> LOG, r = tid & (RS - 1);
+        const unsigned slot = G.VW * 4;
+        const unsigned sA = smem_addr(Abase) + s0 * slot, sC = smem_addr(Cbase) + s0 * slot;
+        if (q < G.P1) {
+#pragma unroll
+            for (int k = 0; k < NJ; k++) {
+                const int j = r + k * RS;
+                if (j <= G.P) {
+                    if (j > q && j - RS <= q) {  // first chunk of block 1: keep block 0
+#pragma unroll
+                        for (int u = 0; u < W; u++) {
+                            x0[u] = a0[u];
+                            x1[u] = a1[u];
+                            x2[u] = a2[u];
+                        }
+                    }
+                    int gc0 = q - j;
+                    if (gc0 < 0) gc0 += G.P1;
+                    const int gc1 = gc0 == 0 ? G.P : gc0 - 1;
+                    chunk_mac(sA, sC, j, gc0, gc1, a0, a1, a2);
+                }
+            }
+            if (r + ((G.P - r) / RS) * RS <= q) {  // the lane's last chunk is in block 0
+#pragma unroll
+                for (int u = 0; u < W; u++) {
+                    x0[u] = a0[u];
+                    x1[u] = a1[u];
+                    x2[u] = a2[u];
+                }
+            }
+        }
+        long long v[NV];
+#pragma unroll
+        for (int t = 0; t < ND; t++) {
+            const long long bx = col_digit(x0, x1, x2, t), ba = col_digit(a0, a1, a2, t);
+            v[t] = bx;
+            v[ND + t] = ba - bx;
+        }
+#pragma unroll
+        for (int t = 2 * ND; t < NV; t++) v[t] = 0;
+        const int base = reduce_scatter<NV, LOG>(v, r);
+        if (q < G.P1) {
+            long long *d = stage + (size_t)q * 2 * ND;
+#pragma unroll
+            for (int i = 0; i < NV / RS; i++)
+                if (base + i < 2 * ND) d[base + i] = v[i];
+        }
+    }
+    __syncthreads();
+    for (int c = tid; c < G.GW; c += PT) {
+        long long s = 0;
+        if (c < G.M + 2) {
+            const int u = c / W;
+            if (u <= G.P) s += stage[(u * 2) * ND + c - u * W];
+            if (u >= 1 && c - (u - 1) * W < ND) s += stage[((u - 1) * 2) * ND + c - (u - 1) * W];
+        }
+        const int c1 = c - G.M;
+        if (c1 >= 0) {
+            const int u = c1 / W;
+            if (u <= G.P) s += stage[(u * 2 + 1) * ND + c1 - u * W];
+            if (u >= 1 && c1 - (u - 1) * W < ND) s += stage[((u - 1) * 2 + 1) * ND + c1 - (u - 1) * W];
+        }
+        if (tinfo && tinfo[s0 * TI + 1]) {  // complement correction of a negative term
+            const int y = c - tinfo[s0 * TI + 2];
+            const uint32_t *Cs = Cbase + (size_t)s0 * G.VW;
+            if (y >= 0 && y < G.Lp) s += Cs[gpos(y)];
+            else if (y >= G.Lp && y < 2 * G.Lp) s += (uint32_t)~Cs[gpos(y - G.Lp)];
+            if (y == G.Lp) s += 1;
+            if (y == 2 * G.Lp) s -= 1;
+        }
+        if (s) win[coff + c] += neg_all ? -s : s;
+    }
+    __syncthreads();
+}
+
+__device__ void small_products(const Geo &G, int RS, const Grp &gr, const uint32_t *Abase,
+                               const uint32_t *Cbase, int s0, int n, const int *tinfo, bool neg_all,
+                               long long *stage, long long *win, int coff);
+
+// one variant (8 lanes, at most 4 chunks a lane: Lp <= 248), the general
+// walk otherwise
+__device__ void single_product(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase, int s0,
+                               const int *tinfo, bool neg_all, long long *stage, long long *win,
+                               int coff)
+{
+    if (G.RS == 8 && G.P1 <= 32)
+        single_product_t<3, 4>(G, Abase, Cbase, s0, tinfo, neg_all, stage, win, coff);
+    else
+        small_products(G, G.RS, whole_cta(), Abase, Cbase, s0, 1, tinfo, neg_all, stage, win, coff);
+}
+
 // RS threads per unit: a power of two from 2 to 16 with RS (P+1) <= gr.n
 __device__ void small_products(const Geo &G, int RS, const Grp &gr, const uint32_t *Abase,
                                const uint32_t *Cbase, int s0, int n, const int *tinfo, bool neg_all,
@@ -1062,8 +1173,8 @@ __device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &
             for (int k = 0; k < 2; k++) {
                 const int *ti = S.tinfo + k * TI;
                 if (!ti[0]) continue;
-                small_products(G, G.RS, whole_cta(), S.vA, S.vC, k, 1, S.tinfo, false, S.bstage,
-                               S.win + (size_t)k * G.WW, ti[3] * W);
+                single_product(G, S.vA, S.vC, k, S.tinfo, false, S.bstage, S.win + (size_t)k * G.WW,
+                               ti[3] * W);
             }
             pr.mark(PR_MAC);
             for (int k = 0; k < 2; k++) {
@@ -1316,7 +1427,7 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
             width = (int)(hi - lo);
         }
         if (prod)
-            small_products(G, G.RS, whole_cta(), hA, tauC, 0, 1, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.bstage, win,
+            single_product(G, hA, tauC, 0, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.bstage, win,
                            (int)(lpp - lo));
         pr.mark(PR_HMAC);
         if (lone) {
