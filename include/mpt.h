@@ -194,6 +194,34 @@ int mpt_int_peak_run(int variant, int threads, int iters, double *mean_cycles, d
                      int *distinct_sms, int *grid_out);
 
 /*
+ * Batch of independent trajectories (an ensemble of the problem of Sec. 2:
+ * B initial points, each with its own precision L_j and order N_j; the
+ * paper integrates one trajectory at a time).  Every trajectory takes
+ * nsteps steps of exactly the arithmetic of mpt_integrate (bit-identical
+ * to a single-trajectory run with the same L, N, parameters and state); the
+ * trajectories run concurrently, one CTA each.
+ *
+ * Arguments: B >= 1; Ls[B], Ns[B] as the L and N of mpt_init (L <= 1024,
+ * N <= 4096); the parameters as decimal or rational strings, converted to
+ * each trajectory's L (as mpt_init does); the states in host memory, in the
+ * interchange layout, packed: signs[3B] and exps[3B] (trajectory j's x, y,
+ * z at 3j..3j+2) and limbs (trajectory j's three numbers of L_j limbs each
+ * at offset 3 (L_0 + ... + L_{j-1})).  They are read at the start and, on
+ * success, overwritten with the states after nsteps steps.  Work is queued
+ * on cuda_stream (0 = legacy default stream); the call allocates its device
+ * buffers, returns when the steps are done and frees them.
+ *
+ * Errors: MPT_EINVAL for a size outside the limits, a null pointer or a
+ * malformed number (the message names the trajectory), MPT_ERANGE for an
+ * exponent or accumulator window out of range in any trajectory, MPT_ENOMEM
+ * or MPT_ECUDA from the device.  On any error the states are left as they
+ * were.  (Not part of the paper.)
+ */
+int mpt_integrate_batch(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps,
+                        const char *tau, const char *sigma, const char *R, const char *b,
+                        int32_t *signs, int32_t *exps, uint32_t *limbs, uint64_t cuda_stream);
+
+/*
  * Allocation-free stepping (the paper has no counterpart; it is a service of
  * this library).  Some callers cannot call cudaMalloc when they step: code
  * whose device memory belongs to a pool it may not grow, a plug-in of a

@@ -1,5 +1,6 @@
 // mpt_host.cu -- the C ABI of libmpt (declared in include/mpt.h): contexts,
 // device buffers, parameter and state conversion, launches and error codes.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -521,7 +522,7 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->bar, 0, sizeof(unsigned) * 2, c->st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->gwin, 0, sizeof(long long) * 9 * c->Wcap, c->st);
     if (ce != cudaSuccess) return cuda_fail(ce, "launch preparation");
-    mpt::KArgs a;
+    mpt::KArgs a{};  // value-initialised: vG = 0 (the launch's own grid)
     a.L = c->L;
     a.Lp = c->Lp;
     a.P = c->P;
@@ -713,6 +714,222 @@ int mpt_get_coefficients(mpt_ctx *c, int32_t *s, int32_t *e, uint32_t *l)
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
     if (ce != cudaSuccess) return cuda_fail(ce, "coefficient download");
     from_device_layout(c, dl, de, df, (int)n, s, e, l);
+    return MPT_OK;
+}
+
+int mpt_integrate_batch(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, const char *tau,
+                        const char *sigma, const char *R, const char *b, int32_t *signs,
+                        int32_t *exps, uint32_t *limbs, uint64_t cuda_stream)
+{
+    if (B < 1) return fail(MPT_EINVAL, "batch size %d < 1", B);
+    if (!Ls || !Ns || !signs || !exps || !limbs) return fail(MPT_EINVAL, "null argument");
+    if (nsteps < 0) return fail(MPT_EINVAL, "nsteps = %lld < 0", (long long)nsteps);
+    const char *strs[4] = {sigma, R, b, tau};
+    const char *names[4] = {"sigma", "R", "b", "tau"};
+    for (int j = 0; j < 4; j++)
+        if (!strs[j]) return fail(MPT_EINVAL, "%s is null", names[j]);
+    // per trajectory: sizes, staging batch, shared memory; offsets in the packed arrays
+    struct Traj {
+        int L, Lp, P, N, Wcap, tb;
+        size_t off_limbs, off_coef, off_coefEF, off_par, off_st;
+        double work;
+    };
+    std::vector<Traj> T(B);
+    size_t n_limbs = 0, n_coef = 0, n_coefEF = 0, n_par = 0, n_st = 0, smem = 0;
+    for (int j = 0; j < B; j++) {
+        Traj &t = T[j];
+        t.L = Ls[j];
+        t.N = Ns[j];
+        if (t.L < 1 || t.L > mpt::MAX_L) return fail(MPT_EINVAL, "trajectory %d: L = %d outside 1..%d", j, t.L, mpt::MAX_L);
+        if (t.N < 1 || t.N > mpt::MAX_N) return fail(MPT_EINVAL, "trajectory %d: N = %d outside 1..%d", j, t.N, mpt::MAX_N);
+        t.Lp = (t.L + mpt::W - 1) / mpt::W * mpt::W;
+        t.P = t.Lp / mpt::W;
+        const int spread = t.Lp > 64 ? t.Lp : 64;
+        t.Wcap = (2 * t.Lp + 2 + spread + 31) / 32 * 32;
+        t.off_limbs = n_limbs;
+        n_limbs += (size_t)3 * t.L;
+        t.off_coef = n_coef;
+        n_coef += (size_t)3 * (t.N + 1) * t.Lp;
+        t.off_coefEF = n_coefEF;
+        n_coefEF += (size_t)3 * (t.N + 1);
+        t.off_par = n_par;
+        n_par += (size_t)4 * t.Lp;
+        t.off_st = n_st;
+        n_st += (size_t)3 * t.Lp;
+        t.work = (double)t.L * t.L * ((double)t.N * (t.N + 1) + 7.0 * t.N);
+    }
+    // host layouts: parameters (parsed once per L) and states
+    std::vector<uint32_t> hparL(n_par, 0u), hstL(n_st, 0u);
+    std::vector<int32_t> hparE(4 * (size_t)B), hparF(4 * (size_t)B), hstE(3 * (size_t)B), hstF(3 * (size_t)B);
+    std::vector<int> done_L;
+    std::vector<std::vector<uint32_t>> parsed_l;
+    std::vector<std::vector<int32_t>> parsed_s, parsed_e;
+    for (int j = 0; j < B; j++) {
+        const Traj &t = T[j];
+        int k = -1;
+        for (size_t i = 0; i < done_L.size(); i++)
+            if (done_L[i] == t.L) k = (int)i;
+        if (k < 0) {
+            std::vector<uint32_t> l((size_t)4 * t.L, 0u);
+            std::vector<int32_t> ps(4), pe(4);
+            for (int q = 0; q < 4; q++) {
+                const int rc = mpt_host::parse_number(strs[q], t.L, &ps[q], &pe[q], &l[(size_t)q * t.L]);
+                if (rc)
+                    return fail(rc == -3 ? MPT_ERANGE : MPT_EINVAL, "cannot use %s = \"%s\"", names[q],
+                                strs[q]);
+            }
+            done_L.push_back(t.L);
+            parsed_l.push_back(l);
+            parsed_s.push_back(ps);
+            parsed_e.push_back(pe);
+            k = (int)done_L.size() - 1;
+        }
+        mpt_ctx tmp;
+        tmp.L = t.L;
+        tmp.Lp = t.Lp;
+        std::vector<uint32_t> dl;
+        std::vector<int32_t> de, df;
+        int rc = to_device_layout(&tmp, parsed_s[k].data(), parsed_e[k].data(), parsed_l[k].data(), 4,
+                                  dl, de, df);
+        if (rc) return rc;
+        std::memcpy(&hparL[t.off_par], dl.data(), sizeof(uint32_t) * 4 * t.Lp);
+        for (int q = 0; q < 4; q++) {
+            hparE[4 * (size_t)j + q] = de[q];
+            hparF[4 * (size_t)j + q] = df[q];
+        }
+        rc = to_device_layout(&tmp, signs + 3 * (size_t)j, exps + 3 * (size_t)j, limbs + t.off_limbs, 3,
+                              dl, de, df);
+        if (rc) return fail(rc, "trajectory %d: %s", j, mpt_last_error());
+        std::memcpy(&hstL[t.off_st], dl.data(), sizeof(uint32_t) * 3 * t.Lp);
+        for (int q = 0; q < 3; q++) {
+            hstE[3 * (size_t)j + q] = de[q];
+            hstF[3 * (size_t)j + q] = df[q];
+        }
+    }
+    if (nsteps == 0) return MPT_OK;
+    // staging batches and shared memory on this device
+    int dev = 0, smem_optin = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess)
+        ce = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (ce != cudaSuccess) return cuda_fail(ce, "device query");
+    for (int j = 0; j < B; j++) {
+        Traj &t = T[j];
+        int tb = 64;
+        while (tb > 8 && mpt::smem_bytes(t.L, t.Lp, t.N, t.Wcap, tb) > (size_t)smem_optin) tb /= 2;
+        t.tb = tb;
+        const size_t sm = mpt::smem_bytes(t.L, t.Lp, t.N, t.Wcap, tb);
+        if (sm > (size_t)smem_optin)
+            return fail(MPT_EINVAL, "trajectory %d: L = %d, N = %d need %zu bytes of shared memory", j,
+                        t.L, t.N, sm);
+        if (sm > smem) smem = sm;
+    }
+    cudaStream_t st = (cudaStream_t)(uintptr_t)cuda_stream;
+    uint32_t *coefL = nullptr, *parL = nullptr, *stL = nullptr;
+    int32_t *coefE = nullptr, *coefF = nullptr, *parE = nullptr, *parF = nullptr, *stE = nullptr, *stF = nullptr;
+    int *status = nullptr;
+    unsigned *bar = nullptr;
+    long long *gwin = nullptr;
+    mpt::KArgs *dargs = nullptr;
+    ce = dalloc(&coefL, n_coef);
+    if (ce == cudaSuccess) ce = dalloc(&coefE, n_coefEF);
+    if (ce == cudaSuccess) ce = dalloc(&coefF, n_coefEF);
+    if (ce == cudaSuccess) ce = dalloc(&parL, n_par);
+    if (ce == cudaSuccess) ce = dalloc(&parE, 4 * (size_t)B);
+    if (ce == cudaSuccess) ce = dalloc(&parF, 4 * (size_t)B);
+    if (ce == cudaSuccess) ce = dalloc(&stL, n_st);
+    if (ce == cudaSuccess) ce = dalloc(&stE, 3 * (size_t)B);
+    if (ce == cudaSuccess) ce = dalloc(&stF, 3 * (size_t)B);
+    if (ce == cudaSuccess) ce = dalloc(&status, 1);
+    if (ce == cudaSuccess) ce = dalloc(&bar, 2);
+    if (ce == cudaSuccess) ce = dalloc(&gwin, 1);
+    if (ce == cudaSuccess) ce = dalloc(&dargs, (size_t)B);
+    auto release = [&]() {
+        cudaFree(coefL);
+        cudaFree(coefE);
+        cudaFree(coefF);
+        cudaFree(parL);
+        cudaFree(parE);
+        cudaFree(parF);
+        cudaFree(stL);
+        cudaFree(stE);
+        cudaFree(stF);
+        cudaFree(status);
+        cudaFree(bar);
+        cudaFree(gwin);
+        cudaFree(dargs);
+    };
+    if (ce != cudaSuccess) {
+        release();
+        return fail(ce == cudaErrorMemoryAllocation ? MPT_ENOMEM : MPT_ECUDA, "batch buffers: %s",
+                    cudaGetErrorString(ce));
+    }
+    // argument blocks, heaviest trajectories first (CTAs start in index order)
+    std::vector<int> order(B);
+    for (int j = 0; j < B; j++) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return T[x].work > T[y].work; });
+    std::vector<mpt::KArgs> hargs(B);
+    for (int i = 0; i < B; i++) {
+        const int j = order[i];
+        const Traj &t = T[j];
+        mpt::KArgs a{};
+        a.L = t.L;
+        a.Lp = t.Lp;
+        a.P = t.P;
+        a.N = t.N;
+        a.Wcap = t.Wcap;
+        a.tb = t.tb;
+        a.coefL = coefL + t.off_coef;
+        a.coefE = coefE + t.off_coefEF;
+        a.coefF = coefF + t.off_coefEF;
+        a.parL = parL + t.off_par;
+        a.parE = parE + 4 * (size_t)j;
+        a.parF = parF + 4 * (size_t)j;
+        a.stL = stL + t.off_st;
+        a.stE = stE + 3 * (size_t)j;
+        a.stF = stF + 3 * (size_t)j;
+        a.gwin = gwin;
+        a.bar = bar;
+        a.status = status;
+        a.nsteps = nsteps;
+        a.record_every = 0;
+        a.spin_limit = mpt::DEFAULT_SPIN_LIMIT;
+        a.vG = 1;
+        a.vg = 0;
+        hargs[i] = a;
+    }
+    ce = cudaMemcpyAsync(parL, hparL.data(), sizeof(uint32_t) * n_par, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(parE, hparE.data(), sizeof(int32_t) * 4 * B, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(parF, hparF.data(), sizeof(int32_t) * 4 * B, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(stL, hstL.data(), sizeof(uint32_t) * n_st, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(stE, hstE.data(), sizeof(int32_t) * 3 * B, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(stF, hstF.data(), sizeof(int32_t) * 3 * B, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(status, 0, sizeof(int), st);
+    if (ce == cudaSuccess) ce = cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2, st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(dargs, hargs.data(), sizeof(mpt::KArgs) * B, cudaMemcpyHostToDevice, st);
+    if (ce == cudaSuccess) ce = mpt::launch_batch(dargs, B, smem, st);
+    int hstatus = 0;
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hstL.data(), stL, sizeof(uint32_t) * n_st, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hstE.data(), stE, sizeof(int32_t) * 3 * B, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(hstF.data(), stF, sizeof(int32_t) * 3 * B, cudaMemcpyDeviceToHost, st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+    release();
+    if (ce != cudaSuccess) return cuda_fail(ce, "batch launch");
+    if (hstatus == mpt::DEV_ERANGE) return fail(MPT_ERANGE, "exponent or window range exceeded in the batch");
+    if (hstatus != 0) return fail(MPT_ECUDA, "batch kernel status %d", hstatus);
+    // the new states, in the caller's order and layout
+    for (int j = 0; j < B; j++) {
+        const Traj &t = T[j];
+        mpt_ctx tmp;
+        tmp.L = t.L;
+        tmp.Lp = t.Lp;
+        std::vector<uint32_t> dl(hstL.begin() + t.off_st, hstL.begin() + t.off_st + 3 * (size_t)t.Lp);
+        std::vector<int32_t> de(hstE.begin() + 3 * (size_t)j, hstE.begin() + 3 * (size_t)j + 3);
+        std::vector<int32_t> df(hstF.begin() + 3 * (size_t)j, hstF.begin() + 3 * (size_t)j + 3);
+        from_device_layout(&tmp, dl, de, df, 3, signs + 3 * (size_t)j, exps + 3 * (size_t)j, limbs + t.off_limbs);
+    }
     return MPT_OK;
 }
 

@@ -43,6 +43,9 @@ struct KArgs {
     long long record_every;
     long long *prof;        // [2][PROF_SLOTS] per-phase SM cycles of CTAs 0 and G-1, or null
     long long spin_limit;   // polls before a device-side wait gives up
+    int vG, vg;             // lock-step kernel: grid size and CTA index it runs as
+                            // (vG = 0: the launch's own grid); a batch runs each
+                            // trajectory on one CTA (vG = 1, vg = 0)
 };
 
 constexpr long long DEFAULT_SPIN_LIMIT = 20LL * 1000 * 1000;
@@ -95,5 +98,8 @@ size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb);
 cudaError_t launch_integrate(const KArgs &a, int grid, size_t smem, cudaStream_t st);
 // largest co-resident grid for this smem size (0 on error)
 int max_coresident_ctas(size_t smem);
+// independent trajectories: CTA j runs the lock-step kernel for args[j] (device
+// array of B argument blocks, each with vG = 1, vg = 0)
+cudaError_t launch_batch(const KArgs *args, int B, size_t smem, cudaStream_t st);
 
 }  // namespace mpt

@@ -252,7 +252,7 @@ extern "C" int mpt_integrate_noalloc(int L, int N, int64_t nsteps, const int32_t
 
     unsigned char *s = d->scratch;
     cudaStream_t st = (cudaStream_t)(uintptr_t)cuda_stream;
-    KArgs a;
+    KArgs a{};  // value-initialised: vG = 0 (the launch's own grid)
     a.L = L;
     a.Lp = lay.Lp;
     a.P = lay.P;

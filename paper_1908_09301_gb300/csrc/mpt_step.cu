@@ -69,6 +69,10 @@ __device__ __forceinline__ void set_status(int *status, int code)
     atomicCAS(status, 0, code);
 }
 
+// the grid the kernel runs as: the launch's, or one CTA per trajectory (batch)
+__device__ __forceinline__ int vgrid(const KArgs &a) { return a.vG ? a.vG : (int)gridDim.x; }
+__device__ __forceinline__ int vrank(const KArgs &a) { return a.vG ? a.vg : (int)blockIdx.x; }
+
 // per-phase cycle counters (thread 0 of the first and the last CTA)
 struct Prof {
     long long *p;
@@ -186,12 +190,12 @@ __device__ bool grid_barrier(const Smem &S, const KArgs &a)
 {
     Prof pr(a);
     __syncthreads();
-    if (gridDim.x > 1) {
+    if (vgrid(a) > 1) {
         if (threadIdx.x == 0) {
             unsigned gen = ld_acquire(&a.bar[1]);
             __threadfence();
             unsigned arrived = atomicAdd(&a.bar[0], 1u);
-            if (arrived == gridDim.x - 1) {
+            if (arrived == (unsigned)vgrid(a) - 1) {
                 atomicExch(&a.bar[0], 0u);
                 __threadfence();
                 atomicAdd(&a.bar[1], 1u);
@@ -647,7 +651,7 @@ __device__ void run_unit(const Smem &S, const KArgs &a, int slot, int q)
 // and then into the global accumulators
 __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
 {
-    const int G = gridDim.x, g = blockIdx.x;
+    const int G = vgrid(a), g = vrank(a);
     Prof pr(a);
     place_windows(S, a, m);
     if (!cta_ok(S, a)) return;
@@ -700,7 +704,7 @@ __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
 __device__ void close_phase(const Smem &S, const KArgs &a, int m, int set)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int G = gridDim.x;
+    const int G = vgrid(a);
     const int N1 = a.N + 1;
     Prof pr(a);
     if (warp < 3) {
@@ -733,7 +737,7 @@ __device__ void close_phase(const Smem &S, const KArgs &a, int m, int set)
             S.expT[tg * N1 + m + 1] = e;
             S.flgT[tg * N1 + m + 1] = f;
         }
-        if (blockIdx.x == 0) {
+        if (vrank(a) == 0) {
             uint32_t *g = a.coefL + ((size_t)tg * N1 + m + 1) * a.Lp;
             for (int x = lane; x < a.Lp; x += 32) g[x] = out[x];
             if (lane == 0) {
@@ -751,7 +755,7 @@ __device__ void close_phase(const Smem &S, const KArgs &a, int m, int set)
 // slot 2j: tau (A layout) and h_j (C layout); slot 2j+1: c_i (A layout).
 __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
 {
-    const int G = gridDim.x, g = blockIdx.x;
+    const int G = vgrid(a), g = vrank(a);
     int c_first, nc;
     if (G >= 3) {
         if (g >= 3) return;
@@ -901,9 +905,8 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
     }
 }
 
-__global__ void __launch_bounds__(NT, 1) taylor_kernel(KArgs a)
+__device__ void taylor_body(const KArgs &a, unsigned char *smem_raw)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     Smem S = carve(smem_raw, a);
     const int N1 = a.N + 1;
     Prof tot(a);
@@ -919,7 +922,7 @@ __global__ void __launch_bounds__(NT, 1) taylor_kernel(KArgs a)
         for (int e = threadIdx.x; e < 3 * a.Lp; e += NT) {
             uint32_t v = __ldcg(&a.stL[e]);
             S.newc[e] = v;
-            if (blockIdx.x == 0) {
+            if (vrank(a) == 0) {
                 int comp = e / a.Lp, x = e - comp * a.Lp;
                 a.coefL[(size_t)comp * N1 * a.Lp + x] = v;
             }
@@ -928,7 +931,7 @@ __global__ void __launch_bounds__(NT, 1) taylor_kernel(KArgs a)
             int e = __ldcg(&a.stE[threadIdx.x]), f = __ldcg(&a.stF[threadIdx.x]);
             S.expT[threadIdx.x * N1] = e;
             S.flgT[threadIdx.x * N1] = f;
-            if (blockIdx.x == 0) {
+            if (vrank(a) == 0) {
                 a.coefE[threadIdx.x * N1] = e;
                 a.coefF[threadIdx.x * N1] = f;
             }
@@ -955,6 +958,22 @@ __global__ void __launch_bounds__(NT, 1) taylor_kernel(KArgs a)
     }
     __syncthreads();
     tot.mark(PR_TOTAL);
+}
+
+__global__ void __launch_bounds__(NT, 1) taylor_kernel(KArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    taylor_body(a, smem_raw);
+}
+
+// one trajectory per CTA: its own argument block, a grid of one
+__global__ void __launch_bounds__(NT, 1) taylor_batch_kernel(const KArgs *args)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ KArgs a;
+    if (threadIdx.x == 0) a = args[blockIdx.x];
+    __syncthreads();
+    taylor_body(a, smem_raw);
 }
 
 }  // namespace
@@ -987,6 +1006,15 @@ int max_coresident_ctas(size_t smem)
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, taylor_kernel, NT, smem) != cudaSuccess)
         return 0;
     return per * sms;
+}
+
+cudaError_t launch_batch(const KArgs *args, int B, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(taylor_batch_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    taylor_batch_kernel<<<B, NT, smem, st>>>(args);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_integrate(const KArgs &a, int grid, size_t smem, cudaStream_t st)

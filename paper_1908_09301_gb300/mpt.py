@@ -59,6 +59,9 @@ SIGNATURES = {
                                         ctypes.POINTER(ctypes.c_int)]),
     "mpt_integrate_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int64, vp, vp,
                                              vp, vp, vp, vp, ctypes.c_uint64]),
+    "mpt_integrate_batch": (ctypes.c_int, [ctypes.c_int, vp, vp, ctypes.c_int64, ctypes.c_char_p,
+                                           ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, vp, vp,
+                                           vp, ctypes.c_uint64]),
     "mpt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mpt_last_error": (ctypes.c_char_p, []),
 }
@@ -276,6 +279,33 @@ def integrate_noalloc(L: int, N: int, nsteps: int, params, state, stream: int | 
     ss, se, sl = state
     _check(lib().mpt_integrate_noalloc(int(L), int(N), int(nsteps), _ptr(ps), _ptr(pe), _ptr(pl),
                                        _ptr(ss), _ptr(se), _ptr(sl), ctypes.c_uint64(int(stream))))
+
+
+def integrate_batch(Ls, Ns, nsteps: int, states, tau: str = "0.01", sigma: str = "10",
+                    R: str = "28", b: str = "8/3", stream: int = 0):
+    """nsteps Taylor steps of B independent trajectories through
+    ``mpt_integrate_batch``.  ``Ls``, ``Ns``: per-trajectory limbs and order;
+    ``states``: per trajectory (signs[3], exps[3], limbs[3, L_j]) in the
+    interchange layout (host).  Returns the new states in the same form."""
+    B = len(Ls)
+    if B != len(Ns) or B != len(states):
+        raise ValueError("Ls, Ns and states must have the same length")
+    Lv = np.ascontiguousarray(np.asarray(Ls, np.int32))
+    Nv = np.ascontiguousarray(np.asarray(Ns, np.int32))
+    signs = np.ascontiguousarray(np.concatenate([np.asarray(st[0], np.int32).reshape(3) for st in states]))
+    exps = np.ascontiguousarray(np.concatenate([np.asarray(st[1], np.int32).reshape(3) for st in states]))
+    limbs = np.ascontiguousarray(np.concatenate(
+        [np.asarray(st[2], np.uint32).reshape(3 * int(L)) for st, L in zip(states, Ls)]))
+    _check(lib().mpt_integrate_batch(int(B), _ptr(Lv), _ptr(Nv), int(nsteps), str(tau).encode(),
+                                     str(sigma).encode(), str(R).encode(), str(b).encode(),
+                                     _ptr(signs), _ptr(exps), _ptr(limbs), ctypes.c_uint64(int(stream))))
+    out, off = [], 0
+    for j, L in enumerate(Ls):
+        L = int(L)
+        out.append((signs[3 * j:3 * j + 3].copy(), exps[3 * j:3 * j + 3].copy(),
+                    limbs[off:off + 3 * L].reshape(3, L).copy()))
+        off += 3 * L
+    return out
 
 
 def int_peak(variant: int, iters: int = 20000, threads: int = 1024):
