@@ -187,6 +187,80 @@ def config_of(wl, ctas):
             "parallelism": "replicas"}
 
 
+def ensemble_bench(args):
+    """B trajectories of the perturbed ensemble (K in {200, 400, 800} digits,
+    N = 0.6 K, Sec. 5's point plus 1e-20 perturbations) through one
+    mpt_integrate_batch call of ``steps`` steps, states from and to host
+    memory; against the same trajectories solved one at a time (a timed sample
+    of each K, scaled to the batch)."""
+    import torch
+
+    from paper_1908_09301_gb300 import mpt
+
+    torch.cuda.set_device(0)
+    ens = WL.perturbed_ensemble(args.ensemble)
+    Ls, Ns = [t.L for t in ens], [t.N for t in ens]
+    states = []
+    for t in ens:
+        s, e, l = zip(*(mpt.parse_number(v, t.L) for v in t.x0))
+        states.append((s, e, l))
+    work = sum(t.L * t.L * (t.N * (t.N + 1) + 7 * t.N) for t in ens)  # limb products per step
+    mpt.integrate_batch(Ls, Ns, 1, states)  # warm-up (module load, first launch)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    t0 = time.perf_counter()
+    mpt.integrate_batch(Ls, Ns, args.steps, states)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    clocks = sampler.stop()
+    value = len(ens) * args.steps / dt
+    # the same trajectories one at a time: one trajectory of each K, timed
+    single_ms = {}
+    for K in sorted({t.K for t in ens}):
+        t = next(x for x in ens if x.K == K)
+        with mpt.Context(N=t.N, L=t.L) as c:
+            c.set_state(*t.x0)
+            c.integrate(1)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            c.integrate(2)
+            single_ms[K] = (time.perf_counter() - t1) / 2 * 1000.0
+    one_at_a_time_s = sum(single_ms[t.K] for t in ens) * args.steps / 1000.0
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * IMAD_PER_SM_CLK / 2 * sm_max * 1e6
+    achieved = work * args.steps / dt
+    mix = {K: sum(1 for t in ens if t.K == K) for K in sorted({t.K for t in ens})}
+    line = {
+        "metric": "trajectory-steps/sec of a perturbed ensemble (bit-exact)", "value": value,
+        "unit": "trajectory-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
+        "ms_per_step": dt / args.steps * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (Sec. 5 point plus seeded 1e-20 perturbations, exact rationals)",
+        "config": {"workload": f"perturbed_ensemble_{len(ens)}", "trajectories": len(ens),
+                   "digits_mix": mix, "N": "0.6 K", "timing": "wall time of one mpt_integrate_batch "
+                   "call (states from and to host memory)"},
+        "gpu_launches": 1,
+        "limb_macs_per_step": work,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "limb-MAC/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": (f"derived: {sms} SMs x {IMAD_PER_SM_CLK} INT32 multiply-adds "
+                                     f"per SM per clock / 2 per limb product x {sm_max:.0f} MHz")},
+        "one_at_a_time": {"value": len(ens) * args.steps / one_at_a_time_s,
+                          "unit": "trajectory-steps/s",
+                          "ms_per_step_by_digits": {str(k): round(v, 3) for k, v in single_ms.items()},
+                          "sample": "one trajectory of each K through the context API, 2 steps, "
+                                    "scaled to the ensemble"},
+        "e2e": {"value": value, "unit": "trajectory-steps/s",
+                "h2d_bytes_per_step": int(sum(12 + 12 * t.L for t in ens) / args.steps),
+                "d2h_bytes_per_step": int(sum(12 + 12 * t.L for t in ens) / args.steps)},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -197,11 +271,15 @@ def main():
     ap.add_argument("--ctas", type=int, default=0, help="CTAs of the launch (0 = library choice)")
     ap.add_argument("--cpu-steps", type=int, default=2, help="oracle steps for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ensemble", type=int, default=0,
+                    help="instead of the headline: B trajectories of the perturbed ensemble")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WL.WORKLOADS[args.workload]
     if args.impl == "reference":
         return reference_arm(args, wl)
+    if args.ensemble:
+        return ensemble_bench(args)
 
     import numpy as np
     import torch

@@ -967,7 +967,7 @@ __global__ void __launch_bounds__(NT, 1) taylor_kernel(KArgs a)
 }
 
 // one trajectory per CTA: its own argument block, a grid of one
-__global__ void __launch_bounds__(NT, 1) taylor_batch_kernel(const KArgs *args)
+__global__ void __launch_bounds__(NT, 2) taylor_batch_kernel(const KArgs *args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ KArgs a;
