@@ -33,11 +33,11 @@
 //
 // Limb products use units: unit q of a product A' * C (A' of M = (P+1)W
 // limbs, C of Lp limbs) owns columns qW..qW+W-1 of two blocks (block 1 is M
-// columns up); a group of RS lanes of one warp shares a unit, each taking a
-// contiguous share of its (term, chunk) sequence, in which every term's
-// block-0 chunks come before any block-1 chunk, so a lane switches blocks at
-// most once.  The shares are combined by a reduce-scatter within the lane
-// group, then added into the window one column per thread.
+// columns up); a group of RS lanes of one warp shares a unit: lane r first
+// takes chunk r of every term, then a contiguous share of the chunks RS..P
+// of all terms, so the chunks a lane meets only increase and it switches
+// blocks at most once.  The lanes' sums are combined by a reduce-scatter
+// within the lane group, then added into the window one column per thread.
 //
 // Hand-over: a monotone "published" counter (release/acquire, 3 per
 // coefficient) and per-set monotone completion counters; every wait is
@@ -254,65 +254,63 @@ __device__ bool wait_geq(PSmem &S, const KArgs &a, const unsigned *flag, unsigne
 
 // ------------------------------------------------------------------ unit products
 
-// The walk of one thread: share r of Re of unit q's (term, chunk) sequence,
-// in which every term's block-0 chunks (j <= q) come before any block-1 chunk.
-// a = the sums of all its products, x = their block-0 part; strad: the share
-// straddles the block switch; b1only: it lies in block 1.
+// The walk of lane r (of RS = 2^LOG) of unit q over the n terms in slots
+// [s0, s0+n), in two phases: first chunk j = r of every term (a fixed chunk,
+// so only the slot advances), then a contiguous share of the remaining
+// chunks RS..P of all terms, chunk-major.  The chunks a lane meets only
+// increase, so its block-0 part (chunks j <= q) is complete before its first
+// chunk j > q; x keeps that part, a the whole sum.
+template <int LOG>
 __device__ __forceinline__ void unit_walk(const Geo &G, const uint32_t *Abase, const uint32_t *Cbase,
-                                          int s0, int n, int q, int r, int Re, uint32_t (&a0)[W],
+                                          int s0, int n, int q, int r, uint32_t (&a0)[W],
                                           uint32_t (&a1)[W], uint32_t (&a2)[W], uint32_t (&x0)[W],
-                                          uint32_t (&x1)[W], uint32_t (&x2)[W], bool &strad,
-                                          bool &b1only)
+                                          uint32_t (&x1)[W], uint32_t (&x2)[W])
 {
-    const int I = n * G.P1;
-    const int i0 = I * r / Re, i1 = I * (r + 1) / Re;
-    const int nA = n * (q + 1);  // block-0 items: chunks 0..q of every term
-    strad = i0 < nA && i1 > nA;
-    b1only = i0 >= nA;
-    const int lenB = G.P - q;    // block-1 chunks per term
-    int t, j, ph;
-    if (i0 < nA) {
-        ph = 0;
-        t = i0 / (q + 1);
-        j = i0 - t * (q + 1);
-    } else {
-        ph = 1;
-        const int ib = i0 - nA;
-        t = ib / lenB;
-        j = q + 1 + ib - t * lenB;
-    }
-    const unsigned sAb = smem_addr(Abase), sCb = smem_addr(Cbase), slot = G.VW * 4;
-    unsigned sA = sAb + (s0 + t) * slot, sC = sCb + (s0 + t) * slot;
-    for (int it = i0; it < i1; it++) {
-        const bool sw = (it == nA);  // first block-1 item: keep the block-0 sums
-        if (__any_sync(__activemask(), sw)) {
-#pragma unroll
-            for (int k = 0; k < W; k++) {
-                x0[k] = sw ? a0[k] : x0[k];
-                x1[k] = sw ? a1[k] : x1[k];
-                x2[k] = sw ? a2[k] : x2[k];
-            }
-        }
+    constexpr int RS = 1 << LOG;
+    const unsigned slot = G.VW * 4;
+    const unsigned sAb = smem_addr(Abase), sCb = smem_addr(Cbase);
+    bool snap = false;  // x holds the block-0 part
+    if (r <= G.P) {
+        const int j = r;
+        if (j > q) snap = true;  // all of this lane's chunks are in block 1: x stays 0
         int gc0 = q - j;
         if (gc0 < 0) gc0 += G.P1;
         const int gc1 = gc0 == 0 ? G.P : gc0 - 1;
-        chunk_mac(sA, sC, j, gc0, gc1, a0, a1, a2);
-        // next item, without branches: the end of a term's block-0 run moves to
-        // the next term (or, after the last, to block 1 of the first term); the
-        // end of a block-1 run moves to the next term
-        j++;
-        const bool endA = (ph == 0) & (j > q);
-        const bool endB = (ph != 0) & (j == G.P1);
-        t += (endA | endB) ? 1 : 0;
-        const bool toB = endA & (t == n);
-        j = endB ? q + 1 : (endA ? (toB ? q + 1 : 0) : j);
-        t = toB ? 0 : t;
-        ph = toB ? 1 : ph;
-        const unsigned off = (unsigned)(s0 + t) * slot;
-        sA = sAb + off;
-        sC = sCb + off;
+        unsigned sA = sAb + s0 * slot, sC = sCb + s0 * slot;
+        for (int t = 0; t < n; t++) {
+            chunk_mac(sA, sC, j, gc0, gc1, a0, a1, a2);
+            sA += slot;
+            sC += slot;
+        }
     }
-    if (i1 <= nA) {
+    const int J2 = G.P1 - RS;
+    if (J2 > 0) {
+        const int I = J2 * n, i0 = I * r / RS, i1 = I * (r + 1) / RS;
+        const int jj = i0 / n;
+        int t = i0 - jj * n, j = RS + jj;
+        for (int it = i0; it < i1; it++) {
+            const bool sw = !snap && j > q;  // first chunk of block 1: keep block 0
+            if (__any_sync(__activemask(), sw)) {
+#pragma unroll
+                for (int k = 0; k < W; k++) {
+                    x0[k] = sw ? a0[k] : x0[k];
+                    x1[k] = sw ? a1[k] : x1[k];
+                    x2[k] = sw ? a2[k] : x2[k];
+                }
+            }
+            snap = snap || sw;
+            int gc0 = q - j;
+            if (gc0 < 0) gc0 += G.P1;
+            const int gc1 = gc0 == 0 ? G.P : gc0 - 1;
+            const unsigned off = (unsigned)(s0 + t) * slot;
+            chunk_mac(sAb + off, sCb + off, j, gc0, gc1, a0, a1, a2);
+            t++;
+            const bool wrap = t == n;
+            t = wrap ? 0 : t;
+            j += wrap ? 1 : 0;
+        }
+    }
+    if (!snap) {
 #pragma unroll
         for (int k = 0; k < W; k++) {
             x0[k] = a0[k];
@@ -396,15 +394,14 @@ __device__ void small_products_t(const Geo &G, const Grp &gr, const uint32_t *Ab
         uint32_t a0[W], a1[W], a2[W], x0[W], x1[W], x2[W];
 #pragma unroll
         for (int k = 0; k < W; k++) a0[k] = a1[k] = a2[k] = x0[k] = x1[k] = x2[k] = 0u;
-        bool strad = false, b1only = false;
         const int q = tid >> LOG, r = tid & (RS - 1);
-        if (q < G.P1) unit_walk(G, Abase, Cbase, s0, n, q, r, RS, a0, a1, a2, x0, x1, x2, strad, b1only);
+        if (q < G.P1) unit_walk<LOG>(G, Abase, Cbase, s0, n, q, r, a0, a1, a2, x0, x1, x2);
         long long v[NV];
 #pragma unroll
         for (int t = 0; t < ND; t++) {
             const long long bx = col_digit(x0, x1, x2, t), ba = col_digit(a0, a1, a2, t);
-            v[t] = b1only ? 0 : bx;
-            v[ND + t] = b1only ? ba : (strad ? ba - bx : 0);
+            v[t] = bx;
+            v[ND + t] = ba - bx;
         }
 #pragma unroll
         for (int t = 2 * ND; t < NV; t++) v[t] = 0;
