@@ -1536,17 +1536,25 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 off[2] = bk[BK_EINNER];
                 wd[2] = bk[BK_EWIDTH];
                 for (int cc = threadIdx.x; cc < width; cc += PT) {
-                    long long v = 0;
+                    // the three loads first (one round trip), then the zeroing
+                    long long u[3];
+                    long long *q[3];
 #pragma unroll
                     for (int part = 0; part < 3; part++) {
                         const int y = cc - off[part];
+                        q[part] = nullptr;
+                        u[part] = 0;
                         if (off[part] >= 0 && y >= 0 && y < wd[part]) {
-                            long long *q = gp + (size_t)part * a.Wcap + y;
-                            const long long u = __ldcg(q);
-                            if (u) {
-                                v += u;
-                                *q = 0;
-                            }
+                            q[part] = gp + (size_t)part * a.Wcap + y;
+                            u[part] = __ldcg(q[part]);
+                        }
+                    }
+                    long long v = 0;
+#pragma unroll
+                    for (int part = 0; part < 3; part++) {
+                        if (u[part]) {
+                            v += u[part];
+                            *q[part] = 0;
                         }
                     }
                     if (v) win[cc] += v;
