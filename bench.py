@@ -261,6 +261,114 @@ def ensemble_bench(args):
     return 0
 
 
+SYSTEM_X0 = {"lorenz": ("-15.8", "-17.48", "35.64"), "roessler": ("1.5", "-2.25", "0.125"),
+             "chen": ("-3.5", "2.75", "20.5")}
+
+
+def system_work(system, L, N):
+    """Limb products of one step of a general system: each product of a
+    parameter and a coefficient, each Cauchy-sum term and each Horner step is
+    one L x L product (as in W = L^2 (N(N+1) + 7N) for Lorenz)."""
+    nlin = sum(1 for t in system["fixed"] if t[2] >= 0 and t[3] >= 0)
+    nq = len(system["quad"])
+    return L * L * (nlin * N + nq * N * (N + 1) // 2 + 3 * N)
+
+
+def system_bench(args):
+    """A general quadratic system (mpt_set_system, the lock-step kernel) at K
+    digits and order N, timed like the headline: inputs resident, CUDA events
+    on the launching stream, L2 flushed between timed steps; an end-to-end leg
+    through host buffers; the general-system oracle on the first indices of
+    one step as the CPU baseline, scaled by the work."""
+    import numpy as np
+    import torch
+
+    from paper_1908_09301_gb300 import mpt
+    from paper_1908_09301_gb300 import systems as SY
+
+    torch.cuda.set_device(0)
+    name = args.system
+    system = SY.SYSTEMS[name]
+    L = mpt.limbs_for_digits(args.sys_k)
+    N = args.sys_n
+    x0 = SYSTEM_X0[name]
+    stream = torch.cuda.current_stream()
+    ctx = mpt.Context(N=N, L=L, tau="0.01", stream=stream.cuda_stream)
+    ctx.set_system(system)
+    ctx.set_state(*x0)
+    ctas = ctx.launch()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        ctx.launch_async(1)
+        ctx.wait()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        ctx.launch_async(1)
+        ev[k][1].record(stream)
+        ctx.wait()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    # end to end through the C ABI: host state in, one step, host state out
+    hs, he, hl = ctx.get_state()
+    state_bytes = int(hs.nbytes + he.nbytes + hl.nbytes)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.set_state_raw(hs, he, hl)
+        ctx.step()
+        hs, he, hl = ctx.get_state()
+    e2e_s = (time.perf_counter() - t0) / args.steps
+    ctx.close()
+    work = system_work(system, L, N)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * IMAD_PER_SM_CLK / 2 * sm_max * 1e6
+    achieved = work / (ms / 1000.0)
+    line = {
+        "metric": "Taylor steps/sec and INT32 limb-MAC fraction of peak of a general quadratic "
+                  "system (bit-exact)",
+        "value": 1000.0 / ms, "unit": "steps/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32", "data": "synthetic (a fixed initial point, exact decimals)",
+        "config": {"workload": f"{name}_k{args.sys_k}_n{N}", "system": name, "K_digits": args.sys_k,
+                   "L_limbs": L, "N_order": N, "tau": "0.01", "x0": list(x0), "ctas": ctas,
+                   "kernel": "lock-step (general system)",
+                   "l2": "flushed between timed steps (256 MiB memset)"},
+        "gpu_launches": args.steps,
+        "limb_macs_per_step": work,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "limb-MAC/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": (f"derived: {sms} SMs x {IMAD_PER_SM_CLK} INT32 multiply-adds "
+                                     f"per SM per clock / 2 per limb product x {sm_max:.0f} MHz")},
+        "e2e": {"value": 1.0 / e2e_s, "unit": "steps/s", "h2d_bytes_per_step": state_bytes,
+                "d2h_bytes_per_step": state_bytes},
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        from oracle import system_oracle as SO
+        ns = min(N, args.sys_cpu_n)
+        par = SO.param_values(L, system)
+        st = [SO.T(O.parse_rational(v), L) for v in x0]
+        t0 = time.perf_counter()
+        SO.coefficients(L, ns, system, par, st)
+        dt = time.perf_counter() - t0
+        nlin = sum(1 for t in system["fixed"] if t[2] >= 0 and t[3] >= 0)
+        wsamp = L * L * (nlin * ns + len(system["quad"]) * ns * (ns + 1) // 2)
+        line["cpu_baseline"] = {"value": wsamp / dt / work, "unit": "steps/s", "cores": 1,
+                                "kind": "oracle",
+                                "sample": f"coefficients 0..{ns} of one step of {name}_k{args.sys_k}_n{N} "
+                                          f"({dt:.1f} s, exact fractions), scaled to a full step by the work"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -273,6 +381,11 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="instead of the headline: B trajectories of the perturbed ensemble")
+    ap.add_argument("--system", default="", choices=["", "lorenz", "roessler", "chen"],
+                    help="instead of the headline: a general quadratic system")
+    ap.add_argument("--sys-k", type=int, default=2000, help="digits of --system")
+    ap.add_argument("--sys-n", type=int, default=1000, help="order of --system")
+    ap.add_argument("--sys-cpu-n", type=int, default=150, help="oracle indices for its cpu_baseline")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WL.WORKLOADS[args.workload]
@@ -280,6 +393,8 @@ def main():
         return reference_arm(args, wl)
     if args.ensemble:
         return ensemble_bench(args)
+    if args.system:
+        return system_bench(args)
 
     import numpy as np
     import torch

@@ -155,6 +155,30 @@ int mpt_set_kernel(mpt_ctx *ctx, int kind);
 int mpt_get_kernel(const mpt_ctx *ctx, int *kind);
 
 /*
+ * A general three-component quadratic system instead of Lorenz.  The paper
+ * notes (Sec. 2, after Fig. 1) that the recursion of Eq. (3) is automatic
+ * differentiation, so any right-hand side built from sums and products gives
+ * Cauchy sums of the same form.  For
+ *     x_k' = sum A x_j + sum s x_i x_j + c_k        (k = 0, 1, 2)
+ * the coefficients are x_k[m+1] = trunc_L(bracket / (m+1)) with the exact
+ * bracket  sum A x_j[m] + sum s sum_{l=0}^{m} x_i[m-l] x_j[l] + c_k [m = 0],
+ * and the step is Eq. (2) by Horner's rule with the context's tau.
+ *   params[npar]:   parameter strings (decimal or a/b), parsed exactly and
+ *                   truncated to L limbs; npar <= 15.
+ *   fixed[nfixed][4] {target, neg, p, j}: the term p * x_j (p >= 0, j >= 0),
+ *                   the lone x_j (p = -1) or the constant p (j = -1; index 0
+ *                   only); neg 1 subtracts it; nfixed <= 32.
+ *   quad[nquad][4] {target, neg, i, j}: the Cauchy product x_i * x_j;
+ *                   nquad <= 16.
+ * Host arrays, copied; targets and components are 0, 1, 2.  Malformed
+ * input: MPT_EINVAL, the context unchanged.  From then on the context runs
+ * the lock-step kernel (mpt_set_kernel(2) is refused) and mpt_get_params is
+ * refused; the state is kept.  Synchronous on the context's stream.
+ */
+int mpt_set_system(mpt_ctx *ctx, int npar, const char *const *params, int nfixed,
+                   const int32_t *fixed, int nquad, const int32_t *quad);
+
+/*
  * Bound of every device-side wait (grid barrier, hand-over flags), in polls;
  * 0 restores the default (tens of millions, seconds).  When a wait runs out
  * the launch stops, the call returns MPT_ETIMEDOUT and the state is put back

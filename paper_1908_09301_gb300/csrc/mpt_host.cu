@@ -97,6 +97,10 @@ struct mpt_ctx {
     // parameters in the interchange layout (host)
     int32_t par_s[4] = {0, 0, 0, 0}, par_e[4] = {0, 0, 0, 0};
     std::vector<uint32_t> par_l;
+    // a general quadratic system (mpt_set_system): its term table on the
+    // device, its parameters (tau last) in parL
+    int *sysT = nullptr;
+    int sysNF = 0, sysNQ = 0, sys_npar = 0;
 };
 
 namespace {
@@ -108,7 +112,7 @@ size_t prof_len(const mpt_ctx *c) { return (size_t)(2 + c->sms) * mpt::PROF_SLOT
 // device fits its fixed-role CTAs and at least one worker
 int kind_for(const mpt_ctx *c)
 {
-    if (c->kind_req == 1) return 1;
+    if (c->kind_req == 1 || c->sysT) return 1;  // the pipelined kernel is Lorenz's own
     bool pipe_ok = c->pipe_max_grid >= c->pipe_C + 1 && c->N >= 3;
     if (c->kind_req == 2) return pipe_ok ? 2 : 1;
     double work = (double)c->N * c->Lp * c->Lp;
@@ -206,6 +210,8 @@ int upload_state(mpt_ctx *c, const int32_t *s, const int32_t *e, const uint32_t 
 
 void free_all(mpt_ctx *c)
 {
+    if (c->sysT) cudaFree(c->sysT);
+    c->sysT = nullptr;
     void *ptrs[] = {c->coefL, c->coefE, c->coefF, c->parL, c->parE, c->parF, c->stL, c->stBackL,
                     c->stE, c->stF, c->stBackEF, c->gwin, c->bar, c->status, c->recS, c->recE,
                     c->recL, c->prof, c->pub, c->done, c->gin, c->imid};
@@ -335,9 +341,9 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
     ce = dalloc(&c->coefL, 3 * N1 * c->Lp);
     if (ce == cudaSuccess) ce = dalloc(&c->coefE, 3 * N1);
     if (ce == cudaSuccess) ce = dalloc(&c->coefF, 3 * N1);
-    if (ce == cudaSuccess) ce = dalloc(&c->parL, (size_t)4 * c->Lp);
-    if (ce == cudaSuccess) ce = dalloc(&c->parE, 4);
-    if (ce == cudaSuccess) ce = dalloc(&c->parF, 4);
+    if (ce == cudaSuccess) ce = dalloc(&c->parL, (size_t)mpt::SYS_MAX_PAR * c->Lp);
+    if (ce == cudaSuccess) ce = dalloc(&c->parE, mpt::SYS_MAX_PAR);
+    if (ce == cudaSuccess) ce = dalloc(&c->parF, mpt::SYS_MAX_PAR);
     if (ce == cudaSuccess) ce = dalloc(&c->stL, (size_t)3 * c->Lp);
     if (ce == cudaSuccess) ce = dalloc(&c->stBackL, (size_t)3 * c->Lp);
     if (ce == cudaSuccess) ce = dalloc(&c->stE, 3);
@@ -449,6 +455,7 @@ int mpt_get_state(mpt_ctx *c, int32_t *s, int32_t *e, uint32_t *l)
 int mpt_get_params(mpt_ctx *c, int32_t *s, int32_t *e, uint32_t *l)
 {
     if (!c || !s || !e || !l) return fail(MPT_EINVAL, "null argument");
+    if (c->sysT) return fail(MPT_EINVAL, "the context runs a general system (no sigma, R, b)");
     for (int j = 0; j < 4; j++) {
         s[j] = c->par_s[j];
         e[j] = c->par_e[j];
@@ -477,6 +484,7 @@ int mpt_set_kernel(mpt_ctx *c, int kind)
 {
     if (!c) return fail(MPT_EINVAL, "null context");
     if (kind < 0 || kind > 2) return fail(MPT_EINVAL, "kernel kind %d outside 0..2", kind);
+    if (kind == 2 && c->sysT) return fail(MPT_EINVAL, "the pipelined kernel runs Lorenz only");
     c->kind_req = kind;
     return MPT_OK;
 }
@@ -485,6 +493,66 @@ int mpt_get_kernel(const mpt_ctx *c, int *kind)
 {
     if (!c || !kind) return fail(MPT_EINVAL, "null argument");
     *kind = kind_for(c);
+    return MPT_OK;
+}
+
+int mpt_set_system(mpt_ctx *c, int npar, const char *const *params, int nfixed, const int32_t *fixed,
+                   int nquad, const int32_t *quad)
+{
+    if (!c) return fail(MPT_EINVAL, "null context");
+    if (npar < 0 || npar > mpt::SYS_MAX_PAR - 1)
+        return fail(MPT_EINVAL, "npar = %d outside 0..%d", npar, mpt::SYS_MAX_PAR - 1);
+    if (nfixed < 0 || nfixed > mpt::SYS_MAX_FIXED)
+        return fail(MPT_EINVAL, "nfixed = %d outside 0..%d", nfixed, mpt::SYS_MAX_FIXED);
+    if (nquad < 0 || nquad > mpt::SYS_MAX_QUAD)
+        return fail(MPT_EINVAL, "nquad = %d outside 0..%d", nquad, mpt::SYS_MAX_QUAD);
+    if ((npar > 0 && !params) || (nfixed > 0 && !fixed) || (nquad > 0 && !quad))
+        return fail(MPT_EINVAL, "null argument");
+    for (int t = 0; t < nfixed; t++) {
+        const int32_t *f = fixed + 4 * t;
+        const bool ok = f[0] >= 0 && f[0] < 3 && (f[1] == 0 || f[1] == 1) && f[2] >= -1 && f[2] < npar &&
+                        f[3] >= -1 && f[3] < 3 && (f[2] >= 0 || f[3] >= 0);
+        if (!ok) return fail(MPT_EINVAL, "fixed term %d = {%d, %d, %d, %d} is malformed", t, f[0], f[1], f[2], f[3]);
+    }
+    for (int t = 0; t < nquad; t++) {
+        const int32_t *q = quad + 4 * t;
+        const bool ok = q[0] >= 0 && q[0] < 3 && (q[1] == 0 || q[1] == 1) && q[2] >= 0 && q[2] < 3 &&
+                        q[3] >= 0 && q[3] < 3;
+        if (!ok) return fail(MPT_EINVAL, "Cauchy product %d = {%d, %d, %d, %d} is malformed", t, q[0], q[1], q[2], q[3]);
+    }
+    // the parameters, then tau (kept from mpt_init), in the interchange layout
+    const int L = c->L, np = npar + 1;
+    std::vector<int32_t> ps(np), pe(np);
+    std::vector<uint32_t> pl((size_t)np * L, 0u);
+    for (int j = 0; j < npar; j++) {
+        if (!params[j]) return fail(MPT_EINVAL, "parameter %d is null", j);
+        int rc = mpt_host::parse_number(params[j], L, &ps[j], &pe[j], &pl[(size_t)j * L]);
+        if (rc) return fail(rc == -3 ? MPT_ERANGE : MPT_EINVAL, "cannot use parameter %d = \"%s\"", j, params[j]);
+    }
+    ps[npar] = c->par_s[3];
+    pe[npar] = c->par_e[3];
+    std::memcpy(&pl[(size_t)npar * L], &c->par_l[(size_t)3 * L], sizeof(uint32_t) * L);
+    std::vector<uint32_t> dl;
+    std::vector<int32_t> de, df;
+    int rc = to_device_layout(c, ps.data(), pe.data(), pl.data(), np, dl, de, df);
+    if (rc) return rc;
+    rc = wait_steps(c);
+    if (rc) return rc;
+    cudaError_t ce = cudaSuccess;
+    if (!c->sysT) ce = dalloc(&c->sysT, (size_t)4 * (mpt::SYS_MAX_FIXED + mpt::SYS_MAX_QUAD));
+    std::vector<int32_t> tab((size_t)4 * (nfixed + nquad));
+    if (nfixed) std::memcpy(tab.data(), fixed, sizeof(int32_t) * 4 * nfixed);
+    if (nquad) std::memcpy(tab.data() + 4 * nfixed, quad, sizeof(int32_t) * 4 * nquad);
+    if (ce == cudaSuccess && !tab.empty())
+        ce = cudaMemcpy(c->sysT, tab.data(), sizeof(int32_t) * tab.size(), cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(c->parL, dl.data(), sizeof(uint32_t) * np * c->Lp, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(c->parE, de.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice);
+    if (ce == cudaSuccess) ce = cudaMemcpy(c->parF, df.data(), sizeof(int32_t) * np, cudaMemcpyHostToDevice);
+    if (ce != cudaSuccess) return cuda_fail(ce, "system upload");
+    c->sysNF = nfixed;
+    c->sysNQ = nquad;
+    c->sys_npar = npar;
+    c->have_coefficients = false;
     return MPT_OK;
 }
 
@@ -548,6 +616,11 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
     a.record_every = nrec > 0 ? record_every : 0;
     a.prof = c->prof;
     a.spin_limit = c->spin_limit;
+    a.sysT = c->sysT;
+    a.sysNF = c->sysNF;
+    a.sysNQ = c->sysNQ;
+    a.npar = c->sysT ? c->sys_npar + 1 : 4;
+    a.ptau = c->sysT ? c->sys_npar : 3;
     if (c->prof) {
         ce = cudaMemsetAsync(c->prof, 0, sizeof(long long) * prof_len(c), c->st);
         if (ce != cudaSuccess) return cuda_fail(ce, "profile reset");

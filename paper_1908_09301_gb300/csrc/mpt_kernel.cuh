@@ -46,7 +46,17 @@ struct KArgs {
     int vG, vg;             // lock-step kernel: grid size and CTA index it runs as
                             // (vG = 0: the launch's own grid); a batch runs each
                             // trajectory on one CTA (vG = 1, vg = 0)
+    // lock-step kernel: a general three-component quadratic system instead of
+    // Lorenz (null: the Lorenz brackets of Eq. (3), parameters sigma, R, b, tau)
+    const int *sysT;        // [sysNF][4] fixed terms, then [sysNQ][4] Cauchy products
+    int sysNF, sysNQ;
+    int npar, ptau;         // parameters in parL, tau's index among them
 };
+
+// limits of a general system
+constexpr int SYS_MAX_PAR = 16;    // parameters, tau included
+constexpr int SYS_MAX_FIXED = 32;  // fixed terms (linear and constant)
+constexpr int SYS_MAX_QUAD = 16;   // Cauchy products
 
 constexpr long long DEFAULT_SPIN_LIMIT = 20LL * 1000 * 1000;
 

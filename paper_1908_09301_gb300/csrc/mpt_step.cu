@@ -105,7 +105,7 @@ struct Smem {
     uint32_t *newc;   // [3][Lp]
     uint32_t *slots;  // [tb][AV + CV]
     int *tinfo;       // [tb][2]
-    int *misc;        // [128]
+    int *misc;        // [MISC_INTS]
     int AV, CV, M;
 };
 
@@ -122,11 +122,12 @@ __host__ __device__ inline void vec_sizes(int Lp, int &AV, int &CV, int &M)
 enum {
     MS_BASE = 0,    // [3] long long window base (lowest limb position) per target: ints 0..5
     MS_WIDTH = 8,   // [3] window width (0 = no non-zero term)
-    MS_PNZ = 12,    // [4] non-zero limb count of each parameter
     MS_RED = 16,    // [8 warps][6] long long reduction scratch -> ints 16..111
     MS_HE = 112,    // [3] Horner: exponent of h per local component
     MS_HF = 116,    // [3] Horner: flags of h
     MS_ERR = 120,   // status snapshot shared by the CTA
+    MS_PNZ = 124,   // [SYS_MAX_PAR] non-zero limb count of each parameter
+    MISC_INTS = MS_PNZ + SYS_MAX_PAR,
 };
 
 // The status word as one value for the whole CTA, so that every thread takes
@@ -228,16 +229,18 @@ struct Term {
     int neg;     // the bracket subtracts this term
     int add;     // lone number (no product): c = bsrc
     int asrc, bsrc;
+    int skip;    // no term at this index (a constant of the right-hand side, m > 0)
 };
 
 // Terms of the brackets of Eq. (3) at i = m (T = 2m + 7 of them):
 //   X: +sigma beta_m, -sigma alpha_m
 //   Y: +R alpha_m, -beta_m, -sum_{k=0}^{m} alpha_{m-k} gamma_k
 //   Z: -b gamma_m, +sum_{k=0}^{m} alpha_{m-k} beta_k
-__device__ __forceinline__ Term term_of(int m, int t, int N1)
+__device__ __forceinline__ Term lorenz_term(int m, int t, int N1)
 {
     Term r;
     r.add = 0;
+    r.skip = 0;
     if (t == 0) { r.target = T_X; r.neg = 0; r.asrc = -1 - P_SIGMA; r.bsrc = 1 * N1 + m; }
     else if (t == 1) { r.target = T_X; r.neg = 1; r.asrc = -1 - P_SIGMA; r.bsrc = 0 * N1 + m; }
     else if (t == 2) { r.target = T_Y; r.neg = 0; r.asrc = -1 - P_R; r.bsrc = 0 * N1 + m; }
@@ -251,6 +254,49 @@ __device__ __forceinline__ Term term_of(int m, int t, int N1)
         r.target = T_Z; r.neg = 0; r.asrc = 0 * N1 + (m - k); r.bsrc = 1 * N1 + k;
     }
     return r;
+}
+
+// Terms of a general three-component quadratic system (the AD reading of
+// Eq. (3), Sec. 2 after Fig. 1) at index m: the fixed terms first, each
+// {target, neg, p, j} = p x_j (p >= 0, j >= 0), the lone x_j (p < 0) or the
+// constant p (j < 0; index 0 only); then per Cauchy product {target, neg,
+// i, j} its m+1 terms x_i[m-l] x_j[l], l = 0..m.  T = NF + NQ (m+1).
+__device__ __forceinline__ Term term_of(const KArgs &a, int m, int t, int N1)
+{
+    if (!a.sysT) return lorenz_term(m, t, N1);
+    Term r;
+    r.add = 0;
+    r.skip = 0;
+    r.asrc = 0;
+    if (t < a.sysNF) {
+        const int *e = a.sysT + 4 * t;
+        const int p = __ldg(e + 2), j = __ldg(e + 3);
+        r.target = __ldg(e);
+        r.neg = __ldg(e + 1);
+        if (j >= 0) {
+            r.bsrc = j * N1 + m;
+            if (p >= 0) r.asrc = -1 - p;
+            else r.add = 1;
+        } else {
+            r.add = 1;
+            r.bsrc = -1 - p;
+            r.skip = m != 0;
+        }
+    } else {
+        const int u = t - a.sysNF, q = u / (m + 1), l = u - q * (m + 1);
+        const int *e = a.sysT + 4 * (a.sysNF + q);
+        r.target = __ldg(e);
+        r.neg = __ldg(e + 1);
+        r.asrc = __ldg(e + 2) * N1 + (m - l);
+        r.bsrc = __ldg(e + 3) * N1 + l;
+    }
+    return r;
+}
+
+// terms of index m
+__device__ __forceinline__ int nterms(const KArgs &a, int m)
+{
+    return a.sysT ? a.sysNF + a.sysNQ * (m + 1) : 2 * m + 7;
 }
 
 struct Meta {
@@ -559,12 +605,13 @@ __device__ __forceinline__ long long win_base(const Smem &S, int tg)
 // and of the sum's growth; lone number: Lp limbs plus two).
 __device__ void place_windows(const Smem &S, const KArgs &a, int m)
 {
-    const int T = 2 * m + 7;
+    const int T = nterms(a, m);
     const int N1 = a.N + 1;
     long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
     long long hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
     for (int t = threadIdx.x; t < T; t += NT) {
-        Term tm = term_of(m, t, N1);
+        Term tm = term_of(a, m, t, N1);
+        if (tm.skip) continue;
         Meta mb = meta_of(S, a, tm.bsrc);
         if (!(mb.f & F_NZ)) continue;
         long long lp, top;
@@ -593,7 +640,7 @@ __device__ void stage_terms(const Smem &S, const KArgs &a, int m, int t0, int nt
         int r = e - slot * 2 * Lp;
         int which = r >= Lp;  // 0: A operand, 1: B operand
         int x = r - which * Lp;
-        Term tm = term_of(m, t0 + slot, N1);
+        Term tm = term_of(a, m, t0 + slot, N1);
         uint32_t *base = S.slots + (size_t)slot * (S.AV + S.CV);
         if (tm.add) {
             if (which == 0) base[phys(x)] = fetch_limb(S, a, tm.bsrc, m, x);
@@ -604,10 +651,10 @@ __device__ void stage_terms(const Smem &S, const KArgs &a, int m, int t0, int nt
         }
     }
     for (int slot = threadIdx.x; slot < nt; slot += NT) {
-        Term tm = term_of(m, t0 + slot, N1);
+        Term tm = term_of(a, m, t0 + slot, N1);
         Meta mb = meta_of(S, a, tm.bsrc);
         int flags = 0, off = 0;
-        bool skip = !(mb.f & F_NZ);
+        bool skip = tm.skip || !(mb.f & F_NZ);
         long long lp = 0;
         int neg = tm.neg ^ (mb.f & F_NEG);
         if (tm.add) {
@@ -663,7 +710,7 @@ __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
         long long *nxt = a.gwin + (size_t)((set + 1) % 3) * 3 * a.Wcap;
         for (int e = g * NT + threadIdx.x; e < 3 * a.Wcap; e += G * NT) nxt[e] = 0;
     }
-    const long long T = 2 * m + 7;
+    const long long T = nterms(a, m);
     const long long U = T * a.P;
     const long long u0 = U * g / G, u1 = U * (g + 1) / G;
     if (u0 < u1) {
@@ -756,6 +803,7 @@ __device__ void close_phase(const Smem &S, const KArgs &a, int m, int set)
 __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
 {
     const int G = vgrid(a), g = vrank(a);
+    const int ptau = a.sysT ? a.ptau : P_TAU;
     int c_first, nc;
     if (G >= 3) {
         if (g >= 3) return;
@@ -777,7 +825,7 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
         uint32_t *s0 = S.slots + (size_t)(2 * j) * SL;
         uint32_t *s1 = S.slots + (size_t)(2 * j + 1) * SL;
         for (int x = threadIdx.x; x < Lp; x += NT) {
-            s0[phys(x)] = __ldg(&a.parL[(size_t)P_TAU * Lp + x]);
+            s0[phys(x)] = __ldg(&a.parL[(size_t)ptau * Lp + x]);
             s0[S.AV + phys(x)] = S.newc[comp * Lp + x];  // coefficient N
             s1[phys(x)] = __ldcg(&a.coefL[((size_t)comp * N1 + N - 1) * Lp + x]);
         }
@@ -786,7 +834,7 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
             hF[j] = S.flgT[comp * N1 + N];
         }
     }
-    const int tauE = __ldg(&a.parE[P_TAU]), tauF = __ldg(&a.parF[P_TAU]);
+    const int tauE = __ldg(&a.parE[ptau]), tauF = __ldg(&a.parF[ptau]);
     __syncthreads();
     Prof pr(a);
     for (int i = N - 1; i >= 0; i--) {
@@ -910,7 +958,7 @@ __device__ void taylor_body(const KArgs &a, unsigned char *smem_raw)
     Smem S = carve(smem_raw, a);
     const int N1 = a.N + 1;
     Prof tot(a);
-    if (threadIdx.x < 4) {
+    if (threadIdx.x < (a.sysT ? a.npar : 4)) {
         int nz = 0;
         for (int x = 0; x < a.Lp; x++) nz += __ldg(&a.parL[(size_t)threadIdx.x * a.Lp + x]) != 0u;
         S.misc[MS_PNZ + threadIdx.x] = nz;
@@ -991,7 +1039,7 @@ size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb)
     o = align16(o + sizeof(uint32_t) * 3 * Lp);
     o = align16(o + sizeof(uint32_t) * (size_t)tb * (AV + CV));
     o = align16(o + sizeof(int) * 2 * tb);
-    o = align16(o + sizeof(int) * 128);
+    o = align16(o + sizeof(int) * MISC_INTS);
     return o;
 }
 

@@ -53,6 +53,7 @@ SIGNATURES = {
     "mpt_get_launch": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
     "mpt_set_kernel": (ctypes.c_int, [vp, ctypes.c_int]),
     "mpt_get_kernel": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
+    "mpt_set_system": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int, vp, ctypes.c_int, vp]),
     "mpt_int_peak_run": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_double),
                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int),
@@ -251,6 +252,17 @@ class Context:
     def set_kernel(self, kind: int):
         """0 = library choice, 1 = lock-step, 2 = pipelined (``mpt_set_kernel``)."""
         _check(lib().mpt_set_kernel(self._h, int(kind)))
+
+    def set_system(self, system):
+        """A general three-component quadratic system (``mpt_set_system``):
+        a dict with ``params`` (strings), ``fixed`` ((target, neg, p, j)
+        tuples) and ``quad`` ((target, neg, i, j) tuples)."""
+        params = [str(p).encode() for p in system.get("params", [])]
+        fixed = np.ascontiguousarray(np.asarray(system.get("fixed", []), np.int32).reshape(-1, 4))
+        quad = np.ascontiguousarray(np.asarray(system.get("quad", []), np.int32).reshape(-1, 4))
+        arr = (ctypes.c_char_p * max(1, len(params)))(*params)
+        _check(lib().mpt_set_system(self._h, len(params), ctypes.cast(arr, ctypes.c_void_p),
+                                    len(fixed), _ptr(fixed), len(quad), _ptr(quad)))
 
     def kernel(self) -> int:
         k = ctypes.c_int()
