@@ -369,6 +369,75 @@ def system_bench(args):
     return 0
 
 
+def grad_bench(args):
+    """Jacobians of the n-step map with respect to (x0, sigma, R, b) for B
+    trajectories (300 digits, N = 150, 500 steps, tau = 0.01: Sec. 5's point
+    plus seeded 1e-20 perturbations), by multiple-precision central
+    differences: 13 bit-exact runs a trajectory, all in one batch launch."""
+    import numpy as np
+    import torch
+
+    from paper_1908_09301_gb300 import grad, mpt
+
+    torch.cuda.set_device(0)
+    B, K, N, steps = args.grad, 300, 150, args.grad_steps
+    L = mpt.limbs_for_digits(K)
+    ens = WL.perturbed_ensemble(B)
+    x0s = [t.x0 for t in ens]
+    grad.flow_jacobian(x0s[:2], L=L, N=N, nsteps=2)  # warm-up (module load, first launches)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    t0 = time.perf_counter()
+    F, J = grad.flow_jacobian(x0s, L=L, N=N, nsteps=steps)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    clocks = sampler.stop()
+    runs = 13 * B
+    work = runs * steps * L * L * (N * (N + 1) + 7 * N)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * IMAD_PER_SM_CLK / 2 * sm_max * 1e6
+    nbytes = runs * (12 + 12 * L)
+    line = {
+        "metric": "3x6 Jacobians/sec of the n-step map w.r.t. (x0, sigma, R, b), float64 from "
+                  "multiple-precision central differences",
+        "value": B / dt, "unit": "Jacobians/s", "n_gpus": 1, "steps": steps, "warmup": 1,
+        "ms_per_step": dt / steps * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u32",
+        "data": "synthetic (Sec. 5 point plus seeded 1e-20 perturbations, exact rationals)",
+        "config": {"workload": f"jacobians_{B}_k{K}_n{N}_{steps}steps", "trajectories": B,
+                   "K_digits": K, "L_limbs": L, "N_order": N, "tau": "0.01", "h": "1e-100",
+                   "runs_per_trajectory": 13, "timing": "wall time of grad.flow_jacobian (one "
+                   "mpt_integrate_batch_params call, states from and to host memory, exact differences "
+                   "on the host)"},
+        "gpu_launches": 1,
+        "limb_macs": work,
+        "roofline": {"bound": "alu", "achieved": work / dt, "peak": peak, "unit": "limb-MAC/s",
+                     "frac": work / dt / peak, "traffic": None,
+                     "peak_source": (f"derived: {sms} SMs x {IMAD_PER_SM_CLK} INT32 multiply-adds "
+                                     f"per SM per clock / 2 per limb product x {sm_max:.0f} MHz")},
+        "e2e": {"value": B / dt, "unit": "Jacobians/s", "h2d_bytes_per_step": int(nbytes / steps),
+                "d2h_bytes_per_step": int(nbytes / steps)},
+        "clocks": clocks,
+        "check": {"J_finite": bool(np.isfinite(J).all()), "J_abs_max": float(np.abs(J).max())},
+    }
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        nth = O.default_threads()
+        cs = args.cpu_steps_grad
+        p, st = O.params(L), O.state(L, x0s[0])
+        t1 = time.perf_counter()
+        O.integrate(L, N, cs, p, st, nthreads=nth)
+        dc = time.perf_counter() - t1
+        line["cpu_baseline"] = {"value": 1.0 / (13 * steps * dc / cs), "unit": "Jacobians/s", "cores": nth,
+                                "kind": "oracle",
+                                "sample": f"{cs} steps of one run (L = {L}, N = {N}, {dc:.1f} s), scaled "
+                                          f"to the 13 x {steps} steps of one Jacobian"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -386,6 +455,10 @@ def main():
     ap.add_argument("--sys-k", type=int, default=2000, help="digits of --system")
     ap.add_argument("--sys-n", type=int, default=1000, help="order of --system")
     ap.add_argument("--sys-cpu-n", type=int, default=150, help="oracle indices for its cpu_baseline")
+    ap.add_argument("--grad", type=int, default=0,
+                    help="instead of the headline: Jacobians of B trajectories (300 digits, N = 150)")
+    ap.add_argument("--grad-steps", type=int, default=500, help="steps of the map for --grad")
+    ap.add_argument("--cpu-steps-grad", type=int, default=20, help="oracle steps for --grad's cpu_baseline")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     wl = WL.WORKLOADS[args.workload]
@@ -395,6 +468,8 @@ def main():
         return ensemble_bench(args)
     if args.system:
         return system_bench(args)
+    if args.grad:
+        return grad_bench(args)
 
     import numpy as np
     import torch

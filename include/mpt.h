@@ -246,6 +246,18 @@ int mpt_integrate_batch(int B, const int32_t *Ls, const int32_t *Ns, int64_t nst
                         int32_t *signs, int32_t *exps, uint32_t *limbs, uint64_t cuda_stream);
 
 /*
+ * The same batch with parameters of each trajectory's own: sigma[j], R[j],
+ * b[j] (B strings each, host) for trajectory j; tau is common.  Trajectories
+ * with equal L and equal strings share one parse.  Used for the derivatives
+ * of the flow with respect to the parameters (runs at sigma +- h, ...).
+ * Errors and layouts as mpt_integrate_batch.
+ */
+int mpt_integrate_batch_params(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps,
+                               const char *tau, const char *const *sigma, const char *const *R,
+                               const char *const *b, int32_t *signs, int32_t *exps,
+                               uint32_t *limbs, uint64_t cuda_stream);
+
+/*
  * Allocation-free stepping (the paper has no counterpart; it is a service of
  * this library).  Some callers cannot call cudaMalloc when they step: code
  * whose device memory belongs to a pool it may not grow, a plug-in of a

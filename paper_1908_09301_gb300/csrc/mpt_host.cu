@@ -790,17 +790,24 @@ int mpt_get_coefficients(mpt_ctx *c, int32_t *s, int32_t *e, uint32_t *l)
     return MPT_OK;
 }
 
-int mpt_integrate_batch(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, const char *tau,
-                        const char *sigma, const char *R, const char *b, int32_t *signs,
-                        int32_t *exps, uint32_t *limbs, uint64_t cuda_stream)
+}  // extern "C"
+
+namespace {
+
+// the batch, with the parameters (sigma, R, b) of trajectory j at sig[j * per],
+// Rr[j * per], bb[j * per] (per = 0: one set for all)
+int batch_impl(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, const char *tau,
+               const char *const *sig, const char *const *Rr, const char *const *bb, int per,
+               int32_t *signs, int32_t *exps, uint32_t *limbs, uint64_t cuda_stream)
 {
     if (B < 1) return fail(MPT_EINVAL, "batch size %d < 1", B);
-    if (!Ls || !Ns || !signs || !exps || !limbs) return fail(MPT_EINVAL, "null argument");
+    if (!Ls || !Ns || !signs || !exps || !limbs || !sig || !Rr || !bb)
+        return fail(MPT_EINVAL, "null argument");
     if (nsteps < 0) return fail(MPT_EINVAL, "nsteps = %lld < 0", (long long)nsteps);
-    const char *strs[4] = {sigma, R, b, tau};
     const char *names[4] = {"sigma", "R", "b", "tau"};
-    for (int j = 0; j < 4; j++)
-        if (!strs[j]) return fail(MPT_EINVAL, "%s is null", names[j]);
+    if (!tau) return fail(MPT_EINVAL, "tau is null");
+    for (int j = 0; j < (per ? B : 1); j++)
+        if (!sig[j] || !Rr[j] || !bb[j]) return fail(MPT_EINVAL, "trajectory %d: a parameter is null", j);
     // per trajectory: sizes, staging batch, shared memory; offsets in the packed arrays
     struct Traj {
         int L, Lp, P, N, Wcap, tb;
@@ -831,27 +838,35 @@ int mpt_integrate_batch(int B, const int32_t *Ls, const int32_t *Ns, int64_t nst
         n_st += (size_t)3 * t.Lp;
         t.work = (double)t.L * t.L * ((double)t.N * (t.N + 1) + 7.0 * t.N);
     }
-    // host layouts: parameters (parsed once per L) and states
+    // host layouts: parameters (parsed once per L and parameter set) and states
     std::vector<uint32_t> hparL(n_par, 0u), hstL(n_st, 0u);
     std::vector<int32_t> hparE(4 * (size_t)B), hparF(4 * (size_t)B), hstE(3 * (size_t)B), hstF(3 * (size_t)B);
     std::vector<int> done_L;
+    std::vector<int> done_j;  // a trajectory with that parameter set
     std::vector<std::vector<uint32_t>> parsed_l;
     std::vector<std::vector<int32_t>> parsed_s, parsed_e;
     for (int j = 0; j < B; j++) {
         const Traj &t = T[j];
+        const int jp = j * per;
+        const char *strs[4] = {sig[jp], Rr[jp], bb[jp], tau};
         int k = -1;
-        for (size_t i = 0; i < done_L.size(); i++)
-            if (done_L[i] == t.L) k = (int)i;
+        for (size_t i = 0; i < done_L.size() && k < 0; i++) {
+            const int q = done_j[i] * per;
+            if (done_L[i] == t.L && std::strcmp(sig[q], strs[0]) == 0 && std::strcmp(Rr[q], strs[1]) == 0 &&
+                std::strcmp(bb[q], strs[2]) == 0)
+                k = (int)i;
+        }
         if (k < 0) {
             std::vector<uint32_t> l((size_t)4 * t.L, 0u);
             std::vector<int32_t> ps(4), pe(4);
             for (int q = 0; q < 4; q++) {
                 const int rc = mpt_host::parse_number(strs[q], t.L, &ps[q], &pe[q], &l[(size_t)q * t.L]);
                 if (rc)
-                    return fail(rc == -3 ? MPT_ERANGE : MPT_EINVAL, "cannot use %s = \"%s\"", names[q],
-                                strs[q]);
+                    return fail(rc == -3 ? MPT_ERANGE : MPT_EINVAL, "trajectory %d: cannot use %s = \"%s\"",
+                                j, names[q], strs[q]);
             }
             done_L.push_back(t.L);
+            done_j.push_back(j);
             parsed_l.push_back(l);
             parsed_s.push_back(ps);
             parsed_e.push_back(pe);
@@ -1004,6 +1019,25 @@ int mpt_integrate_batch(int B, const int32_t *Ls, const int32_t *Ns, int64_t nst
         from_device_layout(&tmp, dl, de, df, 3, signs + 3 * (size_t)j, exps + 3 * (size_t)j, limbs + t.off_limbs);
     }
     return MPT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mpt_integrate_batch(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, const char *tau,
+                        const char *sigma, const char *R, const char *b, int32_t *signs,
+                        int32_t *exps, uint32_t *limbs, uint64_t cuda_stream)
+{
+    return batch_impl(B, Ls, Ns, nsteps, tau, &sigma, &R, &b, 0, signs, exps, limbs, cuda_stream);
+}
+
+int mpt_integrate_batch_params(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps,
+                               const char *tau, const char *const *sigma, const char *const *R,
+                               const char *const *b, int32_t *signs, int32_t *exps, uint32_t *limbs,
+                               uint64_t cuda_stream)
+{
+    return batch_impl(B, Ls, Ns, nsteps, tau, sigma, R, b, 1, signs, exps, limbs, cuda_stream);
 }
 
 }  // extern "C"

@@ -9,10 +9,9 @@ limbs and h far below float64 resolution but far above the truncation:
 
 so at 300 digits (L = 32) and h = 1e-100 both terms are near 1e-200 relative,
 and the float64 Jacobian is the derivative of the exact-arithmetic order-N map
-rounded once.  All runs of a call go through ``mpt_integrate_batch``: one batch
-for the base point and the six state perturbations of every initial point, one
-for each of the six parameter perturbations.  The differences are formed
-exactly on the host.
+rounded once.  All runs of a call (the base point and the twelve perturbed
+runs of every initial point) go through one ``mpt_integrate_batch_params``
+launch.  The differences are formed exactly on the host.
 
 ``TaylorFlow`` wraps it as a ``torch.autograd.Function``: float64 inputs (their
 exact binary values are the multiple-precision inputs), float64 outputs; the
@@ -57,10 +56,15 @@ def _values(st):
 
 def run_points(points, params, tau, L, N, nsteps, stream=0):
     """The states after nsteps steps from each point (three exact values) with
-    parameters (sigma, R, b) (exact values), as exact Fractions."""
+    parameters (sigma, R, b) (exact values; or one such triple per point), as
+    exact Fractions, in one batch launch."""
+    if params and isinstance(params[0], (list, tuple)):
+        sig, R, b = ([ratstr(p[k]) for p in params] for k in range(3))
+    else:
+        sig, R, b = (ratstr(p) for p in params)
     out = mpt.integrate_batch([L] * len(points), [N] * len(points), nsteps,
-                              [_state(q, L) for q in points], ratstr(exact(tau)),
-                              *[ratstr(p) for p in params], stream=stream)
+                              [_state(q, L) for q in points], ratstr(exact(tau)), sig, R, b,
+                              stream=stream)
     return [_values(st) for st in out]
 
 
@@ -72,36 +76,34 @@ def flow_jacobian(x0s, params=("10", "28", "8/3"), tau="0.01", L=32, N=150, nste
     xs = [[exact(v) for v in p] for p in x0s]
     ps = [exact(v) for v in params]
     B = len(xs)
-    pts = []
+    # per initial point: [the point,] then u + h e_j and u - h e_j for the six
+    # inputs; all runs of all points in one batch
+    pts, pars = [], []
     for x in xs:
         if with_value:
             pts.append(list(x))
-        for j in range(3):
+            pars.append(ps)
+        for j in range(6):
             for sg in (1, -1):
-                q = list(x)
-                q[j] += sg * h
+                q, p = list(x), list(ps)
+                if j < 3:
+                    q[j] += sg * h
+                else:
+                    p[j - 3] += sg * h
                 pts.append(q)
-    res = run_points(pts, ps, tau, L, N, nsteps, stream)
-    per = 7 if with_value else 6
+                pars.append(p)
+    res = run_points(pts, pars, tau, L, N, nsteps, stream)
+    per = 13 if with_value else 12
+    off = 1 if with_value else 0
     J = np.zeros((B, 3, 6))
     F = []
     for b in range(B):
         r = res[b * per:(b + 1) * per]
         F.append(r[0] if with_value else None)
-        off = 1 if with_value else 0
-        for j in range(3):
+        for j in range(6):
             plus, minus = r[off + 2 * j], r[off + 2 * j + 1]
             for i in range(3):
                 J[b, i, j] = float((plus[i] - minus[i]) / (2 * h))
-    for j in range(3):
-        runs = []
-        for sg in (1, -1):
-            q = list(ps)
-            q[j] += sg * h
-            runs.append(run_points(xs, q, tau, L, N, nsteps, stream))
-        for b in range(B):
-            for i in range(3):
-                J[b, i, 3 + j] = float((runs[0][b][i] - runs[1][b][i]) / (2 * h))
     return F, J
 
 

@@ -63,6 +63,8 @@ SIGNATURES = {
     "mpt_integrate_batch": (ctypes.c_int, [ctypes.c_int, vp, vp, ctypes.c_int64, ctypes.c_char_p,
                                            ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, vp, vp,
                                            vp, ctypes.c_uint64]),
+    "mpt_integrate_batch_params": (ctypes.c_int, [ctypes.c_int, vp, vp, ctypes.c_int64, ctypes.c_char_p,
+                                                  vp, vp, vp, vp, vp, vp, ctypes.c_uint64]),
     "mpt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mpt_last_error": (ctypes.c_char_p, []),
 }
@@ -293,12 +295,14 @@ def integrate_noalloc(L: int, N: int, nsteps: int, params, state, stream: int | 
                                        _ptr(ss), _ptr(se), _ptr(sl), ctypes.c_uint64(int(stream))))
 
 
-def integrate_batch(Ls, Ns, nsteps: int, states, tau: str = "0.01", sigma: str = "10",
-                    R: str = "28", b: str = "8/3", stream: int = 0):
+def integrate_batch(Ls, Ns, nsteps: int, states, tau: str = "0.01", sigma="10",
+                    R="28", b="8/3", stream: int = 0):
     """nsteps Taylor steps of B independent trajectories through
     ``mpt_integrate_batch``.  ``Ls``, ``Ns``: per-trajectory limbs and order;
     ``states``: per trajectory (signs[3], exps[3], limbs[3, L_j]) in the
-    interchange layout (host).  Returns the new states in the same form."""
+    interchange layout (host).  ``sigma``, ``R``, ``b``: one string each, or a
+    list of B strings each (``mpt_integrate_batch_params``).  Returns the new
+    states in the same form."""
     B = len(Ls)
     if B != len(Ns) or B != len(states):
         raise ValueError("Ls, Ns and states must have the same length")
@@ -308,9 +312,19 @@ def integrate_batch(Ls, Ns, nsteps: int, states, tau: str = "0.01", sigma: str =
     exps = np.ascontiguousarray(np.concatenate([np.asarray(st[1], np.int32).reshape(3) for st in states]))
     limbs = np.ascontiguousarray(np.concatenate(
         [np.asarray(st[2], np.uint32).reshape(3 * int(L)) for st, L in zip(states, Ls)]))
-    _check(lib().mpt_integrate_batch(int(B), _ptr(Lv), _ptr(Nv), int(nsteps), str(tau).encode(),
-                                     str(sigma).encode(), str(R).encode(), str(b).encode(),
-                                     _ptr(signs), _ptr(exps), _ptr(limbs), ctypes.c_uint64(int(stream))))
+    if isinstance(sigma, (list, tuple)):
+        if not (len(sigma) == len(R) == len(b) == B):
+            raise ValueError("per-trajectory sigma, R, b need B strings each")
+        arrs = [(ctypes.c_char_p * B)(*[str(v).encode() for v in vs]) for vs in (sigma, R, b)]
+        _check(lib().mpt_integrate_batch_params(
+            int(B), _ptr(Lv), _ptr(Nv), int(nsteps), str(tau).encode(),
+            *[ctypes.cast(a, ctypes.c_void_p) for a in arrs],
+            _ptr(signs), _ptr(exps), _ptr(limbs), ctypes.c_uint64(int(stream))))
+    else:
+        _check(lib().mpt_integrate_batch(int(B), _ptr(Lv), _ptr(Nv), int(nsteps), str(tau).encode(),
+                                         str(sigma).encode(), str(R).encode(), str(b).encode(),
+                                         _ptr(signs), _ptr(exps), _ptr(limbs),
+                                         ctypes.c_uint64(int(stream))))
     out, off = [], 0
     for j, L in enumerate(Ls):
         L = int(L)

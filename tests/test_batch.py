@@ -107,3 +107,30 @@ def test_batch_refuses_bad_sizes():
         assert b"trajectory" in lib.mpt_last_error()
     assert lib.mpt_integrate_batch(0, None, None, 1, b"0.01", b"10", b"28", b"8/3", None, None, None,
                                    ctypes.c_uint64(0)) == mpt.MPT_EINVAL
+
+
+@pytest.mark.gpu
+def test_batch_with_parameters_of_each_trajectory_matches_oracle():
+    pytest.importorskip("torch")
+    pars = [("10", "28", "8/3"), ("10.5", "27", "2.5"), ("-3/7", "28", "8/3"), ("10", "28", "8/3"),
+            ("16", "45.92", "4")]
+    Ls = [6, 9, 6, 13, 4]
+    Ns = [12, 7, 10, 9, 14]
+    x0s = [O.X0, ("1.5", "-2.25", "20.125"), O.X0, ("0.1", "0.2", "0.3"), ("-1", "2", "30")]
+    states = [lib_state(L, x) for L, x in zip(Ls, x0s)]
+    out = mpt.integrate_batch(Ls, Ns, 3, states, O.TAU, [p[0] for p in pars], [p[1] for p in pars],
+                              [p[2] for p in pars])
+    for j in range(len(Ls)):
+        want = oracle_state(Ls[j], Ns[j], 3, x0s[j], par=pars[j] + (O.TAU,))
+        assert same(out[j], want), j
+
+
+@pytest.mark.gpu
+def test_batch_with_parameters_rejects_a_bad_parameter():
+    pytest.importorskip("torch")
+    Ls, Ns = [5, 5], [6, 6]
+    states = [lib_state(5, O.X0), lib_state(5, O.X0)]
+    with pytest.raises(mpt.MPTError):
+        mpt.integrate_batch(Ls, Ns, 1, states, O.TAU, ["10", "1/0"], ["28", "28"], ["8/3", "8/3"])
+    with pytest.raises(ValueError):
+        mpt.integrate_batch(Ls, Ns, 1, states, O.TAU, ["10"], ["28", "28"], ["8/3", "8/3"])
