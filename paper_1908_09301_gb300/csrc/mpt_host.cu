@@ -62,7 +62,7 @@ int record_error(int code, const char *msg)
 }  // namespace mpt
 
 struct mpt_ctx {
-    int L = 0, Lp = 0, P = 0, N = 0, Wcap = 0, tb = 0;
+    int L = 0, Lp = 0, P = 0, N = 0, Wcap = 0, tb = 0, nwin = 1;
     int dev = 0, sms = 0;
     cudaStream_t st = nullptr;
     int ctas_req = 0;
@@ -312,7 +312,11 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
     int tb = 64;
     while (tb > 8 && mpt::smem_bytes(L, c->Lp, c->N, c->Wcap, tb) > (size_t)smem_optin) tb /= 2;
     c->tb = tb;
-    c->smem = mpt::smem_bytes(L, c->Lp, c->N, c->Wcap, tb);
+    // window copies for the lock-step term phase, as many (up to 8) as fit
+    int nwin = 8;
+    while (nwin > 1 && mpt::smem_bytes(L, c->Lp, c->N, c->Wcap, tb, nwin) > (size_t)smem_optin) nwin /= 2;
+    c->nwin = nwin;
+    c->smem = mpt::smem_bytes(L, c->Lp, c->N, c->Wcap, tb, nwin);
     if (c->smem > (size_t)smem_optin) {
         delete c;
         return fail(MPT_EINVAL, "L = %d, N = %d need %zu bytes of shared memory (device has %d)", L,
@@ -597,6 +601,7 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
     a.N = c->N;
     a.Wcap = c->Wcap;
     a.tb = c->tb;
+    a.nwin = c->nwin;
     a.coefL = c->coefL;
     a.coefE = c->coefE;
     a.coefF = c->coefF;
@@ -810,7 +815,7 @@ int batch_impl(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, cons
         if (!sig[j] || !Rr[j] || !bb[j]) return fail(MPT_EINVAL, "trajectory %d: a parameter is null", j);
     // per trajectory: sizes, staging batch, shared memory; offsets in the packed arrays
     struct Traj {
-        int L, Lp, P, N, Wcap, tb;
+        int L, Lp, P, N, Wcap, tb, nwin;
         size_t off_limbs, off_coef, off_coefEF, off_par, off_st;
         double work;
     };
@@ -896,17 +901,24 @@ int batch_impl(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, cons
     }
     if (nsteps == 0) return MPT_OK;
     // staging batches and shared memory on this device
-    int dev = 0, smem_optin = 0;
+    int dev = 0, smem_optin = 0, smem_sm = 0;
     cudaError_t ce = cudaGetDevice(&dev);
     if (ce == cudaSuccess)
         ce = cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (ce == cudaSuccess)
+        ce = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     if (ce != cudaSuccess) return cuda_fail(ce, "device query");
     for (int j = 0; j < B; j++) {
         Traj &t = T[j];
         int tb = 64;
         while (tb > 8 && mpt::smem_bytes(t.L, t.Lp, t.N, t.Wcap, tb) > (size_t)smem_optin) tb /= 2;
         t.tb = tb;
-        const size_t sm = mpt::smem_bytes(t.L, t.Lp, t.N, t.Wcap, tb);
+        // window copies (up to 8) while two CTAs still share an SM
+        const size_t two = smem_sm > 2048 ? (size_t)smem_sm / 2 - 1024 : 0;
+        int nwin = 8;
+        while (nwin > 1 && mpt::smem_bytes(t.L, t.Lp, t.N, t.Wcap, tb, nwin) > two) nwin /= 2;
+        t.nwin = nwin;
+        const size_t sm = mpt::smem_bytes(t.L, t.Lp, t.N, t.Wcap, tb, nwin);
         if (sm > (size_t)smem_optin)
             return fail(MPT_EINVAL, "trajectory %d: L = %d, N = %d need %zu bytes of shared memory", j,
                         t.L, t.N, sm);
@@ -967,6 +979,7 @@ int batch_impl(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, cons
         a.N = t.N;
         a.Wcap = t.Wcap;
         a.tb = t.tb;
+        a.nwin = t.nwin;
         a.coefL = coefL + t.off_coef;
         a.coefE = coefE + t.off_coefEF;
         a.coefF = coefF + t.off_coefEF;

@@ -51,6 +51,8 @@ struct KArgs {
     const int *sysT;        // [sysNF][4] fixed terms, then [sysNQ][4] Cauchy products
     int sysNF, sysNQ;
     int npar, ptau;         // parameters in parL, tau's index among them
+    int nwin;               // lock-step kernel: copies of the three windows the term
+                            // phase adds into (warp w uses copy w mod nwin; 0 = 1)
 };
 
 // limits of a general system
@@ -103,7 +105,7 @@ int pipe_max_ctas(size_t smem);
 cudaError_t launch_pipe(const KArgs &a, const PArgs &pa, int grid, size_t smem, cudaStream_t st);
 
 // dynamic shared memory bytes for a configuration
-size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb);
+size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb, int nwin = 1);
 // launch nsteps steps on `grid` CTAs (cooperative when grid > 1)
 cudaError_t launch_integrate(const KArgs &a, int grid, size_t smem, cudaStream_t st);
 // largest co-resident grid for this smem size (0 on error)

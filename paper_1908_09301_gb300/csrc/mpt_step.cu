@@ -141,13 +141,15 @@ __device__ __forceinline__ bool cta_ok(const Smem &S, const KArgs &a)
     return S.misc[MS_ERR] == 0;
 }
 
+__device__ __forceinline__ int nwin_of(const KArgs &a) { return a.nwin > 1 ? a.nwin : 1; }
+
 __device__ Smem carve(unsigned char *base, const KArgs &a)
 {
     Smem S;
     vec_sizes(a.Lp, S.AV, S.CV, S.M);
     size_t o = 0;
     S.win = (long long *)(base + o);
-    o = align16(o + sizeof(long long) * 3 * a.Wcap);
+    o = align16(o + sizeof(long long) * 3 * (size_t)nwin_of(a) * a.Wcap);
     S.dig = (uint32_t *)(base + o);
     o = align16(o + sizeof(uint32_t) * 3 * a.Wcap);
     S.expT = (int *)(base + o);
@@ -557,7 +559,7 @@ __device__ void init_slots(const Smem &S, const KArgs &a)
         uint32_t *Cv = S.slots + (size_t)slot * (S.AV + S.CV) + S.AV;
         if (x >= a.Lp) Cv[phys(x)] = 0u;
     }
-    for (int e = threadIdx.x; e < 3 * a.Wcap; e += NT) S.win[e] = 0;
+    for (int e = threadIdx.x; e < 3 * nwin_of(a) * a.Wcap; e += NT) S.win[e] = 0;
 }
 
 // block-wide min (lo) / max (hi) for three targets; returns in S.misc
@@ -676,7 +678,8 @@ __device__ void stage_terms(const Smem &S, const KArgs &a, int m, int t0, int nt
     }
 }
 
-__device__ void run_unit(const Smem &S, const KArgs &a, int slot, int q)
+// unit q of the term in `slot`, added into window copy `copy`
+__device__ void run_unit(const Smem &S, const KArgs &a, int slot, int q, int copy)
 {
     const int off = S.tinfo[2 * slot];
     const int flags = S.tinfo[2 * slot + 1];
@@ -684,7 +687,7 @@ __device__ void run_unit(const Smem &S, const KArgs &a, int slot, int q)
     const int tg = (flags >> 4) & 3;
     const bool neg = flags & 1;
     const uint32_t *A = S.slots + (size_t)slot * (S.AV + S.CV);
-    long long *win = S.win + (size_t)tg * a.Wcap;
+    long long *win = S.win + ((size_t)copy * 3 + tg) * a.Wcap;
     if (flags & 2) {
         add_unit(A, q, win, off, neg);
     } else if (flags & 8) {
@@ -722,13 +725,32 @@ __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
             pr.mark(PR_STAGE);
             const long long ua = max(u0, (long long)tb0 * a.P);
             const long long ub = min(u1, (long long)(tb0 + nt) * a.P);
+            // the column sums of many terms land on the same columns: each warp
+            // adds into a window copy of its own, so that the shared-memory
+            // atomics of different warps do not queue on the same words
+            const int copy = (int)(threadIdx.x >> 5) % nwin_of(a);
             for (long long u = ua + threadIdx.x; u < ub; u += NT) {
                 const int t = (int)(u / a.P);
-                run_unit(S, a, t - tb0, (int)(u - (long long)t * a.P));
+                run_unit(S, a, t - tb0, (int)(u - (long long)t * a.P), copy);
             }
             __syncthreads();
             pr.mark(PR_MAC);
         }
+    }
+    if (nwin_of(a) > 1) {  // the copies into copy 0 (and emptied)
+        for (int tg = 0; tg < 3; tg++) {
+            const int wd = S.misc[MS_WIDTH + tg];
+            for (int c = threadIdx.x; c < wd; c += NT) {
+                long long v = 0;
+                for (int k = 1; k < nwin_of(a); k++) {
+                    long long *w = S.win + ((size_t)k * 3 + tg) * a.Wcap + c;
+                    v += *w;
+                    *w = 0;
+                }
+                if (v) S.win[tg * a.Wcap + c] += v;
+            }
+        }
+        __syncthreads();
     }
     if (G > 1) {
         long long *dst = a.gwin + (size_t)set * 3 * a.Wcap;
@@ -886,7 +908,7 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
         const int units = 2 * nc * a.P;
         for (int u = threadIdx.x; u < units; u += NT) {
             const int slot = u / a.P;
-            run_unit(S, a, slot, u - slot * a.P);
+            run_unit(S, a, slot, u - slot * a.P, 0);
         }
         __syncthreads();
         pr.mark(PR_HMAC);
@@ -1026,13 +1048,13 @@ __global__ void __launch_bounds__(NT, 2) taylor_batch_kernel(const KArgs *args)
 
 }  // namespace
 
-size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb)
+size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb, int nwin)
 {
     (void)L;
     int AV, CV, M;
     vec_sizes(Lp, AV, CV, M);
     size_t o = 0;
-    o = align16(o + sizeof(long long) * 3 * Wcap);
+    o = align16(o + sizeof(long long) * 3 * (size_t)(nwin > 1 ? nwin : 1) * Wcap);
     o = align16(o + sizeof(uint32_t) * 3 * Wcap);
     o = align16(o + sizeof(int) * 3 * (N + 1));
     o = align16(o + sizeof(int) * 3 * (N + 1));
