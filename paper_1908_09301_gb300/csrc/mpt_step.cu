@@ -105,6 +105,7 @@ struct Smem {
     uint32_t *newc;   // [3][Lp]
     uint32_t *slots;  // [tb][AV + CV]
     int *tinfo;       // [tb][2]
+    int *srcs;        // [tb][2] operand sources of the staged terms
     int *misc;        // [MISC_INTS]
     int AV, CV, M;
 };
@@ -161,6 +162,8 @@ __device__ Smem carve(unsigned char *base, const KArgs &a)
     S.slots = (uint32_t *)(base + o);
     o = align16(o + sizeof(uint32_t) * (size_t)a.tb * (S.AV + S.CV));
     S.tinfo = (int *)(base + o);
+    o = align16(o + sizeof(int) * 2 * a.tb);
+    S.srcs = (int *)(base + o);
     o = align16(o + sizeof(int) * 2 * a.tb);
     S.misc = (int *)(base + o);
     return S;
@@ -316,17 +319,6 @@ __device__ __forceinline__ Meta meta_of(const Smem &S, const KArgs &a, int src)
         r.f = __ldg(&a.parF[-1 - src]);
     }
     return r;
-}
-
-// limb x of an operand: parameter, the newest coefficient (index m, kept in
-// shared memory by every CTA) or an older coefficient from global memory
-__device__ __forceinline__ uint32_t fetch_limb(const Smem &S, const KArgs &a, int src, int m, int x)
-{
-    if (src < 0) return __ldg(&a.parL[(size_t)(-1 - src) * a.Lp + x]);
-    const int N1 = a.N + 1;
-    int comp = src / N1, idx = src - comp * N1;
-    if (idx == m) return S.newc[comp * a.Lp + x];
-    return __ldcg(&a.coefL[(size_t)src * a.Lp + x]);
 }
 
 // ------------------------------------------------------------------ the limb-product tile
@@ -632,26 +624,26 @@ __device__ void place_windows(const Smem &S, const KArgs &a, int m)
     reduce_windows(S, a, lo, hi);
 }
 
-// stage terms [t0, t0 + nt) of index m into slots; record offset and flags
+// where a staged operand comes from: a row of the coefficient table (>= 0),
+// parameter p (-1 - p), the newest coefficient of component c in shared memory
+// (SRC_NEWC - c), or nothing
+enum { SRC_NEWC = -100, SRC_NONE = -1000 };
+
+__device__ __forceinline__ int src_code(int src, int m, int N1)
+{
+    if (src < 0) return src;
+    const int comp = src / N1, idx = src - comp * N1;
+    return idx == m ? SRC_NEWC - comp : src;
+}
+
+// stage terms [t0, t0 + nt) of index m into slots; record offset and flags.
+// One thread per slot places the term and records where its operands come
+// from; then all threads copy the operands' limbs, element by element over
+// the whole batch, with no per-element term lookup.
 __device__ void stage_terms(const Smem &S, const KArgs &a, int m, int t0, int nt)
 {
     const int N1 = a.N + 1;
     const int Lp = a.Lp;
-    for (int e = threadIdx.x; e < nt * 2 * Lp; e += NT) {
-        int slot = e / (2 * Lp);
-        int r = e - slot * 2 * Lp;
-        int which = r >= Lp;  // 0: A operand, 1: B operand
-        int x = r - which * Lp;
-        Term tm = term_of(a, m, t0 + slot, N1);
-        uint32_t *base = S.slots + (size_t)slot * (S.AV + S.CV);
-        if (tm.add) {
-            if (which == 0) base[phys(x)] = fetch_limb(S, a, tm.bsrc, m, x);
-        } else if (which == 0) {
-            base[phys(x)] = fetch_limb(S, a, tm.asrc, m, x);
-        } else {
-            base[S.AV + phys(x)] = fetch_limb(S, a, tm.bsrc, m, x);
-        }
-    }
     for (int slot = threadIdx.x; slot < nt; slot += NT) {
         Term tm = term_of(a, m, t0 + slot, N1);
         Meta mb = meta_of(S, a, tm.bsrc);
@@ -675,6 +667,54 @@ __device__ void stage_terms(const Smem &S, const KArgs &a, int m, int t0, int nt
         flags |= tm.target << 4;
         S.tinfo[2 * slot] = off;
         S.tinfo[2 * slot + 1] = flags;
+        int ca = SRC_NONE, cb = SRC_NONE;
+        if (!skip) {
+            if (tm.add) {
+                ca = src_code(tm.bsrc, m, N1);  // a lone number goes to the A layout
+            } else {
+                ca = src_code(tm.asrc, m, N1);
+                cb = src_code(tm.bsrc, m, N1);
+            }
+        }
+        S.srcs[2 * slot] = ca;
+        S.srcs[2 * slot + 1] = cb;
+    }
+    __syncthreads();
+    // element e of slot s: operand e / Lp (0 A, 1 B), limb e mod Lp; each
+    // thread takes elements NT apart, four at a time (loads before stores, so
+    // that their latencies overlap)
+    constexpr int U = 4;
+    const int E = 2 * Lp;
+    int slot = threadIdx.x / E, r = threadIdx.x - slot * E;
+    const int dslot = NT / E, dr = NT - dslot * E;
+    while (slot < nt) {
+        int dst[U];
+        uint32_t v[U];
+#pragma unroll
+        for (int k = 0; k < U; k++) {
+            dst[k] = -1;
+            v[k] = 0u;
+            if (slot < nt) {
+                const int which = r >= Lp ? 1 : 0;
+                const int x = r - which * Lp;
+                const int code = S.srcs[2 * slot + which];
+                if (code != SRC_NONE) {
+                    if (code >= 0) v[k] = __ldcg(&a.coefL[(size_t)code * Lp + x]);
+                    else if (code <= SRC_NEWC) v[k] = S.newc[(SRC_NEWC - code) * Lp + x];
+                    else v[k] = __ldg(&a.parL[(size_t)(-1 - code) * Lp + x]);
+                    dst[k] = slot * (S.AV + S.CV) + (which ? S.AV + phys(x) : phys(x));
+                }
+            }
+            slot += dslot;
+            r += dr;
+            if (r >= E) {
+                r -= E;
+                slot++;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < U; k++)
+            if (dst[k] >= 0) S.slots[dst[k]] = v[k];
     }
 }
 
@@ -1060,6 +1100,7 @@ size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb, int nwin)
     o = align16(o + sizeof(int) * 3 * (N + 1));
     o = align16(o + sizeof(uint32_t) * 3 * Lp);
     o = align16(o + sizeof(uint32_t) * (size_t)tb * (AV + CV));
+    o = align16(o + sizeof(int) * 2 * tb);
     o = align16(o + sizeof(int) * 2 * tb);
     o = align16(o + sizeof(int) * MISC_INTS);
     return o;
