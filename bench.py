@@ -17,6 +17,12 @@ limb-product rate with the INT32 multiply-add roofline (bound "alu").
 ``cpu_baseline`` times the CPU oracle on a bounded sample on the host's cores.
 Multi-GPU (torchrun): independent replicas, one per rank, no collective on the
 data path ("replicas only": a single trajectory does not shard).
+
+Other lines, each a JSON line of the same form:
+
+  python bench.py --ensemble B        B trajectories of the perturbed ensemble in one batch
+  python bench.py --system NAME       a general quadratic system (roessler, chen, lorenz)
+  python bench.py --grad B            3x6 flow Jacobians of B trajectories (central differences)
 """
 from __future__ import annotations
 
