@@ -222,7 +222,14 @@ void free_all(mpt_ctx *c)
 template <class T>
 cudaError_t dalloc(T **p, size_t count)
 {
-    return cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
+    const cudaError_t e = cudaMalloc((void **)p, sizeof(T) * (count ? count : 1));
+    // a refused allocation is not sticky, but it stays the runtime's "last
+    // error", which the launch paths read after a kernel launch: clear it
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        (void)cudaGetLastError();
+    }
+    return e;
 }
 
 }  // namespace

@@ -134,3 +134,18 @@ def test_batch_with_parameters_rejects_a_bad_parameter():
         mpt.integrate_batch(Ls, Ns, 1, states, O.TAU, ["10", "1/0"], ["28", "28"], ["8/3", "8/3"])
     with pytest.raises(ValueError):
         mpt.integrate_batch(Ls, Ns, 1, states, O.TAU, ["10"], ["28", "28"], ["8/3", "8/3"])
+
+
+@pytest.mark.gpu
+def test_batch_larger_than_device_memory_reports_enomem():
+    # 25000 trajectories of 512 limbs and order 2000 need about 300 GB of
+    # coefficient tables: the allocation is refused, nothing runs, the states
+    # stay as they were
+    pytest.importorskip("torch")
+    B, L, N = 25000, 512, 2000
+    one = lib_state(L, O.X0)
+    states = [one] * B
+    with pytest.raises(mpt.MPTError) as ei:
+        mpt.integrate_batch([L] * B, [N] * B, 1, states)
+    assert ei.value.code == -2  # MPT_ENOMEM
+    assert np.array_equal(states[0][2], lib_state(L, O.X0)[2])
