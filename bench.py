@@ -155,6 +155,23 @@ def cpu_oracle_rate(wl, nsteps: int):
     return nsteps / dt, threads, dt
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest of every rank's x (the slowest rank sets a timed region);
+    x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, seconds_per_step: float) -> float:
+    """Steps of the whole job per second: every rank runs its own replica, so
+    world steps finish in the slowest rank's step time."""
+    return world / seconds_per_step
+
+
 def reference_arm(args, wl):
     """The reference arm of this repository is the CPU oracle itself."""
     rank = int(os.environ.get("RANK", "0"))
@@ -529,11 +546,8 @@ def main():
         dist.barrier()
     ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms_per_step = sum(ms_steps) / len(ms_steps)
-    if dist is not None:
-        t = torch.tensor([ms_per_step], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_per_step = float(t.item())
-    value = world * 1000.0 / ms_per_step
+    ms_per_step = max_over_ranks(ms_per_step, dist)
+    value = job_rate(world, ms_per_step / 1000.0)
 
     # end to end through the C ABI: host state in, one step, host state out
     s0, e0, l0 = ctx.get_state()
@@ -551,11 +565,8 @@ def main():
         ctx.step()
         hs, he, hl = ctx.get_state()
     e2e_s = time.perf_counter() - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = world * args.steps / e2e_s
+    e2e_s = max_over_ranks(e2e_s, dist)
+    e2e_value = job_rate(world, e2e_s / args.steps)
 
     work = wl.work_per_step()
     peaks = measured_peaks()
