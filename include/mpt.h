@@ -258,6 +258,29 @@ int mpt_integrate_batch_params(int B, const int32_t *Ls, const int32_t *Ns, int6
                                uint32_t *limbs, uint64_t cuda_stream);
 
 /*
+ * Vector-Jacobian products of the n-step map (x0, y0, z0, sigma, R, b) ->
+ * (x, y, z) after nsteps steps of Eq. (3) and Eq. (2), for B initial points,
+ * by central differences of bit-exact runs at L limbs and order N:
+ * J[:, i] = (F(u + h e_i) - F(u - h e_i)) / (2h), h = 10^(-h_digits) (0: 100),
+ * each difference formed exactly and rounded once to double.  Its error is
+ * about |F'''| h^2 + 2^(-32 (L-1)) |F| / h (e.g. 1e-200 of |F| at L = 32,
+ * h = 1e-100).  The 12 B runs go to one batch launch.  (The paper has no
+ * derivatives; this is the differentiation of its flow.)
+ *   x0[B * 3]:         initial values (strings, as mpt_set_state), point-major;
+ *   sigma, R, b, tau:  strings, as mpt_init;
+ *   g[B * 3]:          the upstream gradient of each final state (host);
+ *   g_x0[B * 3]:       out, g^T J with respect to the x0, y0, z0 of each point;
+ *   g_params[3]:       out, g^T J with respect to sigma, R, b, summed over points;
+ *   jac[B * 3 * 6]:    out (nullable), J per point, [output][input].
+ * Host arrays; synchronous on cuda_stream.  Errors as mpt_integrate_batch;
+ * MPT_EINVAL for a malformed string, a null array or h_digits outside 1..10000.
+ */
+int mpt_backward(int B, int L, int N, int64_t nsteps, const char *tau, const char *sigma,
+                 const char *R, const char *b, const char *const *x0, const double *g,
+                 int h_digits, double *g_x0, double *g_params, double *jac,
+                 uint64_t cuda_stream);
+
+/*
  * Allocation-free stepping (the paper has no counterpart; it is a service of
  * this library).  Some callers cannot call cudaMalloc when they step: code
  * whose device memory belongs to a pool it may not grow, a plug-in of a

@@ -7,7 +7,10 @@
 // value.  This file holds a small unsigned big integer with exactly the
 // operations that needs: decimal digits in, shifts, comparison, subtraction
 // and long division.
+#include <algorithm>
+#include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -243,7 +246,143 @@ bool parse_rational(const char *s, Rat &out)
     return true;
 }
 
+// a / d for a small d, a replaced by the quotient; returns the remainder
+uint32_t div_small(BigU &a, uint32_t d)
+{
+    uint64_t r = 0;
+    for (size_t i = a.w.size(); i-- > 0;) {
+        const uint64_t cur = (r << 32) | a.w[i];
+        a.w[i] = (uint32_t)(cur / d);
+        r = cur % d;
+    }
+    a.trim();
+    return (uint32_t)r;
+}
+
+std::string to_decimal(BigU a)
+{
+    if (a.zero()) return "0";
+    std::vector<uint32_t> parts;  // base 10^9, least significant first
+    while (!a.zero()) parts.push_back(div_small(a, 1000000000u));
+    std::string out = std::to_string(parts.back());
+    char buf[16];
+    for (size_t i = parts.size() - 1; i-- > 0;) {
+        std::snprintf(buf, sizeof buf, "%09u", parts[i]);
+        out += buf;
+    }
+    return out;
+}
+
+// M 2^(32 sh) of an L-limb magnitude, sh >= 0
+BigU magnitude(const uint32_t *l, int L, long long sh)
+{
+    BigU m;
+    m.w.assign(l, l + L);
+    m.trim();
+    m.shl(32 * sh);
+    return m;
+}
+
 }  // namespace
+
+// The exact rational x + sgn 10^(-h_digits) of a decimal or rational string,
+// written as "p/q".  Returns 0, or -1 for a malformed x.
+int perturbed_string(const char *x, int h_digits, int sgn, std::string &out)
+{
+    Rat r;
+    if (!parse_rational(x, r) || h_digits < 0 || h_digits > kMaxDecimalExponent) return -1;
+    // (+-num 10^h + sgn den) / (den 10^h)
+    const BigU p = pow10(h_digits);
+    BigU a = mul(r.num, p);
+    const BigU &b = r.den;
+    const bool aneg = r.neg, bneg = sgn < 0;
+    bool neg;
+    BigU n;
+    if (aneg == bneg) {  // same signs: add
+        n = a;
+        BigU t = b;
+        n.w.resize(std::max(n.w.size(), t.w.size()) + 1, 0);
+        uint64_t c = 0;
+        for (size_t i = 0; i < n.w.size(); i++) {
+            const uint64_t v = (uint64_t)n.w[i] + (i < t.w.size() ? t.w[i] : 0) + c;
+            n.w[i] = (uint32_t)v;
+            c = v >> 32;
+        }
+        n.trim();
+        neg = aneg;
+    } else if (cmp(a, b) >= 0) {
+        n = a;
+        sub_inplace(n, b);
+        neg = aneg;
+    } else {
+        n = b;
+        sub_inplace(n, a);
+        neg = bneg;
+    }
+    const BigU q = mul(r.den, p);
+    out = (neg && !n.zero() ? "-" : "") + to_decimal(n) + "/" + to_decimal(q);
+    return 0;
+}
+
+// (v1 - v2) / (2 10^(-h_digits)) of two L-limb numbers in the interchange
+// layout, rounded once to the nearest double (ties to even).
+double diff_over_2h(int L, int32_t s1, int32_t e1, const uint32_t *l1, int32_t s2, int32_t e2,
+                    const uint32_t *l2, int h_digits)
+{
+    bool z1 = true, z2 = true;
+    for (int j = 0; j < L; j++) {
+        z1 = z1 && l1[j] == 0;
+        z2 = z2 && l2[j] == 0;
+    }
+    if (z1 && z2) return 0.0;
+    const long long emin = z1 ? e2 : (z2 ? e1 : std::min(e1, e2));
+    BigU a = z1 ? BigU() : magnitude(l1, L, (long long)e1 - emin);
+    BigU b = z2 ? BigU() : magnitude(l2, L, (long long)e2 - emin);
+    const bool aneg = s1 != 0, bneg = s2 == 0;  // v1 - v2 = v1 + (-v2)
+    bool neg;
+    BigU d;
+    if (aneg == bneg) {
+        d = a;
+        d.w.resize(std::max(d.w.size(), b.w.size()) + 1, 0);
+        uint64_t c = 0;
+        for (size_t i = 0; i < d.w.size(); i++) {
+            const uint64_t v = (uint64_t)d.w[i] + (i < b.w.size() ? b.w[i] : 0) + c;
+            d.w[i] = (uint32_t)v;
+            c = v >> 32;
+        }
+        d.trim();
+        neg = aneg;
+    } else if (cmp(a, b) >= 0) {
+        d = a;
+        sub_inplace(d, b);
+        neg = aneg;
+    } else {
+        d = b;
+        sub_inplace(d, a);
+        neg = bneg;
+    }
+    if (d.zero()) return 0.0;
+    // |result| = Y 2^k, Y = |d| 10^h, k = 32 (emin - L) - 1
+    const BigU y = mul(d, pow10(h_digits));
+    const long long k = 32LL * (emin - L) - 1;
+    const int nb = y.bits();
+    double r;
+    if (nb <= 53) {
+        uint64_t v = 0;
+        for (size_t i = y.w.size(); i-- > 0;) v = (v << 32) | y.w[i];
+        r = std::ldexp((double)v, (int)k);
+    } else {
+        const int drop = nb - 53;
+        uint64_t q = 0;
+        for (int i = nb - 1; i >= drop; i--) q = (q << 1) | (uint64_t)y.bit(i);
+        const int half = y.bit(drop - 1);
+        bool sticky = false;
+        for (int i = drop - 2; i >= 0 && !sticky; i--) sticky = y.bit(i) != 0;
+        if (half && (sticky || (q & 1))) q++;
+        r = std::ldexp((double)q, (int)(k + drop));
+    }
+    return neg ? -r : r;
+}
 
 // trunc_L of an exact decimal or rational string.  Returns 0, or -1 for a
 // malformed string, -3 for an exponent outside |exp| <= 2^30.

@@ -1,10 +1,17 @@
 // host_parse.h -- exact decimal / rational string -> L-limb number (host).
 #pragma once
 #include <cstdint>
+#include <string>
 
 namespace mpt_host {
 // trunc_L of the exact value of `str` (decimal such as "-15.8", "1e-20", or a
 // rational "p/q" of two decimals).  Returns 0, -1 for a malformed string or a
 // zero denominator, -3 for an exponent outside |exp| <= 2^30.
 int parse_number(const char *str, int L, int32_t *sign, int32_t *exp, uint32_t *limbs);
+// the exact x + sgn 10^(-h_digits) as "p/q"; 0, or -1 for a malformed x
+int perturbed_string(const char *x, int h_digits, int sgn, std::string &out);
+// (v1 - v2) / (2 10^(-h_digits)) of two L-limb interchange numbers, rounded
+// once to the nearest double
+double diff_over_2h(int L, int32_t s1, int32_t e1, const uint32_t *l1, int32_t s2, int32_t e2,
+                    const uint32_t *l2, int h_digits);
 }  // namespace mpt_host

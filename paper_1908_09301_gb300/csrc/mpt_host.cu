@@ -1060,4 +1060,69 @@ int mpt_integrate_batch_params(int B, const int32_t *Ls, const int32_t *Ns, int6
     return batch_impl(B, Ls, Ns, nsteps, tau, sigma, R, b, 1, signs, exps, limbs, cuda_stream);
 }
 
+int mpt_backward(int B, int L, int N, int64_t nsteps, const char *tau, const char *sigma, const char *R,
+                 const char *b, const char *const *x0, const double *g, int h_digits, double *g_x0,
+                 double *g_params, double *jac, uint64_t cuda_stream)
+{
+    if (B < 1) return fail(MPT_EINVAL, "batch size %d < 1", B);
+    if (!tau || !sigma || !R || !b || !x0 || !g || !g_x0 || !g_params)
+        return fail(MPT_EINVAL, "null argument");
+    if (h_digits == 0) h_digits = 100;
+    if (h_digits < 1 || h_digits > 10000) return fail(MPT_EINVAL, "h_digits = %d outside 1..10000", h_digits);
+    if (L < 1 || L > mpt::MAX_L) return fail(MPT_EINVAL, "L = %d outside 1..%d", L, mpt::MAX_L);
+    for (int j = 0; j < 3 * B; j++)
+        if (!x0[j]) return fail(MPT_EINVAL, "initial value %d is null", j);
+    // runs: per point j and input i (x0, y0, z0, sigma, R, b), u + h e_i then u - h e_i
+    const int runs = 12 * B;
+    const char *par[3] = {sigma, R, b};
+    std::vector<std::string> pstr((size_t)runs * 3);
+    std::vector<int32_t> ss((size_t)runs * 3), se((size_t)runs * 3), Ls(runs, L), Ns(runs, N);
+    std::vector<uint32_t> sl((size_t)runs * 3 * L);
+    for (int j = 0; j < B; j++)
+        for (int i = 0; i < 6; i++)
+            for (int t = 0; t < 2; t++) {
+                const int run = (j * 6 + i) * 2 + t, sg = t == 0 ? 1 : -1;
+                for (int k = 0; k < 3; k++) {
+                    std::string v = x0[3 * j + k];
+                    if (i == k && mpt_host::perturbed_string(x0[3 * j + k], h_digits, sg, v))
+                        return fail(MPT_EINVAL, "cannot use initial value \"%s\"", x0[3 * j + k]);
+                    const size_t q = (size_t)run * 3 + k;
+                    const int rc = mpt_host::parse_number(v.c_str(), L, &ss[q], &se[q], &sl[q * L]);
+                    if (rc) return fail(rc == -3 ? MPT_ERANGE : MPT_EINVAL, "cannot use initial value \"%s\"",
+                                        x0[3 * j + k]);
+                    std::string pv = par[k];
+                    if (i == 3 + k && mpt_host::perturbed_string(par[k], h_digits, sg, pv))
+                        return fail(MPT_EINVAL, "cannot use parameter \"%s\"", par[k]);
+                    pstr[q] = pv;
+                }
+            }
+    std::vector<const char *> ps[3];
+    for (int k = 0; k < 3; k++) {
+        ps[k].resize(runs);
+        for (int r = 0; r < runs; r++) ps[k][r] = pstr[(size_t)r * 3 + k].c_str();
+    }
+    const int rc = batch_impl(runs, Ls.data(), Ns.data(), nsteps, tau, ps[0].data(), ps[1].data(),
+                              ps[2].data(), 1, ss.data(), se.data(), sl.data(), cuda_stream);
+    if (rc) return rc;
+    for (int p = 0; p < 3; p++) g_params[p] = 0.0;
+    for (int j = 0; j < B; j++) {
+        double J[3][6];
+        for (int i = 0; i < 6; i++)
+            for (int o = 0; o < 3; o++) {
+                const size_t a = ((size_t)(j * 6 + i) * 2) * 3 + o, c = a + 3;
+                J[o][i] = mpt_host::diff_over_2h(L, ss[a], se[a], &sl[a * L], ss[c], se[c], &sl[c * L], h_digits);
+            }
+        for (int i = 0; i < 6; i++) {
+            double v = 0.0;
+            for (int o = 0; o < 3; o++) v += g[3 * j + o] * J[o][i];
+            if (i < 3) g_x0[3 * j + i] = v;
+            else g_params[i - 3] += v;
+        }
+        if (jac)
+            for (int o = 0; o < 3; o++)
+                for (int i = 0; i < 6; i++) jac[((size_t)j * 3 + o) * 6 + i] = J[o][i];
+    }
+    return MPT_OK;
+}
+
 }  // extern "C"

@@ -13,10 +13,11 @@ rounded once.  All runs of a call (the base point and the twelve perturbed
 runs of every initial point) go through one ``mpt_integrate_batch_params``
 launch.  The differences are formed exactly on the host.
 
-``TaylorFlow`` wraps it as a ``torch.autograd.Function``: float64 inputs (their
-exact binary values are the multiple-precision inputs), float64 outputs; the
-backward pass runs the perturbed trajectories and returns the
-vector-Jacobian products.
+``TaylorFlow`` wraps the same differences as a ``torch.autograd.Function``:
+float64 inputs (their exact binary values are the multiple-precision inputs),
+float64 outputs; its backward pass is ``mpt_backward`` (the twelve perturbed
+runs of every point in one batch launch, the differences formed exactly and
+rounded once on the host, and the vector-Jacobian products).
 """
 from __future__ import annotations
 
@@ -132,11 +133,14 @@ def _torch_function():
 
         @staticmethod
         def backward(ctx, g):
+            # the twelve perturbed runs of every point and the products g^T J
+            # through the C ABI (mpt_backward)
             xs, ps, L, N, nsteps, tau = ctx.cfg
-            _, J = flow_jacobian(xs, ps, tau, L, N, nsteps, with_value=False)
-            Jt = torch.as_tensor(J, dtype=torch.float64, device=g.device)
-            vj = torch.einsum("bi,bij->bj", g.to(torch.float64), Jt)
-            return vj[:, :3], vj[:, 3:].sum(0), None, None, None, None
+            gx, gp, _ = mpt.backward([[ratstr(exact(v)) for v in x] for x in xs],
+                                     g.detach().to(torch.float64).cpu().numpy(), L, N, nsteps,
+                                     ratstr(exact(tau)), *[ratstr(exact(v)) for v in ps])
+            return (torch.as_tensor(gx, dtype=torch.float64, device=g.device),
+                    torch.as_tensor(gp, dtype=torch.float64, device=g.device), None, None, None, None)
 
     _FN = TaylorFlow
     return _FN

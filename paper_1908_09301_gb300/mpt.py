@@ -65,6 +65,9 @@ SIGNATURES = {
                                            vp, ctypes.c_uint64]),
     "mpt_integrate_batch_params": (ctypes.c_int, [ctypes.c_int, vp, vp, ctypes.c_int64, ctypes.c_char_p,
                                                   vp, vp, vp, vp, vp, vp, ctypes.c_uint64]),
+    "mpt_backward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_char_p,
+                                    ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, vp, vp, ctypes.c_int,
+                                    vp, vp, vp, ctypes.c_uint64]),
     "mpt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mpt_last_error": (ctypes.c_char_p, []),
 }
@@ -332,6 +335,27 @@ def integrate_batch(Ls, Ns, nsteps: int, states, tau: str = "0.01", sigma="10",
                     limbs[off:off + 3 * L].reshape(3, L).copy()))
         off += 3 * L
     return out
+
+
+def backward(x0s, g, L: int, N: int, nsteps: int, tau: str = "0.01", sigma: str = "10", R: str = "28",
+             b: str = "8/3", h_digits: int = 100, with_jacobian: bool = False, stream: int = 0):
+    """``mpt_backward``: for initial points x0s (B triples of strings) and the
+    upstream gradients g [B, 3], returns g^T J with respect to the points
+    [B, 3] and to (sigma, R, b) [3], and the Jacobians [B, 3, 6] if asked."""
+    B = len(x0s)
+    strs = [str(v).encode() for p in x0s for v in p]
+    if len(strs) != 3 * B:
+        raise ValueError("each initial point needs three values")
+    arr = (ctypes.c_char_p * len(strs))(*strs)
+    gv = np.ascontiguousarray(np.asarray(g, np.float64).reshape(B, 3))
+    gx = np.zeros((B, 3), np.float64)
+    gp = np.zeros(3, np.float64)
+    J = np.zeros((B, 3, 6), np.float64) if with_jacobian else None
+    _check(lib().mpt_backward(int(B), int(L), int(N), int(nsteps), str(tau).encode(), str(sigma).encode(),
+                              str(R).encode(), str(b).encode(), ctypes.cast(arr, ctypes.c_void_p), _ptr(gv),
+                              int(h_digits), _ptr(gx), _ptr(gp), _ptr(J) if J is not None else None,
+                              ctypes.c_uint64(int(stream))))
+    return gx, gp, J
 
 
 def int_peak(variant: int, iters: int = 20000, threads: int = 1024):

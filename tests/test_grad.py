@@ -149,3 +149,26 @@ def test_autograd_wrapper_passes_gradcheck(gpu):
     p = torch.tensor([10.0, 28.0, 8.0 / 3.0], dtype=torch.float64, requires_grad=True)
     fn = lambda a, b: gpu.taylor_flow(a, b, L=12, N=20, nsteps=10)
     assert torch.autograd.gradcheck(fn, (x0, p), eps=1e-6, atol=1e-6, rtol=1e-4)
+
+
+@pytest.mark.gpu
+def test_c_abi_backward_equals_the_python_differences(gpu):
+    from paper_1908_09301_gb300 import mpt
+    L, N, steps = 9, 10, 4
+    x0s = [O.X0, ("1.5", "-2.25", "20.125"), ("0.1", "-0.2", "0.3")]
+    g = np.array([[1.0, -2.0, 0.5], [0.25, 0.0, 3.0], [-1.0, 1.0, 1.0]])
+    gx, gp, J = mpt.backward(x0s, g, L, N, steps, h_digits=25, with_jacobian=True)
+    _, Jp = gpu.flow_jacobian(x0s, L=L, N=N, nsteps=steps, h=Fraction(1, 10 ** 25), with_value=False)
+    assert np.array_equal(J, Jp)  # C++ and Python differences: both exact, rounded once
+    want = np.einsum("bi,bij->bj", g, J)
+    assert np.allclose(gx, want[:, :3], rtol=1e-15, atol=0)
+    assert np.allclose(gp, want[:, 3:].sum(0), rtol=1e-14, atol=0)
+
+
+@pytest.mark.gpu
+def test_c_abi_backward_rejects_bad_input(gpu):
+    from paper_1908_09301_gb300 import mpt
+    with pytest.raises(mpt.MPTError):
+        mpt.backward([("1", "2", "x")], np.zeros((1, 3)), 5, 6, 1)
+    with pytest.raises(mpt.MPTError):
+        mpt.backward([("1", "2", "3")], np.zeros((1, 3)), 5, 6, 1, h_digits=20000)
