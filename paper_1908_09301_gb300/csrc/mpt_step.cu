@@ -332,17 +332,16 @@ __device__ __forceinline__ Meta meta_of(const Smem &S, const KArgs &a, int src)
 // Lp <= x < Lp+W), which makes the hand-over from block1 to block2 seamless;
 // the block1 sums are saved at the hand-over (a predicated copy, so the warp
 // never diverges) and block2 = final - saved.
+// The walk of unit q over the limbs of A: a = the sums of all its columns'
+// products, s = those of block 1 (saved at the hand-over).
 template <bool SPARSE>
-__device__ void mac_pair(const uint32_t *A, const uint32_t *C, int q, int P, int Lp, int M,
-                         long long *win, int off, bool neg)
+__device__ __forceinline__ void unit_sums(const uint32_t *A, const uint32_t *C, int q, int P, int M,
+                                          uint32_t (&a0)[W], uint32_t (&a1)[W], uint32_t (&a2)[W],
+                                          uint32_t (&s0)[W], uint32_t (&s1)[W], uint32_t (&s2)[W])
 {
-    uint32_t a0[W], a1[W], a2[W], s0[W], s1[W], s2[W], bw[W];
+    uint32_t bw[W];
 #pragma unroll
-    for (int k = 0; k < W; k++) {
-        a0[k] = a1[k] = a2[k] = 0u;
-        s0[k] = s1[k] = s2[k] = 0u;
-        bw[k] = C[phys(q * W + k)];
-    }
+    for (int k = 0; k < W; k++) bw[k] = C[phys(q * W + k)];
     for (int j = 0; j <= P; j++) {
         const bool snap = (j == q + 1);
 #pragma unroll
@@ -368,30 +367,107 @@ __device__ void mac_pair(const uint32_t *A, const uint32_t *C, int q, int P, int
             bw[0] = Cp[W - 1 - u];
         }
     }
+}
+
+// column t of block 1 (v1) and of block 2 (v2) of a unit's sums
+__device__ __forceinline__ void unit_digit(const uint32_t (&a0)[W], const uint32_t (&a1)[W],
+                                           const uint32_t (&a2)[W], const uint32_t (&s0)[W],
+                                           const uint32_t (&s1)[W], const uint32_t (&s2)[W], int t,
+                                           long long &v1, long long &v2)
+{
+    v1 = 0;
+    v2 = 0;
+    if (t < W) {
+        v1 += s0[t];
+        v2 += (long long)a0[t] - s0[t];
+    }
+    if (t >= 1 && t - 1 < W) {
+        v1 += s1[t - 1];
+        v2 += (long long)a1[t - 1] - s1[t - 1];
+    }
+    if (t >= 2 && t - 2 < W) {
+        v1 += s2[t - 2];
+        v2 += (long long)a2[t - 2] - s2[t - 2];
+    }
+}
+
+template <bool SPARSE>
+__device__ void mac_pair(const uint32_t *A, const uint32_t *C, int q, int P, int Lp, int M,
+                         long long *win, int off, bool neg)
+{
+    uint32_t a0[W], a1[W], a2[W], s0[W], s1[W], s2[W];
+#pragma unroll
+    for (int k = 0; k < W; k++) a0[k] = a1[k] = a2[k] = s0[k] = s1[k] = s2[k] = 0u;
+    unit_sums<SPARSE>(A, C, q, P, M, a0, a1, a2, s0, s1, s2);
     // block1 = saved sums at columns qW + t, block2 = final - saved at qW + Lp + t
     long long *w1 = win + off + q * W;
     long long *w2 = w1 + Lp;
 #pragma unroll
     for (int t = 0; t < W + 2; t++) {
-        long long v1 = 0, v2 = 0;
-        if (t < W) {
-            v1 += s0[t];
-            v2 += (long long)a0[t] - s0[t];
-        }
-        if (t >= 1 && t - 1 < W) {
-            v1 += s1[t - 1];
-            v2 += (long long)a1[t - 1] - s1[t - 1];
-        }
-        if (t >= 2 && t - 2 < W) {
-            v1 += s2[t - 2];
-            v2 += (long long)a2[t - 2] - s2[t - 2];
-        }
+        long long v1, v2;
+        unit_digit(a0, a1, a2, s0, s1, s2, t, v1, v2);
         if (neg) {
             v1 = -v1;
             v2 = -v2;
         }
         if (v1) atomicAdd((unsigned long long *)&w1[t], (unsigned long long)v1);
         if (v2) atomicAdd((unsigned long long *)&w2[t], (unsigned long long)v2);
+    }
+}
+
+// A unit of the term phase, called by all 32 lanes of a warp together
+// (`prod` false: no work for this lane).  The lanes hold units of
+// consecutive terms with the same q, so lanes whose sums go to the same
+// columns (same window, offset and q) are neighbours: each run of them is
+// summed by shuffles into its first lane, which alone adds into the window.
+__device__ void mac_unit_warp(const uint32_t *A, const uint32_t *C, int q, int P, int Lp, int M,
+                              long long *win, int off, bool neg, bool prod, bool sparse)
+{
+    const int lane = threadIdx.x & 31;
+    uint32_t a0[W], a1[W], a2[W], s0[W], s1[W], s2[W];
+#pragma unroll
+    for (int k = 0; k < W; k++) a0[k] = a1[k] = a2[k] = s0[k] = s1[k] = s2[k] = 0u;
+    if (prod) {
+        if (sparse) unit_sums<true>(A, C, q, P, M, a0, a1, a2, s0, s1, s2);
+        else unit_sums<false>(A, C, q, P, M, a0, a1, a2, s0, s1, s2);
+    }
+    __syncwarp();
+    long long *w1 = win + off + q * W;
+    const long long key = prod ? (long long)(size_t)w1 : -1 - (long long)lane;
+    const long long prev = __shfl_up_sync(FULL, key, 1);
+    const bool head = lane == 0 || prev != key;
+    const unsigned heads = __ballot_sync(FULL, head);
+    const unsigned above = heads & ~((2u << lane) - 1u);
+    const int seg_end = above ? __ffs(above) - 2 : 31;
+    long long v1[W + 2], v2[W + 2];
+#pragma unroll
+    for (int t = 0; t < W + 2; t++) {
+        unit_digit(a0, a1, a2, s0, s1, s2, t, v1[t], v2[t]);
+        if (neg) {
+            v1[t] = -v1[t];
+            v2[t] = -v2[t];
+        }
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const bool take = lane + d <= seg_end;
+#pragma unroll
+        for (int t = 0; t < W + 2; t++) {
+            const long long o1 = __shfl_down_sync(FULL, v1[t], d);
+            const long long o2 = __shfl_down_sync(FULL, v2[t], d);
+            if (take) {
+                v1[t] += o1;
+                v2[t] += o2;
+            }
+        }
+    }
+    if (prod && head) {
+        long long *w2 = w1 + Lp;
+#pragma unroll
+        for (int t = 0; t < W + 2; t++) {
+            if (v1[t]) atomicAdd((unsigned long long *)&w1[t], (unsigned long long)v1[t]);
+            if (v2[t]) atomicAdd((unsigned long long *)&w2[t], (unsigned long long)v2[t]);
+        }
     }
 }
 
@@ -737,6 +813,24 @@ __device__ void run_unit(const Smem &S, const KArgs &a, int slot, int q, int cop
     }
 }
 
+// run_unit for all lanes of a warp (slot < 0: nothing for this lane); lone
+// numbers are added directly, products through mac_unit_warp
+__device__ void run_unit_warp(const Smem &S, const KArgs &a, int slot, int q, int copy)
+{
+    int off = 0, flags = 4;
+    if (slot >= 0) {
+        off = S.tinfo[2 * slot];
+        flags = S.tinfo[2 * slot + 1];
+    }
+    const bool live = !(flags & 4);
+    const int tg = (flags >> 4) & 3;
+    const bool neg = flags & 1;
+    const uint32_t *A = S.slots + (size_t)(slot >= 0 ? slot : 0) * (S.AV + S.CV);
+    long long *win = S.win + ((size_t)copy * 3 + tg) * a.Wcap;
+    if (live && (flags & 2)) add_unit(A, q, win, off, neg);
+    mac_unit_warp(A, A + S.AV, q, a.P, a.Lp, S.M, win, off, neg, live && !(flags & 2), (flags & 8) != 0);
+}
+
 // this CTA's share of the products of index m, added into the shared windows
 // and then into the global accumulators
 __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
@@ -769,9 +863,19 @@ __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
             // adds into a window copy of its own, so that the shared-memory
             // atomics of different warps do not queue on the same words
             const int copy = (int)(threadIdx.x >> 5) % nwin_of(a);
-            for (long long u = ua + threadIdx.x; u < ub; u += NT) {
-                const int t = (int)(u / a.P);
-                run_unit(S, a, t - tb0, (int)(u - (long long)t * a.P), copy);
+            // units (slot, q) of the batch, slot fastest, a warp's 32 lanes at a
+            // time (every lane of a warp makes the same number of passes)
+            const int total = nt * a.P, lane = threadIdx.x & 31;
+            for (int base = threadIdx.x - lane; base < total; base += NT) {
+                const int i = base + lane;
+                int slot = -1, q = 0;
+                if (i < total) {
+                    q = i / nt;
+                    slot = i - q * nt;
+                    const long long u = (long long)(tb0 + slot) * a.P + q;
+                    if (u < ua || u >= ub) slot = -1;  // another CTA's share
+                }
+                run_unit_warp(S, a, slot, q, copy);
             }
             __syncthreads();
             pr.mark(PR_MAC);
