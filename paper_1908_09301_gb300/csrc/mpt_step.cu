@@ -833,6 +833,8 @@ __device__ void run_unit_warp(const Smem &S, const KArgs &a, int slot, int q, in
 
 // this CTA's share of the products of index m, added into the shared windows
 // and then into the global accumulators
+// ONE_CTA: compiled for a grid of one CTA only (the batch)
+template <bool ONE_CTA>
 __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
 {
     const int G = vgrid(a), g = vrank(a);
@@ -863,19 +865,30 @@ __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
             // adds into a window copy of its own, so that the shared-memory
             // atomics of different warps do not queue on the same words
             const int copy = (int)(threadIdx.x >> 5) % nwin_of(a);
-            // units (slot, q) of the batch, slot fastest, a warp's 32 lanes at a
-            // time (every lane of a warp makes the same number of passes)
-            const int total = nt * a.P, lane = threadIdx.x & 31;
-            for (int base = threadIdx.x - lane; base < total; base += NT) {
-                const int i = base + lane;
-                int slot = -1, q = 0;
-                if (i < total) {
-                    q = i / nt;
-                    slot = i - q * nt;
-                    const long long u = (long long)(tb0 + slot) * a.P + q;
-                    if (u < ua || u >= ub) slot = -1;  // another CTA's share
+            if (ONE_CTA || G == 1) {
+                // one CTA takes every term: units (slot, q), slot fastest, a
+                // warp's 32 lanes at a time (every lane of a warp makes the same
+                // number of passes), so that many lanes share destinations and
+                // combine before the atomics
+                const int total = nt * a.P, lane = threadIdx.x & 31;
+                for (int base = threadIdx.x - lane; base < total; base += NT) {
+                    const int i = base + lane;
+                    int slot = -1, q = 0;
+                    if (i < total) {
+                        q = i / nt;
+                        slot = i - q * nt;
+                        const long long u = (long long)(tb0 + slot) * a.P + q;
+                        if (u < ua || u >= ub) slot = -1;
+                    }
+                    run_unit_warp(S, a, slot, q, copy);
                 }
-                run_unit_warp(S, a, slot, q, copy);
+            } else {
+                // a share of the units of many CTAs: q fastest, few lanes share
+                // destinations
+                for (long long u = ua + threadIdx.x; u < ub; u += NT) {
+                    const int t = (int)(u / a.P);
+                    run_unit(S, a, t - tb0, (int)(u - (long long)t * a.P), copy);
+                }
             }
             __syncthreads();
             pr.mark(PR_MAC);
@@ -1119,6 +1132,7 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
     }
 }
 
+template <bool ONE_CTA>
 __device__ void taylor_body(const KArgs &a, unsigned char *smem_raw)
 {
     Smem S = carve(smem_raw, a);
@@ -1154,7 +1168,7 @@ __device__ void taylor_body(const KArgs &a, unsigned char *smem_raw)
         bool ok = true;
         for (int m = 0; m < a.N && ok; m++) {
             const int set = (int)((step * a.N + m) % 3);
-            term_phase(S, a, m, set);
+            term_phase<ONE_CTA>(S, a, m, set);
             ok = grid_barrier(S, a);
             if (!ok) break;
             close_phase(S, a, m, set);
@@ -1177,7 +1191,7 @@ __device__ void taylor_body(const KArgs &a, unsigned char *smem_raw)
 __global__ void __launch_bounds__(NT, 1) taylor_kernel(KArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    taylor_body(a, smem_raw);
+    taylor_body<false>(a, smem_raw);
 }
 
 // one trajectory per CTA: its own argument block, a grid of one
@@ -1187,7 +1201,7 @@ __global__ void __launch_bounds__(NT, 2) taylor_batch_kernel(const KArgs *args)
     __shared__ KArgs a;
     if (threadIdx.x == 0) a = args[blockIdx.x];
     __syncthreads();
-    taylor_body(a, smem_raw);
+    taylor_body<true>(a, smem_raw);
 }
 
 }  // namespace
