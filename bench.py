@@ -150,9 +150,22 @@ def cpu_oracle_rate(wl, nsteps: int):
     threads = O.default_threads()
     p, s = O.params(wl.L), O.state(wl.L, wl.x0)
     t0 = time.perf_counter()
-    O.integrate(wl.L, wl.N, nsteps, p, s, nthreads=threads)
+    fin, _ = O.integrate(wl.L, wl.N, nsteps, p, s, nthreads=threads)
     dt = time.perf_counter() - t0
-    return nsteps / dt, threads, dt
+    return nsteps / dt, threads, dt, fin
+
+
+def gpu_matches_oracle(mpt, wl, nsteps: int, oracle_state, stream) -> bool:
+    """A fresh context (the launch configuration the bench times) run nsteps
+    steps from the workload's initial point: are its signs, exponents and
+    limbs those of the oracle's state after the same steps?"""
+    import numpy as np
+    with mpt.Context(N=wl.N, L=wl.L, tau=wl.tau, stream=stream) as c:
+        c.set_state(*wl.x0)
+        c.integrate(nsteps)
+        s, e, l = c.get_state()
+    return bool(np.array_equal(s, oracle_state.sign) and np.array_equal(e, oracle_state.exp)
+                and np.array_equal(l, oracle_state.limbs))
 
 
 def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
@@ -194,7 +207,7 @@ def reference_arm(args, wl):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (Sec. 5 initial point)",
-        "config": config_of(wl, None),
+        "config": config_of(wl),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": f"{args.steps} full Taylor steps of {wl.name}"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -203,9 +216,11 @@ def reference_arm(args, wl):
     return 0
 
 
-def config_of(wl, ctas):
+def config_of(wl):
+    """The workload, identical in the GPU arm and the reference arm (launch
+    shapes are reported outside it, under "launch")."""
     return {"workload": wl.name, "K_digits": wl.K, "L_limbs": wl.L, "N_order": wl.N,
-            "tau": wl.tau, "x0": list(wl.x0), "ctas": ctas,
+            "tau": wl.tau, "x0": list(wl.x0),
             "l2": "flushed between timed steps (256 MiB memset)",
             "parallelism": "replicas"}
 
@@ -578,7 +593,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (Sec. 5 initial point, exact decimal inputs)",
-        "config": config_of(wl, ctas),
+        "config": config_of(wl),
+        "launch": {"ctas": ctas, "kernel": "pipelined" if ctx.kernel() == 2 else "lock-step"},
         "gpu_launches": args.steps,
         "limb_macs_per_step": work,
         "limb_macs_per_s": achieved * world,
@@ -593,10 +609,15 @@ def main():
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, threads, dt = cpu_oracle_rate(wl, args.cpu_steps)
+        rate, threads, dt, fin = cpu_oracle_rate(wl, args.cpu_steps)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": threads, "kind": "oracle",
                                 "sample": f"{args.cpu_steps} full Taylor steps of {wl.name} "
                                           f"({dt:.1f} s)"}
+        # the oracle's state after those steps against a fresh GPU run of the
+        # same steps, limb for limb
+        line["bit_exact"] = gpu_matches_oracle(mpt, wl, args.cpu_steps, fin, stream.cuda_stream)
+        line["bit_exact_check"] = (f"state after {args.cpu_steps} steps from x0: GPU (fresh "
+                                   f"context, {ctas} CTAs) vs oracle, signs, exponents, limbs")
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -158,7 +158,8 @@ __global__ void unpack_state(int L, int Lp, const uint32_t *stL, const int32_t *
     }
 }
 
-int device_setup(DeviceSetup **out)
+// the current device's set-up (made on first use) and its index
+int device_setup(DeviceSetup **out, int *dev_out)
 {
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -179,6 +180,7 @@ int device_setup(DeviceSetup **out)
         d.ready = true;
     }
     *out = &d;
+    *dev_out = dev;
     return MPT_OK;
 }
 
@@ -226,10 +228,9 @@ extern "C" int mpt_integrate_noalloc(int L, int N, int64_t nsteps, const int32_t
                      "L = %d, N = %d need %zu bytes of scratch; the static scratch array holds %zu",
                      L, N, lay.total, SCRATCH_BYTES);
     DeviceSetup *d = nullptr;
-    int rc = device_setup(&d);
-    if (rc) return rc;
     int dev = 0;
-    cudaGetDevice(&dev);
+    int rc = device_setup(&d, &dev);
+    if (rc) return rc;
     const void *ptrs[6] = {par_signs, par_exps, par_limbs, signs, exps, limbs};
     const char *names[6] = {"par_signs", "par_exps", "par_limbs", "signs", "exps", "limbs"};
     for (int i = 0; i < 6; i++)

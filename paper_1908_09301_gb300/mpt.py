@@ -123,12 +123,32 @@ def parse_number(text: str, L: int):
 def _ptr(a):
     """Pointer of a numpy array or a torch tensor (host or device)."""
     if isinstance(a, np.ndarray):
-        assert a.flags["C_CONTIGUOUS"]
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffers passed to libmpt must be C-contiguous")
         return ctypes.c_void_p(a.ctypes.data)
     if hasattr(a, "data_ptr"):
-        assert a.is_contiguous()
+        if not a.is_contiguous():
+            raise ValueError("tensors passed to libmpt must be contiguous")
         return ctypes.c_void_p(a.data_ptr())
     raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+_I32, _U32 = "torch.int32", "torch.uint32"
+
+
+def _check_noalloc_buffer(t, name: str, numel: int, dtypes):
+    """A contiguous CUDA tensor of exactly ``numel`` elements of a 32-bit
+    dtype from ``dtypes``; ValueError otherwise."""
+    if not hasattr(t, "data_ptr") or not hasattr(t, "is_cuda"):
+        raise ValueError(f"{name} must be a torch tensor, got {type(t).__name__}")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be on a CUDA device, got {t.device}")
+    if str(t.dtype) not in dtypes:
+        raise ValueError(f"{name} must have dtype {' or '.join(dtypes)}, got {t.dtype}")
+    if t.numel() != numel:
+        raise ValueError(f"{name} must have {numel} elements, got {t.numel()}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
 
 
 def _current_stream() -> int:
@@ -290,10 +310,21 @@ def integrate_noalloc(L: int, N: int, nsteps: int, params, state, stream: int | 
     new state: contiguous torch tensors (int32 / int32 / int32 or uint32
     viewed as 32-bit) on the current CUDA device.  Calls that overlap on the
     GPU race on the shared array."""
-    if stream is None:
-        stream = _current_stream()
     ps, pe, pl = params
     ss, se, sl = state
+    # the C ABI cannot see buffer sizes: check them here, before any pointer
+    # crosses it
+    _check_noalloc_buffer(ps, "par_signs", 4, (_I32,))
+    _check_noalloc_buffer(pe, "par_exps", 4, (_I32,))
+    _check_noalloc_buffer(pl, "par_limbs", 4 * int(L), (_I32, _U32))
+    _check_noalloc_buffer(ss, "signs", 3, (_I32,))
+    _check_noalloc_buffer(se, "exps", 3, (_I32,))
+    _check_noalloc_buffer(sl, "limbs", 3 * int(L), (_I32, _U32))
+    devs = {t.device for t in (ps, pe, pl, ss, se, sl)}
+    if len(devs) != 1:
+        raise ValueError(f"all six tensors must be on one CUDA device, got {sorted(map(str, devs))}")
+    if stream is None:
+        stream = _current_stream()
     _check(lib().mpt_integrate_noalloc(int(L), int(N), int(nsteps), _ptr(ps), _ptr(pe), _ptr(pl),
                                        _ptr(ss), _ptr(se), _ptr(sl), ctypes.c_uint64(int(stream))))
 
