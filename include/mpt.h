@@ -129,6 +129,28 @@ int mpt_launch(mpt_ctx *ctx, int64_t nsteps);
 int mpt_wait(mpt_ctx *ctx);
 
 /*
+ * Shortened sums (pipelined kernel; results are identical either way).  Each
+ * bracket of Eq. (3) and each Horner step of Eq. (2) keeps only the top L
+ * limbs of an exact sum, so by default the products of a sum leave out the
+ * columns more than L + 3 + 2 limbs below the sum's largest term.  The
+ * dropped part is below 2^(32 (c0 + 2)) (c0: the lowest column kept); when
+ * the digits of the computed sum between that bound and the result's lowest
+ * kept limb are all zero or all ones (exact cancellation, special data such
+ * as a fixed point), the launch stops and the library runs it again from the
+ * same state with every product in full, so the result is always the exact
+ * one.  mpt_set_exact(ctx, 1) makes every launch full from the start
+ * (0 restores the default).
+ *
+ * mpt_get_counters: the number of such full reruns since the context was
+ * made, and the 8 x 8 limb-product chunks (64 limb multiply-adds each) the
+ * last launch executed in the pipelined kernel (its rerun included; 0 for
+ * the lock-step kernel, which does not count).  Waits for queued work.
+ * (Not part of the paper.)
+ */
+int mpt_set_exact(mpt_ctx *ctx, int on);
+int mpt_get_counters(mpt_ctx *ctx, int64_t *exact_reruns, int64_t *chunks);
+
+/*
  * The Taylor coefficients of the most recent step: 3*(N+1) numbers,
  * component-major (alpha_0..alpha_N, beta_0..beta_N, gamma_0..gamma_N;
  * index 0 is the state the step started from), host memory.

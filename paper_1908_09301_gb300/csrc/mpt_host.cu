@@ -101,6 +101,13 @@ struct mpt_ctx {
     // device, its parameters (tau last) in parL
     int *sysT = nullptr;
     int sysNF = 0, sysNQ = 0, sys_npar = 0;
+    // the last launch (for an exact rerun of a launch whose shortened sums
+    // could not be shown exact) and the counters of mpt_get_counters
+    long long last_nsteps = 0, last_nrec = 0, last_every = 0;
+    bool last_exact = false;
+    bool force_exact = false;      // mpt_set_exact: every launch in full
+    long long exact_reruns = 0;
+    unsigned long long *chunks = nullptr;  // executed limb-product chunks of the last launch
 };
 
 namespace {
@@ -214,7 +221,7 @@ void free_all(mpt_ctx *c)
     c->sysT = nullptr;
     void *ptrs[] = {c->coefL, c->coefE, c->coefF, c->parL, c->parE, c->parF, c->stL, c->stBackL,
                     c->stE, c->stF, c->stBackEF, c->gwin, c->bar, c->status, c->recS, c->recE,
-                    c->recL, c->prof, c->pub, c->done, c->gin, c->imid};
+                    c->recL, c->prof, c->pub, c->done, c->gin, c->imid, c->chunks};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -367,6 +374,7 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
     if (ce == cudaSuccess) ce = dalloc(&c->done, mpt::PIPE_SETS);
     if (ce == cudaSuccess) ce = dalloc(&c->gin, (size_t)mpt::PIPE_SETS * 9 * c->Wcap);
     if (ce == cudaSuccess) ce = dalloc(&c->imid, (size_t)mpt::PIPE_SETS * 4);
+    if (ce == cudaSuccess) ce = dalloc(&c->chunks, 1);
     if (ce != cudaSuccess) {
         free_all(c);
         delete c;
@@ -393,6 +401,7 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
     if (ce == cudaSuccess) ce = cudaMemset(c->coefL, 0, sizeof(uint32_t) * 3 * N1 * c->Lp);
     if (ce == cudaSuccess) ce = cudaMemset(c->coefE, 0, sizeof(int32_t) * 3 * N1);
     if (ce == cudaSuccess) ce = cudaMemset(c->coefF, 0, sizeof(int32_t) * 3 * N1);
+    if (ce == cudaSuccess) ce = cudaMemset(c->chunks, 0, sizeof(unsigned long long));
     if (ce != cudaSuccess) {
         free_all(c);
         delete c;
@@ -572,8 +581,16 @@ int mpt_set_system(mpt_ctx *c, int npar, const char *const *params, int nfixed, 
 namespace {
 
 // queue nsteps steps on the context's stream; records go to the device buffers
-int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_every)
+// exact: every product in full (a rerun, or mpt_set_exact); rerun: keep the
+// chunk counter of the launch being repeated
+int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_every,
+                 bool exact = false, bool rerun = false)
 {
+    exact = exact || c->force_exact;
+    c->last_nsteps = nsteps;
+    c->last_nrec = nrec;
+    c->last_every = record_every;
+    c->last_exact = exact;
     cudaError_t ce = cudaSuccess;
     if (nrec > c->rec_cap) {
         ce = cudaStreamSynchronize(c->st);
@@ -600,6 +617,8 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
         ce = cudaMemcpyAsync(c->stBackEF + 3, c->stF, sizeof(int32_t) * 3, cudaMemcpyDeviceToDevice, c->st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->bar, 0, sizeof(unsigned) * 2, c->st);
     if (ce == cudaSuccess) ce = cudaMemsetAsync(c->gwin, 0, sizeof(long long) * 9 * c->Wcap, c->st);
+    if (ce == cudaSuccess && !rerun)
+        ce = cudaMemsetAsync(c->chunks, 0, sizeof(unsigned long long), c->st);
     if (ce != cudaSuccess) return cuda_fail(ce, "launch preparation");
     mpt::KArgs a{};  // value-initialised: vG = 0 (the launch's own grid)
     a.L = c->L;
@@ -633,6 +652,8 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
     a.sysNQ = c->sysNQ;
     a.npar = c->sysT ? c->sys_npar + 1 : 4;
     a.ptau = c->sysT ? c->sys_npar : 3;
+    a.exact = exact ? 1 : 0;
+    a.chunks = c->chunks;
     if (c->prof) {
         ce = cudaMemsetAsync(c->prof, 0, sizeof(long long) * prof_len(c), c->st);
         if (ce != cudaSuccess) return cuda_fail(ce, "profile reset");
@@ -675,6 +696,14 @@ int wait_steps(mpt_ctx *c)
         cudaMemsetAsync(c->status, 0, sizeof(int), c->st);
         cudaStreamSynchronize(c->st);
         c->have_coefficients = false;
+        if (status == mpt::DEV_INEXACT && !c->last_exact) {
+            // a shortened sum could not be shown exact: the same launch again,
+            // from the same state, with every product in full
+            c->exact_reruns++;
+            int rc = launch_steps(c, c->last_nsteps, c->last_nrec, c->last_every, true, true);
+            if (rc) return rc;
+            return wait_steps(c);
+        }
         if (status == mpt::DEV_ERANGE)
             return fail(MPT_ERANGE, "exponent out of range, or an exact sum spans more than %d limbs",
                         c->Wcap);
@@ -774,6 +803,31 @@ int mpt_wait(mpt_ctx *c)
     if (!c) return fail(MPT_EINVAL, "null context");
     DeviceGuard g(c->dev);
     return wait_steps(c);
+}
+
+int mpt_set_exact(mpt_ctx *c, int on)
+{
+    if (!c) return fail(MPT_EINVAL, "null context");
+    if (on != 0 && on != 1) return fail(MPT_EINVAL, "on = %d is neither 0 nor 1", on);
+    c->force_exact = on != 0;
+    return MPT_OK;
+}
+
+int mpt_get_counters(mpt_ctx *c, int64_t *exact_reruns, int64_t *chunks)
+{
+    if (!c || !exact_reruns || !chunks) return fail(MPT_EINVAL, "null argument");
+    DeviceGuard g(c->dev);
+    if (c->pending) {
+        int rc = wait_steps(c);
+        if (rc) return rc;
+    }
+    unsigned long long h = 0;
+    cudaError_t ce = cudaMemcpyAsync(&h, c->chunks, sizeof h, cudaMemcpyDeviceToHost, c->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(c->st);
+    if (ce != cudaSuccess) return cuda_fail(ce, "counter download");
+    *exact_reruns = c->exact_reruns;
+    *chunks = (int64_t)h;
+    return MPT_OK;
 }
 
 int mpt_step(mpt_ctx *c) { return mpt_integrate(c, 1, 0, nullptr, nullptr, nullptr); }

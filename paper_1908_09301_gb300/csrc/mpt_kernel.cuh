@@ -16,6 +16,20 @@ constexpr int MAX_N = 4096;  // Taylor order (exponent tables live in shared mem
 constexpr int DEV_ERANGE = 1;    // exponent range or accumulator window exceeded
 constexpr int DEV_TIMEOUT = 2;   // a bounded wait expired
 constexpr int DEV_INTERNAL = 3;  // an internal invariant failed (carry did not settle)
+constexpr int DEV_INEXACT = 4;   // a shortened sum could not be shown to give the exact
+                                 // truncated result: the host reruns the launch in full
+
+// Shortened products (pipelined kernel).  Of an exact bracket sum E only the
+// top L + 1 limbs of |E| reach the truncated quotient (division by a small
+// integer, then truncation to L limbs), so each part of a sum computes only
+// the columns at or above  c0 = T - L - 3 - CUT_GUARD  (T: the part's largest
+// term top, e_a + e_b) and drops the rest.  What is dropped is below
+// 2^(32 (c0 + 2)) in magnitude (fewer than 2^31 limb pairs below the cut,
+// each below 2^64), so if the digits of the computed |E'| between limb c0 + 2
+// and the quotient's lowest kept limb are neither all zero nor all ones, E
+// and E' give the same sign, exponent and limbs.  Otherwise the launch ends
+// with DEV_INEXACT and the host runs it again with every column.
+constexpr int CUT_GUARD = 2;
 
 // flag bits of a stored number
 constexpr int F_NEG = 1;
@@ -53,6 +67,9 @@ struct KArgs {
     int npar, ptau;         // parameters in parL, tau's index among them
     int nwin;               // lock-step kernel: copies of the three windows the term
                             // phase adds into (warp w uses copy w mod nwin; 0 = 1)
+    int exact;              // pipelined kernel: 1 = every product in full (no shortened sums)
+    unsigned long long *chunks;  // pipelined kernel: executed 8 x 8 limb-product chunks of
+                                 // the launch are added here (null: not counted)
 };
 
 // limits of a general system

@@ -70,25 +70,31 @@ constexpr int KT = PT - CT;      // compute threads
 // named barriers: FULL + b (a batch in buffer b is ready), EMPTY + b (the
 // compute group is through buffer b), the compute group's, the control group's
 enum { BAR_FULL = 1, BAR_EMPTY = 3, BAR_KT = 5, BAR_CT = 6 };
-// batch descriptor: exit flag, term groups, window parity, group starts and ends
-enum { DS_EXIT = 0, DS_NRUN = 1, DS_PAR = 2, DS_RUN = 4, DS_RUNE = 4 + TB_MAX, DESC_INTS = 4 + 2 * TB_MAX };
+// batch descriptor: exit flag, term groups, window parity, group starts and ends,
+// the window column below which each target's sums are left out (shortened
+// products; INT_MIN / 2: none)
+enum { DS_EXIT = 0, DS_NRUN = 1, DS_PAR = 2, DS_RUN = 4, DS_RUNE = 4 + TB_MAX, DS_CUT = 4 + 2 * TB_MAX,
+       DESC_INTS = 6 + 2 * TB_MAX };
+constexpr int NO_CUT = INT_MIN / 2;
 
 enum { P_SIGMA = 0, P_R = 1, P_B = 2, P_TAU = 3 };
 
 enum {
     MS_STATUS = 0,  // CTA-uniform copy of the status word
-    MS_NRUN = 1,    // (unused)
+    MS_NRUN = 1,    // bracket and Horner close: flags of the buffer digits of a shortened sum
     MS_NEWE = 2,    // [2] exponent and flags of this CTA's newest number
     MS_PSCAL = 8,   // [3][2] sigma, R, b: single non-zero limb index (or -1), value
     MS_WLO = 16,    // [4] long long window bases (ints 16..23)
     MS_WID = 24,    // [2][2] window widths by parity and target (workers); bracket CTAs:
                     // [4] long long workers-window table of the next index (ints 24..31, MS_IMID)
+    MS_CUT = 28,    // [2][2] workers: window column of the cut by parity and target (NO_CUT: none)
     MS_IMID = 24,
     MS_BK = 32,     // [48] bracket setup (ints 32..79)
     MS_RED = 80,    // [RED_LL] long long scratch of the block routines (ints 80..271)
     MS_PARX = 272,  // [4][2] exponent and flags of sigma, R, b, tau (ints 272..279)
     MS_PROF = 336,  // [PROF_SLOTS] long long (ints 336..367)
-    MISC_INTS = 368
+    MS_CHUNKS = 368,  // long long: limb-product chunks this CTA executed
+    MISC_INTS = 372
 };
 
 // bracket setup (ints at MS_BK): lo (long long), width, simple parts, terms, the workers' sums
@@ -102,6 +108,7 @@ enum {
     BK_IWIDTH = 15,
     BK_EINNER = 16, // offset of the edge-term sums (or -1)
     BK_EWIDTH = 17,
+    BK_CUT = 18,    // long long (2 ints): the highest cut of the shortened parts, LLONG_MIN: none
     BK_OINNER = 28, // offset of the outer-pair sums (or -1)
     BK_OWIDTH = 29,
 };
@@ -141,12 +148,15 @@ struct PSmem {
     uint32_t *araw;    // [TB][Lp] first factors as loaded
     uint32_t *cc;      // [2][TB][VW] second factors (cyclic, zero above Lp)
     uint32_t *ash;     // [2][TB][VW] first factors shifted / complemented
+    long long *cstage; // [KT][W+2] digit sums of one chunk each (shortened products)
     // bracket CTAs (same bytes as the workers' part)
     long long *bstage; // [P1 2][W+2] unit digit sums of the few-term products
     uint32_t *vA;      // [NA][VW]
     uint32_t *vC;      // [NC][VW]
     uint32_t *raw;     // [3][Lp] limbs of the current coefficient; [2] also Horner's h
     uint32_t *newc;    // [Lp] this CTA's newest number
+    long long *bcstage;  // [PT][W+2] digit sums of one chunk each (shortened products)
+    Divisor *divT;       // [N+1] bracket CTAs: the invariant divisors of 1..N+1 (entry m: m+1)
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -184,6 +194,8 @@ __host__ __device__ inline size_t pipe_layout(const Geo &G, int N, int TB, PSmem
     if (S) S->cc = (uint32_t *)p;
     p = take(sizeof(uint32_t) * 2 * (size_t)TB * G.VW);
     if (S) S->ash = (uint32_t *)p;
+    p = take(sizeof(long long) * (size_t)KT * (W + 2));
+    if (S) S->cstage = (long long *)p;
     const size_t worker_end = o;
     o = u0;
     p = take(sizeof(long long) * (size_t)G.P1 * 2 * (W + 2));
@@ -196,6 +208,10 @@ __host__ __device__ inline size_t pipe_layout(const Geo &G, int N, int TB, PSmem
     if (S) S->raw = (uint32_t *)p;
     p = take(sizeof(uint32_t) * (size_t)G.Lp);
     if (S) S->newc = (uint32_t *)p;
+    p = take(sizeof(long long) * (size_t)PT * (W + 2));
+    if (S) S->bcstage = (long long *)p;
+    p = take(sizeof(Divisor) * (size_t)(N + 1));
+    if (S) S->divT = (Divisor *)p;
     if (worker_end > o) o = worker_end;
     return o;
 }
@@ -570,6 +586,184 @@ __device__ void small_products(const Geo &G, int RS, const Grp &gr, const uint32
     }
 }
 
+// ------------------------------------------------------------------ shortened products
+
+// largest q with q (q + 1) / 2 <= x (x < 2^24)
+__device__ __forceinline__ int tri_root(int x)
+{
+    int q = (int)((sqrtf(8.0f * (float)x + 1.0f) - 1.0f) * 0.5f);
+    while ((q + 1) * (q + 2) / 2 <= x) q++;
+    while (q > 0 && q * (q + 1) / 2 > x) q--;
+    return q;
+}
+
+// Window-relative column below which a part of a bracket (products only,
+// window [lo, hi) with hi = its largest term top + 2Lp + 2 - 2L) leaves its
+// columns out: c0 = T - L - 3 - CUT_GUARD with T the largest term top
+// e_a + e_b; NO_CUT when the launch is exact or no block-0 unit of the
+// part's lowest term would fall below c0.
+__device__ __forceinline__ int part_cut(const KArgs &a, const Geo &G, long long lo, long long hi)
+{
+    if (a.exact || hi <= lo) return NO_CUT;
+    const long long T = hi - 2LL * G.Lp - 2 + 2LL * G.L;
+    const long long r = T - G.L - 3 - CUT_GUARD - lo;
+    return r < W ? NO_CUT : (int)r;
+}
+
+// The column sums, for product columns >= kcut only, of the n terms in slots
+// [s0, s0+n) (the same product layout as small_products), added into
+// win[coff + c]; columns below kcut are left out altogether (see CUT_GUARD).
+// Block 0 of unit q holds columns qW..qW+W-1 and is needed iff
+// q >= Q0 = floor(kcut / W); block 1 of unit q (columns M + qW ..) iff
+// q >= Q1 = floor((kcut - M) / W).  The needed chunks form a list -- block-0
+// units q = Q0..P (chunks j = 0..q), then block-1 units q = P-1 down to Q1
+// (chunks j = q+1..P) -- and in each round thread t of the group takes chunk
+// t of the round's share of it, for all n terms, so every thread has the
+// same work.  Each thread stores its chunk's W+2 digit sums in its own row
+// of cstage ([group threads][W+2]); one thread per (unit, block, digit) adds
+// up the rows of its unit's chunks into stage (the small_products layout,
+// [P+1][2][W+2]); after the last round one thread per column adds the
+// digits of the two units that reach the column (and the complement
+// corrections of negative terms) into the window.  Every thread of group gr
+// calls this; starts and ends with a barrier of the group.  Returns the
+// chunks of one term.
+__device__ int cut_products(const Geo &G, const Grp &gr, const uint32_t *Abase, const uint32_t *Cbase,
+                            int s0, int n, const int *tinfo, bool neg_all, long long *stage,
+                            long long *cstage, long long *win, int coff, int kcut)
+{
+    constexpr int ND = W + 2;
+    const int P = G.P;
+    // unit q's columns of block b are below kcut iff qW + W - 1 < kcut - bM
+    const int Q0 = min(kcut > 0 ? kcut / W : 0, P + 1);
+    const int Q1 = min(kcut > G.M ? (kcut - G.M) / W : 0, P);
+    const int T0 = (P + 1) * (P + 2) / 2 - Q0 * (Q0 + 1) / 2;  // block-0 chunks
+    const int n1 = P - Q1;                                       // block-1 units
+    const int C = T0 + n1 * (n1 + 1) / 2;
+    const int nseg0 = P + 1 - Q0, nseg = nseg0 + n1;            // (unit, block) segments
+    const int tid = gr.t;
+    const unsigned slot = G.VW * 4;
+    const unsigned sAb = smem_addr(Abase) + s0 * slot, sCb = smem_addr(Cbase) + s0 * slot;
+    grp_sync(gr);
+    for (int r0 = 0; r0 < C; r0 += gr.n) {
+        const int r1 = min(C, r0 + gr.n);
+        const int c = r0 + tid;
+        if (c < r1) {
+            uint32_t a0[W], a1[W], a2[W];
+#pragma unroll
+            for (int k = 0; k < W; k++) a0[k] = a1[k] = a2[k] = 0u;
+            int q, j;
+            if (c < T0) {
+                const int x = c + Q0 * (Q0 + 1) / 2;
+                q = tri_root(x);
+                j = x - q * (q + 1) / 2;
+            } else {
+                const int x = c - T0;
+                const int qq = tri_root(x);
+                q = P - 1 - qq;
+                j = q + 1 + (x - qq * (qq + 1) / 2);
+            }
+            int gc0 = q - j;
+            if (gc0 < 0) gc0 += G.P1;
+            const int gc1 = gc0 == 0 ? P : gc0 - 1;
+            unsigned sA = sAb, sC = sCb;
+            for (int t = 0; t < n; t++) {
+                chunk_mac(sA, sC, j, gc0, gc1, a0, a1, a2);
+                sA += slot;
+                sC += slot;
+            }
+            long long *row = cstage + (size_t)tid * ND;
+#pragma unroll
+            for (int t = 0; t < ND; t++) row[t] = col_digit(a0, a1, a2, t);
+        }
+        grp_sync(gr);
+        // one thread per (segment, digit): the rows of the segment's chunks in this round
+        for (int e = tid; e < nseg * ND; e += gr.n) {
+            const int sg = e / ND, t = e - sg * ND;
+            int q, blk, st, len;
+            if (sg < nseg0) {
+                q = Q0 + sg;
+                blk = 0;
+                st = q * (q + 1) / 2 - Q0 * (Q0 + 1) / 2;
+                len = q + 1;
+            } else {
+                q = Q1 + (sg - nseg0);
+                blk = 1;
+                const int qq = P - 1 - q;
+                st = T0 + qq * (qq + 1) / 2;
+                len = qq + 1;
+            }
+            const int ka = max(st, r0) - r0, kb = min(st + len, r1) - r0;
+            long long v0 = 0, v1 = 0, v2 = 0, v3 = 0;
+            int k = ka;
+            for (; k + 4 <= kb; k += 4) {
+                v0 += cstage[(k + 0) * ND + t];
+                v1 += cstage[(k + 1) * ND + t];
+                v2 += cstage[(k + 2) * ND + t];
+                v3 += cstage[(k + 3) * ND + t];
+            }
+            for (; k < kb; k++) v0 += cstage[k * ND + t];
+            long long &d = stage[(q * 2 + blk) * ND + t];
+            d = (r0 == 0 ? 0 : d) + (v0 + v1) + (v2 + v3);
+        }
+        grp_sync(gr);
+    }
+    // stage holds the digits of the needed (unit, block)s only
+    for (int cc = max(kcut, 0) + tid; cc < G.GW; cc += gr.n) {
+        long long sum = 0;
+        if (cc < G.M + 2) {
+            const int u = cc / W;
+            if (u <= P && u >= Q0) sum += stage[(u * 2) * ND + cc - u * W];
+            if (u >= 1 && u - 1 >= Q0 && cc - (u - 1) * W < ND) sum += stage[((u - 1) * 2) * ND + cc - (u - 1) * W];
+        }
+        const int c1 = cc - G.M;
+        if (c1 >= 0) {
+            const int u = c1 / W;
+            if (u <= P - 1 && u >= Q1) sum += stage[(u * 2 + 1) * ND + c1 - u * W];
+            if (u >= 1 && u - 1 <= P - 1 && u - 1 >= Q1 && c1 - (u - 1) * W < ND)
+                sum += stage[((u - 1) * 2 + 1) * ND + c1 - (u - 1) * W];
+        }
+        if (tinfo) {
+            for (int sl = s0; sl < s0 + n; sl++) {
+                const int *ti = tinfo + sl * TI;
+                if (!ti[1]) continue;
+                const int y = cc - ti[2];
+                const uint32_t *Cs = Cbase + (size_t)sl * G.VW;
+                if (y >= 0 && y < G.Lp) sum += Cs[gpos(y)];
+                else if (y >= G.Lp && y < 2 * G.Lp) sum += (uint32_t)~Cs[gpos(y - G.Lp)];
+                if (y == G.Lp) sum += 1;
+                if (y == 2 * G.Lp) sum -= 1;
+            }
+        }
+        if (sum) win[coff + cc] += neg_all ? -sum : sum;
+    }
+    grp_sync(gr);
+    return C;
+}
+
+// The products of the n terms in slots [s0, s0+n): shortened at product
+// column kcut when kcut leaves out at least one block-0 unit (and the launch
+// is not exact), else in full (RS lanes per unit); the executed chunks (per
+// term) are added to *chunks (thread 0 of the group, when given).
+__device__ void products(const Geo &G, int RS, const Grp &gr, const uint32_t *Abase,
+                         const uint32_t *Cbase, int s0, int n, const int *tinfo, bool neg_all,
+                         long long *stage, long long *cstage, long long *win, int coff, int kcut,
+                         long long *chunks)
+{
+    int c;
+    // shortened only where the full product takes more than one chunk per
+    // thread of the group (below that the full walk's latency is no longer)
+    if (kcut >= W && G.P1 * G.P1 > gr.n) {
+        c = cut_products(G, gr, Abase, Cbase, s0, n, tinfo, neg_all, stage, cstage, win, coff, kcut);
+    } else {
+        if (n == 1 && gr.bar == 0)
+            single_product(G, Abase, Cbase, s0, tinfo, neg_all, stage, win, coff);
+        else
+            small_products(G, RS, gr, Abase, Cbase, s0, n, tinfo, neg_all, stage, win, coff);
+        c = G.P1 * G.P1;
+    }
+    if (chunks && gr.t == 0) *chunks += (long long)c * n;
+}
+
 // ------------------------------------------------------------------ workers
 
 // Term t of index m for a CTA of role `role`.  Role 0, the workers: the
@@ -701,6 +895,8 @@ __device__ void ctl_prepare(PSmem &S, const Geo &G, int TB, int buf, int role, i
             desc[DS_EXIT] = 0;
             desc[DS_NRUN] = __popc(Sm);
             desc[DS_PAR] = par;
+            desc[DS_CUT] = S.misc[MS_CUT + 2 * par];
+            desc[DS_CUT + 1] = S.misc[MS_CUT + 2 * par + 1];
         }
     }
     named_sync(BAR_CT, CT);
@@ -881,6 +1077,8 @@ __device__ void worker_control(PSmem &S, const KArgs &a, const PArgs &pa, const 
                     }
                     ll_at(S.misc, MS_WLO + 2 * tg) = hi[tg] > lo[tg] ? lo[tg] : 0;
                     S.misc[MS_WID + 2 * par + tg] = width;
+                    S.misc[MS_CUT + 2 * par + tg] =
+                        width > 0 ? part_cut(a, G, lo[tg], hi[tg]) : NO_CUT;
                 }
             }
             named_sync(BAR_CT, CT);
@@ -927,6 +1125,7 @@ __device__ void worker_compute(PSmem &S, const Geo &G, const PArgs &pa, const KA
 {
     const Grp gr{(int)threadIdx.x, KT, BAR_KT};
     const int TB = pa.tb;
+    long long *chunks = a.chunks ? &ll_at(S.misc, MS_CHUNKS) : nullptr;
     Prof pr(a, true, S.misc, 0);
     for (long long k = 0;; k++) {
         const int b = (int)(k & 1);
@@ -943,9 +1142,10 @@ __device__ void worker_compute(PSmem &S, const Geo &G, const PArgs &pa, const KA
             const int rs = desc[DS_RUN + rr], re = desc[DS_RUNE + rr];
             const int *ti = tinfo + rs * TI;
             if (pr.p) pr.p[PR_X6] += re - rs;
-            small_products(G, G.RSW, gr, S.ash + (size_t)b * TB * G.VW, S.cc + (size_t)b * TB * G.VW,
-                           rs, re - rs, tinfo, false, S.stage, S.win + (size_t)(2 * par + ti[0]) * G.WW,
-                           ti[3] * W);
+            const int cw = desc[DS_CUT + ti[0]];
+            products(G, G.RSW, gr, S.ash + (size_t)b * TB * G.VW, S.cc + (size_t)b * TB * G.VW, rs,
+                     re - rs, tinfo, false, S.stage, S.cstage, S.win + (size_t)(2 * par + ti[0]) * G.WW,
+                     ti[3] * W, cw == NO_CUT ? 0 : cw - ti[3] * W, chunks);
         }
         named_arrive(BAR_EMPTY + b, PT);
         pr.mark(PR_MAC);
@@ -1073,6 +1273,7 @@ __device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &
 {
     const int e = blockIdx.x - (NCL + NOUT);
     const int N1 = G.N1, Lp = G.Lp;
+    long long *chunks = a.chunks ? &ll_at(S.misc, MS_CHUNKS) : nullptr;
     for (int i = threadIdx.x; i < NA * G.VW; i += PT) S.vA[i] = 0u;
     for (int i = threadIdx.x; i < NC * G.VW; i += PT) S.vC[i] = 0u;
     for (int i = threadIdx.x; i < 2 * G.WW; i += PT) S.win[i] = 0;
@@ -1118,7 +1319,7 @@ __device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &
                     for (int k = 0; k < 2; k++) {
                         const EdgeTerm T = EDGE_T[e][k];
                         long long lp, lo, hi;
-                        int neg = 0, on = 0, d = 0, width = 0;
+                        int neg = 0, on = 0, d = 0, width = 0, cut = NO_CUT;
                         if (T.tgt >= 0 && edge_term(S, a, G, T, m, lp, neg)) {
                             edge_window(S, a, G, T.tgt, m, lo, hi);
                             if (hi - lo > a.Wcap) {
@@ -1127,6 +1328,7 @@ __device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &
                                 on = 1;
                                 d = (int)(lp - lo);
                                 width = (int)(hi - lo);
+                                cut = part_cut(a, G, lo, hi);
                             }
                         }
                         int *ti = S.tinfo + k * TI;
@@ -1135,6 +1337,8 @@ __device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &
                         ti[2] = d & 7;
                         ti[3] = d >> 3;
                         ti[4] = width;
+                        // product column of the cut (0: in full)
+                        ti[5] = cut == NO_CUT ? 0 : cut - (d >> 3) * W;
                     }
                 }
             }
@@ -1170,8 +1374,8 @@ __device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &
             for (int k = 0; k < 2; k++) {
                 const int *ti = S.tinfo + k * TI;
                 if (!ti[0]) continue;
-                single_product(G, S.vA, S.vC, k, S.tinfo, false, S.bstage, S.win + (size_t)k * G.WW,
-                               ti[3] * W);
+                products(G, G.RS, whole_cta(), S.vA, S.vC, k, 1, S.tinfo, false, S.bstage, S.bcstage,
+                         S.win + (size_t)k * G.WW, ti[3] * W, ti[5], chunks);
             }
             pr.mark(PR_MAC);
             for (int k = 0; k < 2; k++) {
@@ -1305,6 +1509,16 @@ __device__ bool bracket_setup(PSmem &S, const KArgs &a, const PArgs &pa, const G
     const bool outer = c > 0 && m >= 2 && ohi > olo;
     bk[BK_OINNER] = outer ? (int)(olo - lo) : -1;
     bk[BK_OWIDTH] = outer ? (int)(ohi - olo) : 0;
+    // the cuts the other CTAs take in these parts (the same windows, the same rule)
+    long long cut = LLONG_MIN;
+    const bool present[3] = {edge, inner, outer};
+    const long long plo[3] = {elo, ilo, olo}, phi[3] = {ehi, ihi, ohi};
+    for (int k = 0; k < 3; k++) {
+        if (!present[k]) continue;
+        const int r = part_cut(a, G, plo[k], phi[k]);
+        if (r != NO_CUT) cut = max(cut, plo[k] + r);
+    }
+    ((long long *)(bk + BK_CUT))[0] = cut;
     return true;
 }
 
@@ -1336,19 +1550,38 @@ __device__ void add_simple_parts(const PSmem &S, const Geo &G, long long *win, i
 
 // normalise win[0..width) (base lo) and divide by dv.d into L limbs of out;
 // zero the window.  Exponent and flags via e, f; false on a range error
-// (status set).
+// (status set).  `cut` (absolute limb position; LLONG_MIN: none) is the
+// highest column below which some part of the sum was left out: the digits
+// from cut + 2 up to the quotient's lowest kept limb must then be neither all
+// zero nor all ones, or the sum may differ from the exact one in what the
+// truncated quotient keeps, and the launch ends with DEV_INEXACT.
 __device__ bool close_bracket(PSmem &S, const KArgs &a, const Geo &G, long long *win, int width,
                               long long lo, const Divisor &dv, uint32_t *out, int &e, int &f,
-                              uint32_t *out2 = nullptr)
+                              uint32_t *out2 = nullptr, long long cut = LLONG_MIN)
 {
     e = 0;
     f = 0;
     bool ok = true;
     int top = -1, neg = 0;
+    if (threadIdx.x == 0) S.misc[MS_NRUN] = 0;  // the buffer-digit flags (ordered by the barriers below)
     if (width > 0) {
         const Norm nr = block_normalize(win, S.dig, width, (long long *)(S.misc + MS_RED), a.status);
         top = nr.top;
         neg = nr.neg;
+    }
+    if (cut != LLONG_MIN && top >= 0) {
+        // the buffer digits [cut + 2, s), s = eq - L the quotient's lowest kept
+        // limb (eq as block_divide takes it): bit 0 = one is non-zero, bit 1 =
+        // one is not all ones; gathered while the division runs
+        const long long T = lo + top + 1;
+        const long long eq = (S.dig[top] >= dv.d) ? T : T - 1;
+        const long long b0 = max(cut + 2 - lo, 0LL), b1 = eq - G.L - lo;
+        int bits = 0;
+        for (long long x = b0 + threadIdx.x; x < b1; x += PT) {
+            const uint32_t v = S.dig[x];
+            bits |= (v != 0u ? 1 : 0) | (v != 0xffffffffu ? 2 : 0);
+        }
+        if (bits) atomicOr(&S.misc[MS_NRUN], bits);
     }
     if (top >= 0) {
         const long long eq = block_divide(S.dig, top, lo, dv, G.L, out, S.misc + MS_RED, out2);
@@ -1364,6 +1597,12 @@ __device__ bool close_bracket(PSmem &S, const KArgs &a, const Geo &G, long long 
         for (int x = threadIdx.x; x < G.L; x += PT) out[x] = 0u;
         __syncthreads();
     }
+    if (cut != LLONG_MIN && S.misc[MS_NRUN] != 3) {
+        // the left-out part could reach the kept limbs: the launch is rerun in full
+        __syncthreads();
+        if (threadIdx.x == 0) atomicCAS(a.status, 0, DEV_INEXACT);
+        return false;
+    }
     return ok;
 }
 
@@ -1374,6 +1613,7 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
                                  Prof &pr)
 {
     const int N1 = G.N1, Lp = G.Lp, L = G.L;
+    long long *chunks = a.chunks ? &ll_at(S.misc, MS_CHUNKS) : nullptr;
     uint32_t *hA = S.vA;         // h as first factor (slot 0)
     const uint32_t *tauC = S.vC; // tau (slot 0)
     uint32_t *hp = S.raw + 2 * (size_t)Lp;     // h, plain limbs
@@ -1423,9 +1663,21 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
             }
             width = (int)(hi - lo);
         }
+        // the product's columns below c0 = T - L - 3 - CUT_GUARD (T: the larger
+        // top of tau h and c_i) are left out when that drops a block-0 unit
+        long long cut = LLONG_MIN;
+        int kcut = 0;
+        if (prod && !a.exact) {
+            const long long T = max((long long)tauE + he, lone ? (long long)ce : LLONG_MIN);
+            const long long c0 = T - L - 3 - CUT_GUARD;
+            if (c0 - lpp >= W) {
+                cut = c0;
+                kcut = (int)(c0 - lpp);
+            }
+        }
         if (prod)
-            single_product(G, hA, tauC, 0, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.bstage, win,
-                           (int)(lpp - lo));
+            products(G, G.RS, whole_cta(), hA, tauC, 0, 1, nullptr, ((hf ^ tauF) & F_NEG) != 0, S.bstage,
+                     S.bcstage, win, (int)(lpp - lo), kcut, chunks);
         pr.mark(PR_HMAC);
         if (lone) {
             const int offa = (int)(lpa - lo);
@@ -1439,7 +1691,7 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
         int e, f;
         // h for the next step, plain (hp) and as the product's first factor
         // (hA; when h is zero, the next step has no product)
-        if (!close_bracket(S, a, G, win, width, lo, one, hp, e, f, hA)) {
+        if (!close_bracket(S, a, G, win, width, lo, one, hp, e, f, hA, cut)) {
             ok = false;
             break;
         }
@@ -1481,6 +1733,7 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
     for (int e = threadIdx.x; e < 3 * Lp; e += PT) S.raw[e] = 0u;
     for (int e = threadIdx.x; e < Lp; e += PT) S.newc[e] = 0u;
     for (int e = threadIdx.x; e < 2 * G.WW; e += PT) S.win[e] = 0;
+    for (int m = threadIdx.x; m <= a.N; m += PT) S.divT[m] = make_divisor((uint32_t)(m + 1));
     scan_one_limb_params(S, a, G);
     // tau (Horner's fixed factor)
     to_slot(S.vC, a.parL + (size_t)P_TAU * Lp, Lp);
@@ -1510,9 +1763,10 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             Prof pr(a, prof_on, S.misc);
             const long long g = step * a.N + m;
             const int set = (int)(g % PIPE_SETS);
-            const Divisor dvm = make_divisor((uint32_t)(m + 1));
+            const Divisor dvm = S.divT[m];
             if (threadIdx.x == 0) S.misc[MS_STATUS] = bracket_setup(S, a, pa, G, c, m, set) ? 0 : 1;
             __syncthreads();
+            pr.mark(PR_X1);
             if (S.misc[MS_STATUS]) return;
             const int *bk = S.misc + MS_BK;
             const long long lo = ((const long long *)(bk + BK_LO))[0];
@@ -1563,7 +1817,8 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             }
             __syncthreads();
             int e, f;
-            const bool ok = close_bracket(S, a, G, win, width, lo, dvm, S.newc, e, f);
+            const bool ok = close_bracket(S, a, G, win, width, lo, dvm, S.newc, e, f, nullptr,
+                                          ((const long long *)(bk + BK_CUT))[0]);
             pr.mark(PR_CLOSE);
             if (!ok) return;
             if (threadIdx.x == 0) {
@@ -1641,7 +1896,10 @@ __global__ void __launch_bounds__(PT, 1) pipe_kernel(KArgs a, PArgs pa)
     pipe_layout(G, a.N, pa.tb, &S, smem_raw);
     const bool prof_cta = true;
     if (threadIdx.x < PROF_SLOTS) ((long long *)(S.misc + MS_PROF))[threadIdx.x] = 0;
-    if (threadIdx.x == 0) S.misc[MS_STATUS] = 0;
+    if (threadIdx.x == 0) {
+        S.misc[MS_STATUS] = 0;
+        ll_at(S.misc, MS_CHUNKS) = 0;
+    }
     __syncthreads();
     Prof tot(a, prof_cta, S.misc);
     if (blockIdx.x < (unsigned)NCL)
@@ -1652,6 +1910,8 @@ __global__ void __launch_bounds__(PT, 1) pipe_kernel(KArgs a, PArgs pa)
         edge_loop(S, a, pa, G);
     __syncthreads();
     tot.mark(PR_TOTAL);
+    if (a.chunks && threadIdx.x == 0)
+        atomicAdd(a.chunks, (unsigned long long)ll_at(S.misc, MS_CHUNKS));
     if (a.prof && threadIdx.x == 0) {
         // rows 0 and 1: the beta' bracket CTA and the last worker; then one row per CTA
         const long long *src = (const long long *)(S.misc + MS_PROF);

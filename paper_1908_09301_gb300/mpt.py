@@ -49,6 +49,8 @@ SIGNATURES = {
     "mpt_set_wait_limit": (ctypes.c_int, [vp, ctypes.c_int64]),
     "mpt_get_profile": (ctypes.c_int, [vp, vp, ctypes.c_int]),
     "mpt_wait": (ctypes.c_int, [vp]),
+    "mpt_set_exact": (ctypes.c_int, [vp, ctypes.c_int]),
+    "mpt_get_counters": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "mpt_set_launch": (ctypes.c_int, [vp, ctypes.c_int]),
     "mpt_get_launch": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
     "mpt_set_kernel": (ctypes.c_int, [vp, ctypes.c_int]),
@@ -247,6 +249,17 @@ class Context:
     def wait(self):
         """Finish queued steps and report device-side errors (``mpt_wait``)."""
         _check(lib().mpt_wait(self._h))
+
+    def set_exact(self, on: bool = True):
+        """Every launch with all products in full (``mpt_set_exact``)."""
+        _check(lib().mpt_set_exact(self._h, int(bool(on))))
+
+    def counters(self):
+        """(full reruns so far, limb-product chunks of the last launch)
+        (``mpt_get_counters``)."""
+        r, c = ctypes.c_int64(), ctypes.c_int64()
+        _check(lib().mpt_get_counters(self._h, ctypes.byref(r), ctypes.byref(c)))
+        return r.value, c.value
 
     PROFILE_SLOTS = ["place", "stage", "mac", "flush", "barrier", "close", "horner", "horner_mac",
                      "horner_close", "total", "x1", "x2", "x3", "x4", "x5", "x6"]
