@@ -64,3 +64,36 @@ def integrate(L: int, N: int, nsteps: int, par, st):
     for _ in range(nsteps):
         s = step(L, N, par, s)
     return s
+
+
+def adjoint_step(L: int, N: int, par, coef, gbar, thbar):
+    """The reverse sweep of one step with exact fractions (the oracle's
+    adjoint of Eq. (3) and Eq. (2), see ``mpt_oracle.c``): coef = (alpha,
+    beta, gamma) lists of N+1 Fractions, gbar / thbar three Fractions each;
+    returns (the adjoint of the step's starting state, the updated parameter
+    adjoints)."""
+    sigma, R, b, tau = par
+    al, be, ga = coef
+    P = [Fraction(1)]
+    for _ in range(N):
+        P.append(T(P[-1] * tau, L))
+    Ex, Ey, Ez = [None] * N, [None] * N, [None] * N
+    out = None
+    for j in range(N, -1, -1):
+        sx, sy, sz = gbar[0] * P[j], gbar[1] * P[j], gbar[2] * P[j]
+        if j <= N - 1:
+            sx += -sigma * Ex[j] + R * Ey[j]
+            sy += sigma * Ex[j] - Ey[j]
+            sz += -b * Ez[j]
+        for i in range(j, N):
+            sx += -Ey[i] * ga[i - j] + Ez[i] * be[i - j]
+            sy += Ez[i] * al[i - j]
+            sz += -Ey[i] * al[i - j]
+        if j >= 1:
+            Ex[j - 1], Ey[j - 1], Ez[j - 1] = T(sx / j, L), T(sy / j, L), T(sz / j, L)
+        else:
+            out = (T(sx, L), T(sy, L), T(sz, L))
+    ts = thbar[0] + sum((Ex[i] * (be[i] - al[i]) for i in range(N)), Fraction(0))
+    tr = thbar[1] + sum((Ey[i] * al[i] for i in range(N)), Fraction(0))
+    tb = thbar[2] - sum((Ez[i] * ga[i] for i in range(N)), Fraction(0))
+    return out, (T(ts, L), T(tr, L), T(tb, L))

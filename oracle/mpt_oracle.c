@@ -32,9 +32,26 @@
  * order, so the serial path and the OpenMP path (Sec. 4's per-thread
  * containers sum[2*tid], sum[2*tid+1] folded by the master) agree bit for bit.
  *
+ * The adjoint (reverse sweep, orc_adjoint_step / orc_backward): the derivative
+ * of the exact-arithmetic order-N step map -- Eq. (3) and Eq. (2) read as
+ * exact operations -- with respect to the state and (sigma, R, b), evaluated
+ * at the stored coefficients.  With E_i the bracket of Eq. (3) that gives
+ * coefficient i+1 and Ebar_i = d(out)/d(E_i), going j = N down to 0:
+ *   S_x(j) = gbar_x P_j - sigma Ebar_x,j + R Ebar_y,j
+ *            + sum_{i=j}^{N-1} ( -Ebar_y,i gamma_{i-j} + Ebar_z,i beta_{i-j} )
+ *   S_y(j) = gbar_y P_j + sigma Ebar_x,j - Ebar_y,j + sum_{i=j}^{N-1} Ebar_z,i alpha_{i-j}
+ *   S_z(j) = gbar_z P_j - b Ebar_z,j - sum_{i=j}^{N-1} Ebar_y,i alpha_{i-j}
+ * (the terms with Ebar_j are absent at j = N); Ebar_{j-1} = trunc_L(S(j)/j)
+ * for j >= 1 and the state's adjoint is trunc_L(S(0)).  P_0 = 1,
+ * P_j = trunc_L(P_{j-1} tau) (d(out)/d(c_j) = tau^j by Eq. (2)).  Every S is
+ * formed exactly from stored numbers and truncated once.  Per step the
+ * parameter adjoints become trunc_L(old + sum_i Ebar_x,i (beta_i - alpha_i)),
+ * trunc_L(old + sum_i Ebar_y,i alpha_i), trunc_L(old - sum_i Ebar_z,i gamma_i).
+ *
  * Parity status: pinned (closed-form coefficients, exact-fraction brute force,
  * closed-form special case, exact fixed point, symmetry, (K,N) vs larger (K,N),
- * double-precision RK4) -- see the tests.
+ * double-precision RK4; the adjoint against exact dual-number derivatives of
+ * the order-N map and against central differences of runs) -- see the tests.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -556,6 +573,232 @@ int orc_fma_trunc(int L, const int32_t *s, const int32_t *e, const uint32_t *l,
     dy_free(&c);
     dy_free(&sum);
     return g_err;
+}
+
+/* ----------------------------------------------------------------------- */
+/* The adjoint of the step (see the header). */
+
+/* P_0 = 1, P_j = trunc_L(P_{j-1} tau), j = 1..N: d(x_{n+1})/d(alpha_j) = tau^j
+ * by Eq. (2). */
+static void tau_powers(int L, int N, const mpnum *tau, mpnum *P)
+{
+    mp_set_zero(&P[0], L);
+    P[0].limb[L - 1] = 1u; /* 1 = 1 * 2^(32 (exp - 1)) with exp = 1 */
+    P[0].exp = 1;
+    for (int j = 1; j <= N && !g_err; j++) {
+        dyadic p = dy_mul(&P[j - 1], tau, L);
+        dy_trunc(&p, L, &P[j]);
+        dy_free(&p);
+    }
+}
+
+/* s += sg * a * b */
+static void acc_prod(dyadic *s, int sg, const mpnum *a, const mpnum *b, int L)
+{
+    dyadic p = dy_mul(a, b, L);
+    if (sg < 0) p = dy_neg(p);
+    dy_accumulate(s, &p);
+    dy_free(&p);
+}
+
+/* s += sg * a */
+static void acc_lone(dyadic *s, int sg, const mpnum *a, int L)
+{
+    dyadic p = dy_from_mp(a, L);
+    if (sg < 0) p = dy_neg(p);
+    dy_accumulate(s, &p);
+    dy_free(&p);
+}
+
+/* One step backwards.  al/be/ga: the step's coefficients (N+1 each); P: the
+ * powers of tau; gb[3]: the adjoint of the step's result, replaced by the
+ * adjoint of the step's starting state; th[3]: the running adjoints of
+ * sigma, R, b; Ea/Eb/Eg: N numbers each of scratch (Ebar_x, Ebar_y, Ebar_z). */
+static void adjoint_step(int L, int N, const mpnum par[4], const mpnum *al, const mpnum *be,
+                         const mpnum *ga, const mpnum *P, mpnum *gb, mpnum *th, mpnum *Ea,
+                         mpnum *Eb, mpnum *Eg)
+{
+    const mpnum *sigma = &par[0], *R = &par[1], *b = &par[2];
+    for (int j = N; j >= 0 && !g_err; j--) {
+        dyadic Sx = dy_zero(), Sy = dy_zero(), Sz = dy_zero();
+        /* Eq. (2): x_{n+1} = sum_j alpha_j tau^j */
+        acc_prod(&Sx, 1, &gb[0], &P[j], L);
+        acc_prod(&Sy, 1, &gb[1], &P[j], L);
+        acc_prod(&Sz, 1, &gb[2], &P[j], L);
+        if (j <= N - 1) {
+            /* the linear terms of the brackets E_j of Eq. (3) */
+            acc_prod(&Sx, -1, sigma, &Ea[j], L);
+            acc_prod(&Sx, 1, R, &Eb[j], L);
+            acc_prod(&Sy, 1, sigma, &Ea[j], L);
+            acc_lone(&Sy, -1, &Eb[j], L);
+            acc_prod(&Sz, -1, b, &Eg[j], L);
+        }
+        /* the Cauchy sums of the brackets E_i, i >= j, through their factor of index j */
+        for (int i = j; i <= N - 1; i++) {
+            acc_prod(&Sx, -1, &Eb[i], &ga[i - j], L);
+            acc_prod(&Sx, 1, &Eg[i], &be[i - j], L);
+            acc_prod(&Sy, 1, &Eg[i], &al[i - j], L);
+            acc_prod(&Sz, -1, &Eb[i], &al[i - j], L);
+        }
+        if (j >= 1) {
+            /* alpha_j = E_{j-1} / j */
+            dy_div_trunc(&Sx, (uint32_t)j, L, &Ea[j - 1]);
+            dy_div_trunc(&Sy, (uint32_t)j, L, &Eb[j - 1]);
+            dy_div_trunc(&Sz, (uint32_t)j, L, &Eg[j - 1]);
+        } else {
+            /* alpha_0 = x_n: the state's adjoint */
+            dy_trunc(&Sx, L, &gb[0]);
+            dy_trunc(&Sy, L, &gb[1]);
+            dy_trunc(&Sz, L, &gb[2]);
+        }
+        dy_free(&Sx);
+        dy_free(&Sy);
+        dy_free(&Sz);
+    }
+    /* dE_x,i/dsigma = beta_i - alpha_i, dE_y,i/dR = alpha_i, dE_z,i/db = -gamma_i */
+    dyadic ts = dy_from_mp(&th[0], L), tr = dy_from_mp(&th[1], L), tb = dy_from_mp(&th[2], L);
+    for (int i = 0; i <= N - 1; i++) {
+        acc_prod(&ts, 1, &Ea[i], &be[i], L);
+        acc_prod(&ts, -1, &Ea[i], &al[i], L);
+        acc_prod(&tr, 1, &Eb[i], &al[i], L);
+        acc_prod(&tb, -1, &Eg[i], &ga[i], L);
+    }
+    dy_trunc(&ts, L, &th[0]);
+    dy_trunc(&tr, L, &th[1]);
+    dy_trunc(&tb, L, &th[2]);
+    dy_free(&ts);
+    dy_free(&tr);
+    dy_free(&tb);
+}
+
+static mpnum *mp_array(int n, int L, uint32_t **store)
+{
+    mpnum *m = malloc((size_t)(n ? n : 1) * sizeof(mpnum));
+    *store = calloc((size_t)(n ? n : 1) * L, sizeof(uint32_t));
+    if (!m || !*store) {
+        free(m);
+        free(*store);
+        *store = NULL;
+        g_err = ORC_ENOMEM;
+        return NULL;
+    }
+    for (int j = 0; j < n; j++) {
+        m[j].sign = 0;
+        m[j].exp = 0;
+        m[j].limb = *store + (size_t)j * L;
+    }
+    return m;
+}
+
+/* One reverse step from a step's coefficients (3*(N+1) numbers,
+ * component-major, as orc_coefficients gives them): gb[3] in/out, th[3]
+ * in/out (see adjoint_step). */
+int orc_adjoint_step(int L, int N, const int32_t *par_s, const int32_t *par_e, const uint32_t *par_l,
+                     const int32_t *c_s, const int32_t *c_e, const uint32_t *c_l, int32_t *gb_s,
+                     int32_t *gb_e, uint32_t *gb_l, int32_t *th_s, int32_t *th_e, uint32_t *th_l)
+{
+    if (L < 1 || N < 1) return ORC_EINVAL;
+    g_err = 0;
+    int32_t ps[4], pe[4];
+    memcpy(ps, par_s, sizeof ps);
+    memcpy(pe, par_e, sizeof pe);
+    mpnum par[4], gb[3], th[3];
+    wrap(par, ps, pe, (uint32_t *)par_l, 4, L);
+    wrap(gb, gb_s, gb_e, gb_l, 3, L);
+    wrap(th, th_s, th_e, th_l, 3, L);
+    int32_t *cs = malloc((size_t)3 * (N + 1) * sizeof(int32_t));
+    int32_t *ce = malloc((size_t)3 * (N + 1) * sizeof(int32_t));
+    mpnum *c = malloc((size_t)3 * (N + 1) * sizeof(mpnum));
+    uint32_t *Pst = NULL, *Est = NULL;
+    mpnum *P = mp_array(N + 1, L, &Pst), *E = mp_array(3 * N, L, &Est);
+    if (!cs || !ce || !c || !P || !E) g_err = ORC_ENOMEM;
+    if (!g_err) {
+        memcpy(cs, c_s, (size_t)3 * (N + 1) * sizeof(int32_t));
+        memcpy(ce, c_e, (size_t)3 * (N + 1) * sizeof(int32_t));
+        wrap(c, cs, ce, (uint32_t *)c_l, 3 * (N + 1), L);
+        tau_powers(L, N, &par[3], P);
+        adjoint_step(L, N, par, c, c + (N + 1), c + 2 * (N + 1), P, gb, th, E, E + N, E + 2 * N);
+        for (int k = 0; k < 3; k++) {
+            gb_s[k] = gb[k].sign;
+            gb_e[k] = gb[k].exp;
+            th_s[k] = th[k].sign;
+            th_e[k] = th[k].exp;
+        }
+    }
+    free(cs);
+    free(ce);
+    free(c);
+    free(P);
+    free(Pst);
+    free(E);
+    free(Est);
+    return g_err;
+}
+
+/* nsteps steps from st, then the reverse sweep: gb[3] (in: the adjoint of
+ * the final state; out: of the initial state) and th[3] (out: the adjoints
+ * of sigma, R, b, starting from zero).  The coefficients of every step are
+ * kept (the library recomputes them from checkpoints instead: the same
+ * numbers).  nthreads as orc_integrate (forward sums only). */
+int orc_backward(int L, int N, int64_t nsteps, const int32_t *par_s, const int32_t *par_e,
+                 const uint32_t *par_l, const int32_t *st_s, const int32_t *st_e,
+                 const uint32_t *st_l, int32_t *gb_s, int32_t *gb_e, uint32_t *gb_l, int32_t *th_s,
+                 int32_t *th_e, uint32_t *th_l, int nthreads)
+{
+    if (L < 1 || N < 1 || nsteps < 0) return ORC_EINVAL;
+    const size_t nc = (size_t)3 * (N + 1);
+    int32_t *hs = malloc((size_t)(nsteps ? nsteps : 1) * nc * sizeof(int32_t));
+    int32_t *he = malloc((size_t)(nsteps ? nsteps : 1) * nc * sizeof(int32_t));
+    uint32_t *hl = malloc((size_t)(nsteps ? nsteps : 1) * nc * L * sizeof(uint32_t));
+    int32_t ss[3], se[3];
+    uint32_t *sl = malloc((size_t)3 * L * sizeof(uint32_t));
+    uint32_t *scratch = malloc((size_t)L * sizeof(uint32_t));
+    int rc = ORC_OK;
+    if (!hs || !he || !hl || !sl || !scratch) rc = ORC_ENOMEM;
+    if (rc == ORC_OK) {
+        memcpy(ss, st_s, sizeof ss);
+        memcpy(se, st_e, sizeof se);
+        memcpy(sl, st_l, (size_t)3 * L * sizeof(uint32_t));
+    }
+    int32_t ps[4], pe[4];
+    memcpy(ps, par_s, sizeof ps);
+    memcpy(pe, par_e, sizeof pe);
+    mpnum par[4];
+    wrap(par, ps, pe, (uint32_t *)par_l, 4, L);
+    for (int64_t n = 0; n < nsteps && rc == ORC_OK; n++) {
+        int32_t *cs = hs + n * nc, *ce = he + n * nc;
+        uint32_t *cl = hl + (size_t)n * nc * L;
+        rc = orc_coefficients(L, N, par_s, par_e, par_l, ss, se, sl, cs, ce, cl, nthreads);
+        if (rc) break;
+        mpnum *coef = malloc(nc * sizeof(mpnum));
+        if (!coef) { rc = ORC_ENOMEM; break; }
+        wrap(coef, cs, ce, cl, (int)nc, L);
+        g_err = 0;
+        for (int comp = 0; comp < 3; comp++) {
+            mpnum out = {0, 0, sl + (size_t)comp * L};
+            horner(L, N, &par[3], &coef[comp * (N + 1)], &out, scratch);
+            ss[comp] = out.sign;
+            se[comp] = out.exp;
+        }
+        free(coef);
+        rc = g_err;
+    }
+    if (rc == ORC_OK) {
+        for (int k = 0; k < 3; k++) {
+            th_s[k] = 0;
+            th_e[k] = 0;
+        }
+        memset(th_l, 0, (size_t)3 * L * sizeof(uint32_t));
+        for (int64_t n = nsteps - 1; n >= 0 && rc == ORC_OK; n--)
+            rc = orc_adjoint_step(L, N, par_s, par_e, par_l, hs + n * nc, he + n * nc,
+                                  hl + (size_t)n * nc * L, gb_s, gb_e, gb_l, th_s, th_e, th_l);
+    }
+    free(hs);
+    free(he);
+    free(hl);
+    free(sl);
+    free(scratch);
+    return rc;
 }
 
 int orc_omp_max_threads(void)

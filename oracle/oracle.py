@@ -74,6 +74,11 @@ def lib():
                                         u32p, ctypes.c_int]
             L.orc_fma_trunc.argtypes = [ctypes.c_int, i32p, i32p, u32p, i32p, i32p, u32p]
             L.orc_omp_max_threads.argtypes = []
+            L.orc_adjoint_step.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, u32p, i32p, i32p,
+                                           u32p, i32p, i32p, u32p, i32p, i32p, u32p]
+            L.orc_backward.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, i32p, i32p, u32p,
+                                       i32p, i32p, u32p, i32p, i32p, u32p, i32p, i32p, u32p,
+                                       ctypes.c_int]
             _lib = L
     return _lib
 
@@ -231,6 +236,27 @@ def fma_trunc(L: int, a, b, c):
     o = MPArray(1, L)
     _check(lib().orc_fma_trunc(L, *v.ptrs(), *o.ptrs()))
     return int(o.sign[0]), int(o.exp[0]), [int(x) for x in o.limbs[0]]
+
+
+def adjoint_step(L: int, N: int, par: MPArray, coefs: MPArray, gbar: MPArray, thbar: MPArray):
+    """The reverse sweep of one step from its coefficients (3 (N+1) numbers,
+    as :func:`coefficients`): returns (the adjoint of the step's starting
+    state, the parameter adjoints thbar plus this step's part), 3 numbers
+    each."""
+    g, t = gbar.copy(), thbar.copy()
+    _check(lib().orc_adjoint_step(L, N, *par.ptrs(), *coefs.ptrs(), *g.ptrs(), *t.ptrs()))
+    return g, t
+
+
+def backward(L: int, N: int, nsteps: int, par: MPArray, st: MPArray, gbar: MPArray,
+             nthreads: int = 1):
+    """nsteps steps from st, then the reverse sweep from gbar (the adjoint of
+    the final state): (the adjoint of st, the adjoints of sigma, R, b), 3
+    numbers each."""
+    g, t = gbar.copy(), MPArray(3, L)
+    _check(lib().orc_backward(L, N, int(nsteps), *par.ptrs(), *st.ptrs(), *g.ptrs(), *t.ptrs(),
+                              int(nthreads)))
+    return g, t
 
 
 def omp_max_threads() -> int:
