@@ -280,27 +280,65 @@ int mpt_integrate_batch_params(int B, const int32_t *Ls, const int32_t *Ns, int6
                                uint32_t *limbs, uint64_t cuda_stream);
 
 /*
- * Vector-Jacobian products of the n-step map (x0, y0, z0, sigma, R, b) ->
- * (x, y, z) after nsteps steps of Eq. (3) and Eq. (2), for B initial points,
- * by central differences of bit-exact runs at L limbs and order N:
- * J[:, i] = (F(u + h e_i) - F(u - h e_i)) / (2h), h = 10^(-h_digits) (0: 100),
- * each difference formed exactly and rounded once to double.  Its error is
- * about |F'''| h^2 + 2^(-32 (L-1)) |F| / h (e.g. 1e-200 of |F| at L = 32,
- * h = 1e-100).  The 12 B runs go to one batch launch.  (The paper has no
- * derivatives; this is the differentiation of its flow.)
- *   x0[B * 3]:         initial values (strings, as mpt_set_state), point-major;
- *   sigma, R, b, tau:  strings, as mpt_init;
- *   g[B * 3]:          the upstream gradient of each final state (host);
- *   g_x0[B * 3]:       out, g^T J with respect to the x0, y0, z0 of each point;
- *   g_params[3]:       out, g^T J with respect to sigma, R, b, summed over points;
- *   jac[B * 3 * 6]:    out (nullable), J per point, [output][input].
- * Host arrays; synchronous on cuda_stream.  Errors as mpt_integrate_batch;
- * MPT_EINVAL for a malformed string, a null array or h_digits outside 1..10000.
+ * Derivatives of the n-step map (x0, y0, z0, sigma, R, b) -> (x, y, z) after
+ * nsteps steps of Eq. (3) and Eq. (2) (Sec. 2; the paper has no derivatives,
+ * this is the differentiation of its flow) by a reverse sweep in the same
+ * L-limb format.  It is the derivative of the exact-arithmetic order-N map,
+ * evaluated at the stored (truncated) coefficients: going j = N .. 0 through
+ * each step, the adjoint of coefficient j is the exact sum of gbar tau^j
+ * (Eq. (2)), the linear terms of the brackets E_j of Eq. (3) and the Cauchy
+ * sums of the brackets E_i, i >= j, through their factor of index j; the
+ * adjoint of bracket E_{j-1} is that sum divided by j and truncated once, the
+ * adjoint of the step's starting state is the sum at j = 0 truncated, the
+ * parameter adjoints gain sum_i Ebar_i dE_i/d(sigma, R, b) per step (one
+ * truncation each), and tau^j is P_j = trunc_L(P_{j-1} tau).  The state is
+ * checkpointed every `checkpoint_every` steps (0: 50) and the coefficients of
+ * a segment's steps are recomputed before its sweep, so the cost is about
+ * four forward runs per adjoint vector.
+ *
+ * mpt_backward_raw: B trajectories with a common L and N, G adjoint vectors
+ * per trajectory (item j*G + g belongs to trajectory j); all arrays host
+ * memory in the interchange layout.  par: sigma, R, b, tau (4 numbers);
+ * st: the initial states (3B numbers); g: in, the adjoints of the final
+ * states (3 B G numbers), out, the adjoints of the initial states; th: out,
+ * the adjoints of (sigma, R, b) of every item (3 B G numbers).  MPT_EINVAL
+ * for sizes outside those of mpt_init or a malformed number; MPT_ERANGE /
+ * MPT_ENOMEM / MPT_ECUDA from the device.  Synchronous on cuda_stream.
+ */
+int mpt_backward_raw(int B, int G, int L, int N, int64_t nsteps, int checkpoint_every,
+                     const int32_t *par_signs, const int32_t *par_exps, const uint32_t *par_limbs,
+                     const int32_t *st_signs, const int32_t *st_exps, const uint32_t *st_limbs,
+                     int32_t *g_signs, int32_t *g_exps, uint32_t *g_limbs, int32_t *th_signs,
+                     int32_t *th_exps, uint32_t *th_limbs, uint64_t cuda_stream);
+
+/*
+ * The same in float64 for B initial points given as strings (x0[B * 3],
+ * point-major, as mpt_set_state) and parameters as strings (as mpt_init):
+ *   g[B * 3]:        the upstream gradient of each final state (exact doubles);
+ *   g_x0[B * 3]:     out, g^T J with respect to each point's x0, y0, z0;
+ *   g_params[3]:     out, g^T J with respect to sigma, R, b, summed over points;
+ *   jac[B * 3 * 6]:  out (nullable), J per point, [output][input]; when given,
+ *                    three sweeps per point (gbar = e_x, e_y, e_z) and g_x0,
+ *                    g_params formed from J in double.
+ * Every number is rounded once to the nearest double.
  */
 int mpt_backward(int B, int L, int N, int64_t nsteps, const char *tau, const char *sigma,
                  const char *R, const char *b, const char *const *x0, const double *g,
-                 int h_digits, double *g_x0, double *g_params, double *jac,
+                 int checkpoint_every, double *g_x0, double *g_params, double *jac,
                  uint64_t cuda_stream);
+
+/*
+ * The 3 x 6 Jacobians of the same map by central differences of bit-exact
+ * runs: J[:, i] = (F(u + h e_i) - F(u - h e_i)) / (2h), h = 10^(-h_digits)
+ * (0: 100), each difference formed exactly and rounded once to double; its
+ * error is about |F'''| h^2 + 2^(-32 (L-1)) |F| / h.  The 12 B runs go to one
+ * batch launch.  A check of mpt_backward that needs no adjoint.
+ * jac[B * 3 * 6], [output][input]; errors as mpt_integrate_batch, MPT_EINVAL
+ * for h_digits outside 1..10000.
+ */
+int mpt_jacobian_fd(int B, int L, int N, int64_t nsteps, const char *tau, const char *sigma,
+                    const char *R, const char *b, const char *const *x0, int h_digits, double *jac,
+                    uint64_t cuda_stream);
 
 /*
  * Allocation-free stepping (the paper has no counterpart; it is a service of

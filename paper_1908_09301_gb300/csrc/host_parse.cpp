@@ -287,6 +287,29 @@ BigU magnitude(const uint32_t *l, int L, long long sh)
 
 // The exact rational x + sgn 10^(-h_digits) of a decimal or rational string,
 // written as "p/q".  Returns 0, or -1 for a malformed x.
+// Y 2^k (Y a non-zero magnitude), negated when neg, rounded once to the
+// nearest double (ties to even)
+static double rounded(const BigU &y, long long k, bool neg)
+{
+    const int nb = y.bits();
+    double r;
+    if (nb <= 53) {
+        uint64_t v = 0;
+        for (size_t i = y.w.size(); i-- > 0;) v = (v << 32) | y.w[i];
+        r = std::ldexp((double)v, (int)k);
+    } else {
+        const int drop = nb - 53;
+        uint64_t q = 0;
+        for (int i = nb - 1; i >= drop; i--) q = (q << 1) | (uint64_t)y.bit(i);
+        const int half = y.bit(drop - 1);
+        bool sticky = false;
+        for (int i = drop - 2; i >= 0 && !sticky; i--) sticky = y.bit(i) != 0;
+        if (half && (sticky || (q & 1))) q++;
+        r = std::ldexp((double)q, (int)(k + drop));
+    }
+    return neg ? -r : r;
+}
+
 int perturbed_string(const char *x, int h_digits, int sgn, std::string &out)
 {
     Rat r;
@@ -363,25 +386,39 @@ double diff_over_2h(int L, int32_t s1, int32_t e1, const uint32_t *l1, int32_t s
     }
     if (d.zero()) return 0.0;
     // |result| = Y 2^k, Y = |d| 10^h, k = 32 (emin - L) - 1
-    const BigU y = mul(d, pow10(h_digits));
-    const long long k = 32LL * (emin - L) - 1;
-    const int nb = y.bits();
-    double r;
-    if (nb <= 53) {
-        uint64_t v = 0;
-        for (size_t i = y.w.size(); i-- > 0;) v = (v << 32) | y.w[i];
-        r = std::ldexp((double)v, (int)k);
+    return rounded(mul(d, pow10(h_digits)), 32LL * (emin - L) - 1, neg);
+}
+
+// the L-limb interchange number, rounded once to the nearest double
+double to_double(int L, int32_t s, int32_t e, const uint32_t *l)
+{
+    bool z = true;
+    for (int j = 0; j < L; j++) z = z && l[j] == 0;
+    if (z) return 0.0;
+    return rounded(magnitude(l, L, 0), 32LL * ((long long)e - L), s != 0);
+}
+
+// trunc_L of the exact value of a finite double; 0, or -1 for inf / nan
+int from_double(double v, int L, int32_t *sign, int32_t *exp, uint32_t *limbs)
+{
+    if (!std::isfinite(v)) return -1;
+    int x = 0;
+    const double f = std::frexp(std::fabs(v), &x);  // |v| = f 2^x, 1/2 <= f < 1
+    const uint64_t m = (uint64_t)std::ldexp(f, 53);  // exact: |v| = m 2^(x - 53)
+    BigU num;
+    num.w = {(uint32_t)m, (uint32_t)(m >> 32)};
+    num.trim();
+    std::string str = (v < 0 ? "-" : "");
+    if (x - 53 >= 0) {
+        num.shl(x - 53);
+        str += to_decimal(num);
     } else {
-        const int drop = nb - 53;
-        uint64_t q = 0;
-        for (int i = nb - 1; i >= drop; i--) q = (q << 1) | (uint64_t)y.bit(i);
-        const int half = y.bit(drop - 1);
-        bool sticky = false;
-        for (int i = drop - 2; i >= 0 && !sticky; i--) sticky = y.bit(i) != 0;
-        if (half && (sticky || (q & 1))) q++;
-        r = std::ldexp((double)q, (int)(k + drop));
+        BigU den;
+        den.w = {1u};
+        den.shl(53 - x);
+        str += to_decimal(num) + "/" + to_decimal(den);
     }
-    return neg ? -r : r;
+    return parse_number(str.c_str(), L, sign, exp, limbs);
 }
 
 // trunc_L of an exact decimal or rational string.  Returns 0, or -1 for a

@@ -14,4 +14,8 @@ int perturbed_string(const char *x, int h_digits, int sgn, std::string &out);
 // once to the nearest double
 double diff_over_2h(int L, int32_t s1, int32_t e1, const uint32_t *l1, int32_t s2, int32_t e2,
                     const uint32_t *l2, int h_digits);
+// the L-limb interchange number rounded once to the nearest double (ties to even)
+double to_double(int L, int32_t s, int32_t e, const uint32_t *l);
+// trunc_L of the exact value of a finite double; 0, or -1 for inf / nan
+int from_double(double v, int L, int32_t *sign, int32_t *exp, uint32_t *limbs);
 }  // namespace mpt_host

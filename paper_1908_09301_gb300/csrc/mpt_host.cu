@@ -1114,13 +1114,12 @@ int mpt_integrate_batch_params(int B, const int32_t *Ls, const int32_t *Ns, int6
     return batch_impl(B, Ls, Ns, nsteps, tau, sigma, R, b, 1, signs, exps, limbs, cuda_stream);
 }
 
-int mpt_backward(int B, int L, int N, int64_t nsteps, const char *tau, const char *sigma, const char *R,
-                 const char *b, const char *const *x0, const double *g, int h_digits, double *g_x0,
-                 double *g_params, double *jac, uint64_t cuda_stream)
+int mpt_jacobian_fd(int B, int L, int N, int64_t nsteps, const char *tau, const char *sigma,
+                    const char *R, const char *b, const char *const *x0, int h_digits, double *jac,
+                    uint64_t cuda_stream)
 {
     if (B < 1) return fail(MPT_EINVAL, "batch size %d < 1", B);
-    if (!tau || !sigma || !R || !b || !x0 || !g || !g_x0 || !g_params)
-        return fail(MPT_EINVAL, "null argument");
+    if (!tau || !sigma || !R || !b || !x0 || !jac) return fail(MPT_EINVAL, "null argument");
     if (h_digits == 0) h_digits = 100;
     if (h_digits < 1 || h_digits > 10000) return fail(MPT_EINVAL, "h_digits = %d outside 1..10000", h_digits);
     if (L < 1 || L > mpt::MAX_L) return fail(MPT_EINVAL, "L = %d outside 1..%d", L, mpt::MAX_L);
@@ -1158,24 +1157,13 @@ int mpt_backward(int B, int L, int N, int64_t nsteps, const char *tau, const cha
     const int rc = batch_impl(runs, Ls.data(), Ns.data(), nsteps, tau, ps[0].data(), ps[1].data(),
                               ps[2].data(), 1, ss.data(), se.data(), sl.data(), cuda_stream);
     if (rc) return rc;
-    for (int p = 0; p < 3; p++) g_params[p] = 0.0;
-    for (int j = 0; j < B; j++) {
-        double J[3][6];
+    for (int j = 0; j < B; j++)
         for (int i = 0; i < 6; i++)
             for (int o = 0; o < 3; o++) {
                 const size_t a = ((size_t)(j * 6 + i) * 2) * 3 + o, c = a + 3;
-                J[o][i] = mpt_host::diff_over_2h(L, ss[a], se[a], &sl[a * L], ss[c], se[c], &sl[c * L], h_digits);
+                jac[((size_t)j * 3 + o) * 6 + i] =
+                    mpt_host::diff_over_2h(L, ss[a], se[a], &sl[a * L], ss[c], se[c], &sl[c * L], h_digits);
             }
-        for (int i = 0; i < 6; i++) {
-            double v = 0.0;
-            for (int o = 0; o < 3; o++) v += g[3 * j + o] * J[o][i];
-            if (i < 3) g_x0[3 * j + i] = v;
-            else g_params[i - 3] += v;
-        }
-        if (jac)
-            for (int o = 0; o < 3; o++)
-                for (int i = 0; i < 6; i++) jac[((size_t)j * 3 + o) * 6 + i] = J[o][i];
-    }
     return MPT_OK;
 }
 

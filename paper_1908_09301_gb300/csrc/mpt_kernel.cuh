@@ -67,6 +67,20 @@ struct KArgs {
     int npar, ptau;         // parameters in parL, tau's index among them
     int nwin;               // lock-step kernel: copies of the three windows the term
                             // phase adds into (warp w uses copy w mod nwin; 0 = 1)
+    // batch kernel: after each step, a copy of the step's coefficient table to
+    // histL + step 3 (N+1) Lp and histE/F + step 3 (N+1) (null: none)
+    uint32_t *histL;
+    int32_t *histE, *histF;
+    // batch kernel, reverse sweep (the adjoint of Eq. (3) and Eq. (2)): adj = 1;
+    // the forward coefficients of the launch's steps (as histL above); the powers
+    // of tau [N+1][Lp] the launch computes; parL holds sigma, R, b, tau, then the
+    // adjoint gbar of the state (3 rows, replaced step by step) and the
+    // parameter adjoints (3 rows, accumulated); coefL holds the adjoint series
+    int adj;
+    const uint32_t *fwdL;
+    const int32_t *fwdE, *fwdF;
+    uint32_t *powL;
+    int32_t *powE, *powF;
     int exact;              // pipelined kernel: 1 = every product in full (no shortened sums)
     unsigned long long *chunks;  // pipelined kernel: executed 8 x 8 limb-product chunks of
                                  // the launch are added here (null: not counted)
@@ -74,6 +88,8 @@ struct KArgs {
 
 // limits of a general system
 constexpr int SYS_MAX_PAR = 16;    // parameters, tau included
+// rows of parL in a reverse sweep: sigma, R, b, tau, gbar (x, y, z), thbar (sigma, R, b)
+constexpr int ADJ_GBAR = 4, ADJ_THBAR = 7, ADJ_NPAR = 10;
 constexpr int SYS_MAX_FIXED = 32;  // fixed terms (linear and constant)
 constexpr int SYS_MAX_QUAD = 16;   // Cauchy products
 
@@ -121,8 +137,8 @@ int pipe_fixed_ctas();
 int pipe_max_ctas(size_t smem);
 cudaError_t launch_pipe(const KArgs &a, const PArgs &pa, int grid, size_t smem, cudaStream_t st);
 
-// dynamic shared memory bytes for a configuration
-size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb, int nwin = 1);
+// dynamic shared memory bytes for a configuration (adj: the reverse sweep's tables too)
+size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb, int nwin = 1, bool adj = false);
 // launch nsteps steps on `grid` CTAs (cooperative when grid > 1)
 cudaError_t launch_integrate(const KArgs &a, int grid, size_t smem, cudaStream_t st);
 // largest co-resident grid for this smem size (0 on error)

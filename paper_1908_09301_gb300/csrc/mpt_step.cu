@@ -107,6 +107,8 @@ struct Smem {
     int *tinfo;       // [tb][2]
     int *srcs;        // [tb][2] operand sources of the staged terms
     int *misc;        // [MISC_INTS]
+    int *fexpT, *fflgT;  // reverse sweep: [3][N+1] the forward coefficients of the step
+    int *pexpT, *pflgT;  // reverse sweep: [N+1] the powers of tau
     int AV, CV, M;
 };
 
@@ -128,8 +130,13 @@ enum {
     MS_HF = 116,    // [3] Horner: flags of h
     MS_ERR = 120,   // status snapshot shared by the CTA
     MS_PNZ = 124,   // [SYS_MAX_PAR] non-zero limb count of each parameter
-    MISC_INTS = MS_PNZ + SYS_MAX_PAR,
+    MS_FWDOFF = MS_PNZ + SYS_MAX_PAR,  // long long (2 ints): limb offset of the step in fwdL
+    MISC_INTS = MS_FWDOFF + 2,
 };
+
+// what an index of the lock-step body computes: Eq. (3) (forward); in the
+// reverse sweep: a power of tau, an adjoint index, the parameter adjoints
+enum { MODE_FWD = 0, MODE_POW = 1, MODE_ADJ = 2, MODE_PAR = 3 };
 
 // The status word as one value for the whole CTA, so that every thread takes
 // the same branch after it (a per-thread read could differ while another CTA
@@ -166,6 +173,17 @@ __device__ Smem carve(unsigned char *base, const KArgs &a)
     S.srcs = (int *)(base + o);
     o = align16(o + sizeof(int) * 2 * a.tb);
     S.misc = (int *)(base + o);
+    o = align16(o + sizeof(int) * MISC_INTS);
+    S.fexpT = S.fflgT = S.pexpT = S.pflgT = nullptr;
+    if (a.adj) {
+        S.fexpT = (int *)(base + o);
+        o = align16(o + sizeof(int) * 3 * (a.N + 1));
+        S.fflgT = (int *)(base + o);
+        o = align16(o + sizeof(int) * 3 * (a.N + 1));
+        S.pexpT = (int *)(base + o);
+        o = align16(o + sizeof(int) * (a.N + 1));
+        S.pflgT = (int *)(base + o);
+    }
     return S;
 }
 
@@ -266,8 +284,80 @@ __device__ __forceinline__ Term lorenz_term(int m, int t, int N1)
 // {target, neg, p, j} = p x_j (p >= 0, j >= 0), the lone x_j (p < 0) or the
 // constant p (j < 0; index 0 only); then per Cauchy product {target, neg,
 // i, j} its m+1 terms x_i[m-l] x_j[l], l = 0..m.  T = NF + NQ (m+1).
-__device__ __forceinline__ Term term_of(const KArgs &a, int m, int t, int N1)
+// operand sources of the reverse sweep beyond the coefficient (here: adjoint
+// series) rows: the step's forward coefficients and the powers of tau
+constexpr int SRC_FWD = 1 << 24, SRC_POW = 2 << 24;
+
+// Terms of the reverse sweep (the adjoint of Eq. (3) and Eq. (2)).  The
+// adjoint series is y_X[r] = Ebar_X,{N-1-r} for r < N (Ebar_X,i: the
+// adjoint of the bracket of Eq. (3) that gives coefficient i+1) and y_X[N]
+// the adjoint of the step's starting state; with j = N - m, index m is
+//   y_x[m] = ( gbar_x P_j - sigma y_x[m-1] + R y_y[m-1]
+//              + sum_{l<m} (-y_y[m-1-l] gamma_l + y_z[m-1-l] beta_l) ) / j
+//   y_y[m] = ( gbar_y P_j + sigma y_x[m-1] - y_y[m-1] + sum_{l<m} y_z[m-1-l] alpha_l ) / j
+//   y_z[m] = ( gbar_z P_j - b y_z[m-1] - sum_{l<m} y_y[m-1-l] alpha_l ) / j
+// (divisor 1 at m = N; no y[m-1] terms at m = 0), the Cauchy sums of the
+// brackets E_i, i >= j, read through their factor of index j.  MODE_POW:
+// P_m = P_{m-1} tau.  MODE_PAR: thbar_sigma + sum_i Ebar_x,i (beta_i -
+// alpha_i), thbar_R + sum_i Ebar_y,i alpha_i, thbar_b - sum_i Ebar_z,i gamma_i.
+__device__ __forceinline__ Term adjoint_term(const KArgs &a, int mode, int m, int t, int N1)
 {
+    const int N = a.N;
+    Term r;
+    r.add = 0;
+    r.skip = 0;
+    r.neg = 0;
+    if (mode == MODE_POW) {
+        r.target = 0;
+        r.asrc = SRC_POW + m - 1;
+        r.bsrc = -1 - P_TAU;
+        return r;
+    }
+    if (mode == MODE_PAR) {
+        if (t < 3) {  // the running parameter adjoints
+            r.target = t;
+            r.add = 1;
+            r.asrc = 0;
+            r.bsrc = -1 - (ADJ_THBAR + t);
+            return r;
+        }
+        const int u = t - 3, i = u >> 2, k = u & 3;
+        const int yr = N - 1 - i;  // Ebar_i
+        if (k == 0) { r.target = 0; r.asrc = 0 * N1 + yr; r.bsrc = SRC_FWD + 1 * N1 + i; }
+        else if (k == 1) { r.target = 0; r.neg = 1; r.asrc = 0 * N1 + yr; r.bsrc = SRC_FWD + 0 * N1 + i; }
+        else if (k == 2) { r.target = 1; r.asrc = 1 * N1 + yr; r.bsrc = SRC_FWD + 0 * N1 + i; }
+        else { r.target = 2; r.neg = 1; r.asrc = 2 * N1 + yr; r.bsrc = SRC_FWD + 2 * N1 + i; }
+        return r;
+    }
+    // MODE_ADJ
+    if (t < 3) {  // Eq. (2): gbar_X P_j
+        r.target = t;
+        r.asrc = -1 - (ADJ_GBAR + t);
+        r.bsrc = SRC_POW + (N - m);
+        return r;
+    }
+    if (t < 8) {  // the linear terms of the brackets E_j
+        const int k = m - 1;
+        switch (t) {
+        case 3: r.target = 0; r.neg = 1; r.asrc = -1 - P_SIGMA; r.bsrc = 0 * N1 + k; break;
+        case 4: r.target = 0; r.asrc = -1 - P_R; r.bsrc = 1 * N1 + k; break;
+        case 5: r.target = 1; r.asrc = -1 - P_SIGMA; r.bsrc = 0 * N1 + k; break;
+        case 6: r.target = 1; r.neg = 1; r.add = 1; r.asrc = 0; r.bsrc = 1 * N1 + k; break;
+        default: r.target = 2; r.neg = 1; r.asrc = -1 - P_B; r.bsrc = 2 * N1 + k; break;
+        }
+        return r;
+    }
+    const int u = t - 8, l = u >> 2, k = u & 3, yr = m - 1 - l;
+    if (k == 0) { r.target = 0; r.neg = 1; r.asrc = 1 * N1 + yr; r.bsrc = SRC_FWD + 2 * N1 + l; }
+    else if (k == 1) { r.target = 0; r.asrc = 2 * N1 + yr; r.bsrc = SRC_FWD + 1 * N1 + l; }
+    else if (k == 2) { r.target = 1; r.asrc = 2 * N1 + yr; r.bsrc = SRC_FWD + 0 * N1 + l; }
+    else { r.target = 2; r.neg = 1; r.asrc = 1 * N1 + yr; r.bsrc = SRC_FWD + 0 * N1 + l; }
+    return r;
+}
+
+__device__ __forceinline__ Term term_of(const KArgs &a, int m, int t, int N1, int mode = MODE_FWD)
+{
+    if (mode != MODE_FWD) return adjoint_term(a, mode, m, t, N1);
     if (!a.sysT) return lorenz_term(m, t, N1);
     Term r;
     r.add = 0;
@@ -299,8 +389,11 @@ __device__ __forceinline__ Term term_of(const KArgs &a, int m, int t, int N1)
 }
 
 // terms of index m
-__device__ __forceinline__ int nterms(const KArgs &a, int m)
+__device__ __forceinline__ int nterms(const KArgs &a, int m, int mode = MODE_FWD)
 {
+    if (mode == MODE_POW) return 1;
+    if (mode == MODE_ADJ) return m >= 1 ? 8 + 4 * m : 3;
+    if (mode == MODE_PAR) return 3 + 4 * a.N;
     return a.sysT ? a.sysNF + a.sysNQ * (m + 1) : 2 * m + 7;
 }
 
@@ -311,12 +404,21 @@ struct Meta {
 __device__ __forceinline__ Meta meta_of(const Smem &S, const KArgs &a, int src)
 {
     Meta r;
-    if (src >= 0) {
+    if (src >= SRC_POW) {
+        r.e = S.pexpT[src - SRC_POW];
+        r.f = S.pflgT[src - SRC_POW];
+    } else if (src >= SRC_FWD) {
+        r.e = S.fexpT[src - SRC_FWD];
+        r.f = S.fflgT[src - SRC_FWD];
+    } else if (src >= 0) {
         r.e = S.expT[src];
         r.f = S.flgT[src];
-    } else {
+    } else if (-1 - src < 4) {
         r.e = __ldg(&a.parE[-1 - src]);
         r.f = __ldg(&a.parF[-1 - src]);
+    } else {  // reverse sweep: gbar and the parameter adjoints change during the launch
+        r.e = __ldcg(&a.parE[-1 - src]);
+        r.f = __ldcg(&a.parF[-1 - src]);
     }
     return r;
 }
@@ -673,14 +775,14 @@ __device__ __forceinline__ long long win_base(const Smem &S, int tg)
 // non-zero terms of each bracket and the highest position the exact sum can
 // reach (product: 2Lp columns plus two carry limbs of the 96-bit column sums
 // and of the sum's growth; lone number: Lp limbs plus two).
-__device__ void place_windows(const Smem &S, const KArgs &a, int m)
+__device__ void place_windows(const Smem &S, const KArgs &a, int m, int mode = MODE_FWD)
 {
-    const int T = nterms(a, m);
+    const int T = nterms(a, m, mode);
     const int N1 = a.N + 1;
     long long lo[3] = {LLONG_MAX, LLONG_MAX, LLONG_MAX};
     long long hi[3] = {LLONG_MIN, LLONG_MIN, LLONG_MIN};
     for (int t = threadIdx.x; t < T; t += NT) {
-        Term tm = term_of(a, m, t, N1);
+        Term tm = term_of(a, m, t, N1, mode);
         if (tm.skip) continue;
         Meta mb = meta_of(S, a, tm.bsrc);
         if (!(mb.f & F_NZ)) continue;
@@ -707,7 +809,7 @@ enum { SRC_NEWC = -100, SRC_NONE = -1000 };
 
 __device__ __forceinline__ int src_code(int src, int m, int N1)
 {
-    if (src < 0) return src;
+    if (src < 0 || src >= SRC_FWD) return src;
     const int comp = src / N1, idx = src - comp * N1;
     return idx == m ? SRC_NEWC - comp : src;
 }
@@ -716,12 +818,14 @@ __device__ __forceinline__ int src_code(int src, int m, int N1)
 // One thread per slot places the term and records where its operands come
 // from; then all threads copy the operands' limbs, element by element over
 // the whole batch, with no per-element term lookup.
-__device__ void stage_terms(const Smem &S, const KArgs &a, int m, int t0, int nt)
+__device__ void stage_terms(const Smem &S, const KArgs &a, int m, int t0, int nt, int mode = MODE_FWD)
 {
     const int N1 = a.N + 1;
     const int Lp = a.Lp;
+    // the row held in S.newc: coefficient m (forward), adjoint m - 1 (reverse sweep)
+    const int newest = mode == MODE_FWD ? m : (mode == MODE_ADJ ? m - 1 : -1);
     for (int slot = threadIdx.x; slot < nt; slot += NT) {
-        Term tm = term_of(a, m, t0 + slot, N1);
+        Term tm = term_of(a, m, t0 + slot, N1, mode);
         Meta mb = meta_of(S, a, tm.bsrc);
         int flags = 0, off = 0;
         bool skip = tm.skip || !(mb.f & F_NZ);
@@ -746,10 +850,10 @@ __device__ void stage_terms(const Smem &S, const KArgs &a, int m, int t0, int nt
         int ca = SRC_NONE, cb = SRC_NONE;
         if (!skip) {
             if (tm.add) {
-                ca = src_code(tm.bsrc, m, N1);  // a lone number goes to the A layout
+                ca = src_code(tm.bsrc, newest, N1);  // a lone number goes to the A layout
             } else {
-                ca = src_code(tm.asrc, m, N1);
-                cb = src_code(tm.bsrc, m, N1);
+                ca = src_code(tm.asrc, newest, N1);
+                cb = src_code(tm.bsrc, newest, N1);
             }
         }
         S.srcs[2 * slot] = ca;
@@ -775,9 +879,14 @@ __device__ void stage_terms(const Smem &S, const KArgs &a, int m, int t0, int nt
                 const int x = r - which * Lp;
                 const int code = S.srcs[2 * slot + which];
                 if (code != SRC_NONE) {
-                    if (code >= 0) v[k] = __ldcg(&a.coefL[(size_t)code * Lp + x]);
+                    if (code >= SRC_POW) v[k] = __ldcg(&a.powL[(size_t)(code - SRC_POW) * Lp + x]);
+                    else if (code >= SRC_FWD)
+                        v[k] = __ldcg(&a.fwdL[((const long long *)(S.misc + MS_FWDOFF))[0] +
+                                              (size_t)(code - SRC_FWD) * Lp + x]);
+                    else if (code >= 0) v[k] = __ldcg(&a.coefL[(size_t)code * Lp + x]);
                     else if (code <= SRC_NEWC) v[k] = S.newc[(SRC_NEWC - code) * Lp + x];
-                    else v[k] = __ldg(&a.parL[(size_t)(-1 - code) * Lp + x]);
+                    else if (-1 - code < 4) v[k] = __ldg(&a.parL[(size_t)(-1 - code) * Lp + x]);
+                    else v[k] = __ldcg(&a.parL[(size_t)(-1 - code) * Lp + x]);
                     dst[k] = slot * (S.AV + S.CV) + (which ? S.AV + phys(x) : phys(x));
                 }
             }
@@ -835,11 +944,11 @@ __device__ void run_unit_warp(const Smem &S, const KArgs &a, int slot, int q, in
 // and then into the global accumulators
 // ONE_CTA: compiled for a grid of one CTA only (the batch)
 template <bool ONE_CTA>
-__device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
+__device__ void term_phase(const Smem &S, const KArgs &a, int m, int set, int mode = MODE_FWD)
 {
     const int G = vgrid(a), g = vrank(a);
     Prof pr(a);
-    place_windows(S, a, m);
+    place_windows(S, a, m, mode);
     if (!cta_ok(S, a)) return;
     pr.mark(PR_PLACE);
     if (G > 1) {
@@ -849,14 +958,14 @@ __device__ void term_phase(const Smem &S, const KArgs &a, int m, int set)
         long long *nxt = a.gwin + (size_t)((set + 1) % 3) * 3 * a.Wcap;
         for (int e = g * NT + threadIdx.x; e < 3 * a.Wcap; e += G * NT) nxt[e] = 0;
     }
-    const long long T = nterms(a, m);
+    const long long T = nterms(a, m, mode);
     const long long U = T * a.P;
     const long long u0 = U * g / G, u1 = U * (g + 1) / G;
     if (u0 < u1) {
         const int tA = (int)(u0 / a.P), tB = (int)((u1 - 1) / a.P);
         for (int tb0 = tA; tb0 <= tB; tb0 += a.tb) {
             const int nt = min(a.tb, tB - tb0 + 1);
-            stage_terms(S, a, m, tb0, nt);
+            stage_terms(S, a, m, tb0, nt, mode);
             __syncthreads();
             pr.mark(PR_STAGE);
             const long long ua = max(u0, (long long)tb0 * a.P);
@@ -1132,19 +1241,146 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
     }
 }
 
+// ------------------------------------------------------------------ reverse sweep
+
+// The brackets of one index of the reverse sweep, on one CTA (the windows in
+// shared memory): normalise each target's window, divide by d, truncate to L
+// limbs into S.newc (component = target), and store the result -- a power of
+// tau (MODE_POW, index m), adjoint m (MODE_ADJ), or the parameter adjoints
+// (MODE_PAR).
+__device__ void adj_close(const Smem &S, const KArgs &a, int mode, int m, uint32_t d)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N1 = a.N + 1, Lp = a.Lp;
+    const int ntg = mode == MODE_POW ? 1 : 3;
+    if (warp < ntg) {
+        const int tg = warp;
+        const int wd = S.misc[MS_WIDTH + tg];
+        uint32_t *out = S.newc + tg * Lp;
+        int e = 0, f = 0;
+        if (wd > 0) {
+            uint32_t *dig = S.dig + (size_t)tg * a.Wcap;
+            Norm nr = warp_normalize(S.win + (size_t)tg * a.Wcap, false, dig, wd, a.status);
+            for (int c = lane; c < wd; c += 32) S.win[tg * a.Wcap + c] = 0;
+            if (nr.top >= 0) {
+                long long eq = warp_divide(dig, nr.top, win_base(S, tg), d, a.L, out);
+                if (eq > (1LL << 30) || eq < -(1LL << 30)) {
+                    if (lane == 0) set_status(a.status, DEV_ERANGE);
+                    eq = 0;
+                }
+                e = (int)eq;
+                f = F_NZ | (nr.neg ? F_NEG : 0);
+            }
+        }
+        if (!(f & F_NZ))
+            for (int x = lane; x < a.L; x += 32) out[x] = 0u;
+        for (int x = a.L + lane; x < Lp; x += 32) out[x] = 0u;
+        __syncwarp();
+        uint32_t *gl;
+        int32_t *ge, *gf;
+        int *se = nullptr, *sf = nullptr;
+        if (mode == MODE_POW) {
+            gl = a.powL + (size_t)m * Lp;
+            ge = a.powE + m;
+            gf = a.powF + m;
+            se = S.pexpT + m;
+            sf = S.pflgT + m;
+        } else if (mode == MODE_ADJ) {
+            const int row = tg * N1 + m;
+            gl = a.coefL + (size_t)row * Lp;
+            ge = a.coefE + row;
+            gf = a.coefF + row;
+            se = S.expT + row;
+            sf = S.flgT + row;
+        } else {
+            const int p = ADJ_THBAR + tg;
+            gl = (uint32_t *)a.parL + (size_t)p * Lp;
+            ge = (int32_t *)a.parE + p;
+            gf = (int32_t *)a.parF + p;
+        }
+        for (int x = lane; x < Lp; x += 32) gl[x] = out[x];
+        if (lane == 0) {
+            *ge = e;
+            *gf = f;
+            if (se) {
+                *se = e;
+                *sf = f;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// The reverse sweep over the launch's nsteps steps, last step first (one CTA,
+// one item: a trajectory's forward coefficients and one adjoint gbar): the
+// powers of tau P_0 = 1, P_j = trunc_L(P_{j-1} tau); then per step the
+// adjoint indices m = 0..N (the division by j = N - m, by 1 at m = N; y[N]
+// becomes gbar of the step before) and the parameter adjoints.
+__device__ void adjoint_body(const Smem &S, const KArgs &a)
+{
+    const int N = a.N, N1 = N + 1, Lp = a.Lp;
+    for (int x = threadIdx.x; x < Lp; x += NT) a.powL[x] = x == a.L - 1 ? 1u : 0u;
+    if (threadIdx.x == 0) {
+        a.powE[0] = 1;  // 1 = 1 * 2^(32 (1 - L + L - 1))
+        a.powF[0] = F_NZ;
+        S.pexpT[0] = 1;
+        S.pflgT[0] = F_NZ;
+    }
+    __syncthreads();
+    for (int j = 1; j <= N; j++) {
+        term_phase<true>(S, a, j, 0, MODE_POW);
+        if (!cta_ok(S, a)) return;
+        adj_close(S, a, MODE_POW, j, 1u);
+    }
+    if (!cta_ok(S, a)) return;
+    const size_t nc = 3 * (size_t)N1;
+    for (long long s = a.nsteps - 1; s >= 0; s--) {
+        for (int e = threadIdx.x; e < 3 * N1; e += NT) {
+            S.fexpT[e] = __ldcg(&a.fwdE[(size_t)s * nc + e]);
+            S.fflgT[e] = __ldcg(&a.fwdF[(size_t)s * nc + e]);
+        }
+        if (threadIdx.x == 0) ((long long *)(S.misc + MS_FWDOFF))[0] = s * (long long)nc * Lp;
+        __syncthreads();
+        for (int m = 0; m <= N; m++) {
+            term_phase<true>(S, a, m, 0, MODE_ADJ);
+            if (!cta_ok(S, a)) return;
+            adj_close(S, a, MODE_ADJ, m, m < N ? (uint32_t)(N - m) : 1u);
+        }
+        if (!cta_ok(S, a)) return;
+        // the adjoint of the step's starting state (y[N], in S.newc) is gbar of the step before
+        for (int e = threadIdx.x; e < 3 * Lp; e += NT)
+            ((uint32_t *)a.parL)[(size_t)ADJ_GBAR * Lp + e] = S.newc[e];
+        if (threadIdx.x < 3) {
+            ((int32_t *)a.parE)[ADJ_GBAR + threadIdx.x] = S.expT[threadIdx.x * N1 + N];
+            ((int32_t *)a.parF)[ADJ_GBAR + threadIdx.x] = S.flgT[threadIdx.x * N1 + N];
+        }
+        __syncthreads();
+        term_phase<true>(S, a, 0, 0, MODE_PAR);
+        if (!cta_ok(S, a)) return;
+        adj_close(S, a, MODE_PAR, 0, 1u);
+        if (!cta_ok(S, a)) return;
+    }
+}
+
 template <bool ONE_CTA>
 __device__ void taylor_body(const KArgs &a, unsigned char *smem_raw)
 {
     Smem S = carve(smem_raw, a);
     const int N1 = a.N + 1;
     Prof tot(a);
-    if (threadIdx.x < (a.sysT ? a.npar : 4)) {
+    if (threadIdx.x < (a.adj ? ADJ_NPAR : (a.sysT ? a.npar : 4))) {
         int nz = 0;
         for (int x = 0; x < a.Lp; x++) nz += __ldg(&a.parL[(size_t)threadIdx.x * a.Lp + x]) != 0u;
         S.misc[MS_PNZ + threadIdx.x] = nz;
     }
     init_slots(S, a);
     __syncthreads();
+    if (ONE_CTA && a.adj) {
+        adjoint_body(S, a);
+        __syncthreads();
+        tot.mark(PR_TOTAL);
+        return;
+    }
     for (long long step = 0; step < a.nsteps; step++) {
         // alpha_0, beta_0, gamma_0 = the state (Sec. 2)
         for (int e = threadIdx.x; e < 3 * a.Lp; e += NT) {
@@ -1182,6 +1418,17 @@ __device__ void taylor_body(const KArgs &a, unsigned char *smem_raw)
             __syncthreads();
             ph.mark(PR_HORNER);
         }
+        if (ONE_CTA && a.histL) {
+            // the step's coefficients, kept for a reverse sweep
+            const size_t nc = 3 * (size_t)N1;
+            uint32_t *hl = a.histL + (size_t)step * nc * a.Lp;
+            for (size_t e = threadIdx.x; e < nc * a.Lp; e += NT) hl[e] = __ldcg(&a.coefL[e]);
+            for (int e = threadIdx.x; e < (int)nc; e += NT) {
+                a.histE[(size_t)step * nc + e] = __ldcg(&a.coefE[e]);
+                a.histF[(size_t)step * nc + e] = __ldcg(&a.coefF[e]);
+            }
+            __syncthreads();
+        }
         if (!grid_barrier(S, a)) break;
     }
     __syncthreads();
@@ -1206,7 +1453,7 @@ __global__ void __launch_bounds__(NT, 2) taylor_batch_kernel(const KArgs *args)
 
 }  // namespace
 
-size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb, int nwin)
+size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb, int nwin, bool adj)
 {
     (void)L;
     int AV, CV, M;
@@ -1221,6 +1468,12 @@ size_t smem_bytes(int L, int Lp, int N, int Wcap, int tb, int nwin)
     o = align16(o + sizeof(int) * 2 * tb);
     o = align16(o + sizeof(int) * 2 * tb);
     o = align16(o + sizeof(int) * MISC_INTS);
+    if (adj) {
+        o = align16(o + sizeof(int) * 3 * (N + 1));
+        o = align16(o + sizeof(int) * 3 * (N + 1));
+        o = align16(o + sizeof(int) * (N + 1));
+        o = align16(o + sizeof(int) * (N + 1));
+    }
     return o;
 }
 

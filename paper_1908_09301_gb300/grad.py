@@ -1,23 +1,18 @@
-"""Derivatives of the multiple-precision Taylor flow, by central differences.
+"""Derivatives of the multiple-precision Taylor flow.
 
 The map is (x0, y0, z0, sigma, R, b) -> the Lorenz state after n steps of the
-paper's method (Eq. (3) and Eq. (2), the library's bit-exact runs).  Its 3x6
-Jacobian is taken as (F(u + h e_j) - F(u - h e_j)) / (2h) with the runs at L
-limbs and h far below float64 resolution but far above the truncation:
+paper's method (Eq. (3) and Eq. (2), the library's bit-exact runs).  Its
+derivative is taken by the library's reverse sweep (``mpt_backward``: the
+adjoint of Eq. (3) and Eq. (2) in the same L-limb format, with checkpoints
+and recomputed coefficients), which gives the derivative of the
+exact-arithmetic order-N map to about 2^(-32 (L-1)) relative, rounded once to
+float64.  ``mpt_jacobian_fd`` gives the same Jacobians by central differences
+of bit-exact runs (13 runs a point) as a check; both are formed in the C
+library, this module only marshals.
 
-    |error| ~ |F'''| h^2 + |F| 2^(-32 L) / h,
-
-so at 300 digits (L = 32) and h = 1e-100 both terms are near 1e-200 relative,
-and the float64 Jacobian is the derivative of the exact-arithmetic order-N map
-rounded once.  All runs of a call (the base point and the twelve perturbed
-runs of every initial point) go through one ``mpt_integrate_batch_params``
-launch.  The differences are formed exactly on the host.
-
-``TaylorFlow`` wraps the same differences as a ``torch.autograd.Function``:
-float64 inputs (their exact binary values are the multiple-precision inputs),
-float64 outputs; its backward pass is ``mpt_backward`` (the twelve perturbed
-runs of every point in one batch launch, the differences formed exactly and
-rounded once on the host, and the vector-Jacobian products).
+``TaylorFlow`` wraps the map as a ``torch.autograd.Function``: float64 inputs
+(their exact binary values are the multiple-precision inputs), float64
+outputs; its backward pass is one reverse sweep per point (``mpt_backward``).
 """
 from __future__ import annotations
 
@@ -69,42 +64,37 @@ def run_points(points, params, tau, L, N, nsteps, stream=0):
     return [_values(st) for st in out]
 
 
+def _hdigits(h: Fraction) -> int:
+    k = 0
+    while Fraction(1, 10 ** k) > h:
+        k += 1
+    if Fraction(1, 10 ** k) != h:
+        raise ValueError("h must be a power of ten 10^-k")
+    return k
+
+
 def flow_jacobian(x0s, params=("10", "28", "8/3"), tau="0.01", L=32, N=150, nsteps=500,
-                  h: Fraction = H_DEFAULT, with_value=True, stream=0):
+                  h: Fraction = H_DEFAULT, with_value=True, stream=0, method="adjoint",
+                  checkpoint_every=50):
     """For each initial point of x0s (three values each): the state after
     nsteps steps (exact Fractions; None unless with_value) and its 3x6
-    Jacobian (float64) with respect to (x0, y0, z0, sigma, R, b)."""
-    xs = [[exact(v) for v in p] for p in x0s]
-    ps = [exact(v) for v in params]
-    B = len(xs)
-    # per initial point: [the point,] then u + h e_j and u - h e_j for the six
-    # inputs; all runs of all points in one batch
-    pts, pars = [], []
-    for x in xs:
-        if with_value:
-            pts.append(list(x))
-            pars.append(ps)
-        for j in range(6):
-            for sg in (1, -1):
-                q, p = list(x), list(ps)
-                if j < 3:
-                    q[j] += sg * h
-                else:
-                    p[j - 3] += sg * h
-                pts.append(q)
-                pars.append(p)
-    res = run_points(pts, pars, tau, L, N, nsteps, stream)
-    per = 13 if with_value else 12
-    off = 1 if with_value else 0
-    J = np.zeros((B, 3, 6))
-    F = []
-    for b in range(B):
-        r = res[b * per:(b + 1) * per]
-        F.append(r[0] if with_value else None)
-        for j in range(6):
-            plus, minus = r[off + 2 * j], r[off + 2 * j + 1]
-            for i in range(3):
-                J[b, i, j] = float((plus[i] - minus[i]) / (2 * h))
+    Jacobian (float64) with respect to (x0, y0, z0, sigma, R, b), by the
+    reverse sweep (method "adjoint", three sweeps a point) or by central
+    differences with step h = 10^-k (method "fd")."""
+    xs = [[ratstr(exact(v)) for v in p] for p in x0s]
+    ps = [ratstr(exact(v)) for v in params]
+    t = ratstr(exact(tau))
+    if method == "adjoint":
+        _, _, J = mpt.backward(xs, np.zeros((len(xs), 3)), L, N, nsteps, t, *ps,
+                               checkpoint_every=checkpoint_every, with_jacobian=True, stream=stream)
+    elif method == "fd":
+        J = mpt.jacobian_fd(xs, L, N, nsteps, t, *ps, h_digits=_hdigits(Fraction(h)), stream=stream)
+    else:
+        raise ValueError(f"unknown method {method!r}")
+    F = [None] * len(xs)
+    if with_value:
+        F = run_points([[exact(v) for v in p] for p in x0s], [exact(v) for v in params], tau, L, N,
+                       nsteps, stream)
     return F, J
 
 
@@ -133,8 +123,7 @@ def _torch_function():
 
         @staticmethod
         def backward(ctx, g):
-            # the twelve perturbed runs of every point and the products g^T J
-            # through the C ABI (mpt_backward)
+            # one reverse sweep per point through the C ABI (mpt_backward)
             xs, ps, L, N, nsteps, tau = ctx.cfg
             gx, gp, _ = mpt.backward([[ratstr(exact(v)) for v in x] for x in xs],
                                      g.detach().to(torch.float64).cpu().numpy(), L, N, nsteps,

@@ -70,6 +70,12 @@ SIGNATURES = {
     "mpt_backward": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_char_p,
                                     ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, vp, vp, ctypes.c_int,
                                     vp, vp, vp, ctypes.c_uint64]),
+    "mpt_backward_raw": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int64, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp,
+                                        vp, vp, vp, ctypes.c_uint64]),
+    "mpt_jacobian_fd": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64,
+                                       ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p,
+                                       vp, ctypes.c_int, vp, ctypes.c_uint64]),
     "mpt_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "mpt_last_error": (ctypes.c_char_p, []),
 }
@@ -381,25 +387,70 @@ def integrate_batch(Ls, Ns, nsteps: int, states, tau: str = "0.01", sigma="10",
     return out
 
 
-def backward(x0s, g, L: int, N: int, nsteps: int, tau: str = "0.01", sigma: str = "10", R: str = "28",
-             b: str = "8/3", h_digits: int = 100, with_jacobian: bool = False, stream: int = 0):
-    """``mpt_backward``: for initial points x0s (B triples of strings) and the
-    upstream gradients g [B, 3], returns g^T J with respect to the points
-    [B, 3] and to (sigma, R, b) [3], and the Jacobians [B, 3, 6] if asked."""
-    B = len(x0s)
+def _strings(x0s):
     strs = [str(v).encode() for p in x0s for v in p]
-    if len(strs) != 3 * B:
+    if len(strs) != 3 * len(x0s):
         raise ValueError("each initial point needs three values")
-    arr = (ctypes.c_char_p * len(strs))(*strs)
+    return (ctypes.c_char_p * len(strs))(*strs)
+
+
+def backward(x0s, g, L: int, N: int, nsteps: int, tau: str = "0.01", sigma: str = "10", R: str = "28",
+             b: str = "8/3", checkpoint_every: int = 50, with_jacobian: bool = False, stream: int = 0):
+    """``mpt_backward`` (the reverse sweep): for initial points x0s (B triples
+    of strings) and the upstream gradients g [B, 3], returns g^T J with
+    respect to the points [B, 3] and to (sigma, R, b) [3], and the Jacobians
+    [B, 3, 6] if asked (three sweeps per point)."""
+    B = len(x0s)
+    arr = _strings(x0s)
     gv = np.ascontiguousarray(np.asarray(g, np.float64).reshape(B, 3))
     gx = np.zeros((B, 3), np.float64)
     gp = np.zeros(3, np.float64)
     J = np.zeros((B, 3, 6), np.float64) if with_jacobian else None
     _check(lib().mpt_backward(int(B), int(L), int(N), int(nsteps), str(tau).encode(), str(sigma).encode(),
                               str(R).encode(), str(b).encode(), ctypes.cast(arr, ctypes.c_void_p), _ptr(gv),
-                              int(h_digits), _ptr(gx), _ptr(gp), _ptr(J) if J is not None else None,
+                              int(checkpoint_every), _ptr(gx), _ptr(gp), _ptr(J) if J is not None else None,
                               ctypes.c_uint64(int(stream))))
     return gx, gp, J
+
+
+def backward_raw(par, states, gbar, G: int, L: int, N: int, nsteps: int, checkpoint_every: int = 50,
+                 stream: int = 0):
+    """``mpt_backward_raw``: par = (signs[4], exps[4], limbs[4, L]) for sigma,
+    R, b, tau; states = (signs[3B], exps[3B], limbs[3B, L]); gbar = the
+    adjoints of the final states, 3 B G numbers (item j G + g belongs to
+    trajectory j).  Returns (the adjoints of the initial states, the adjoints
+    of (sigma, R, b)), 3 B G numbers each, in the interchange layout."""
+    ps, pe, pl = (np.ascontiguousarray(x) for x in (par[0], par[1], par[2]))
+    ss, se, sl = (np.ascontiguousarray(x) for x in (states[0], states[1], states[2]))
+    B = len(ss) // 3
+    gs = np.ascontiguousarray(np.asarray(gbar[0], np.int32).copy())
+    ge = np.ascontiguousarray(np.asarray(gbar[1], np.int32).copy())
+    gl = np.ascontiguousarray(np.asarray(gbar[2], np.uint32).reshape(-1, L).copy())
+    if len(gs) != 3 * B * G or len(ps) != 4:
+        raise ValueError("gbar needs 3 B G numbers and par 4")
+    ts = np.zeros(3 * B * G, np.int32)
+    te = np.zeros(3 * B * G, np.int32)
+    tl = np.zeros((3 * B * G, L), np.uint32)
+    _check(lib().mpt_backward_raw(int(B), int(G), int(L), int(N), int(nsteps), int(checkpoint_every),
+                                  _ptr(np.asarray(ps, np.int32)), _ptr(np.asarray(pe, np.int32)),
+                                  _ptr(np.asarray(pl, np.uint32)), _ptr(np.asarray(ss, np.int32)),
+                                  _ptr(np.asarray(se, np.int32)), _ptr(np.asarray(sl, np.uint32)),
+                                  _ptr(gs), _ptr(ge), _ptr(gl), _ptr(ts), _ptr(te), _ptr(tl),
+                                  ctypes.c_uint64(int(stream))))
+    return (gs, ge, gl), (ts, te, tl)
+
+
+def jacobian_fd(x0s, L: int, N: int, nsteps: int, tau: str = "0.01", sigma: str = "10", R: str = "28",
+                b: str = "8/3", h_digits: int = 100, stream: int = 0):
+    """``mpt_jacobian_fd``: the 3 x 6 Jacobians [B, 3, 6] by central
+    differences (h = 10^-h_digits) of bit-exact runs."""
+    B = len(x0s)
+    arr = _strings(x0s)
+    J = np.zeros((B, 3, 6), np.float64)
+    _check(lib().mpt_jacobian_fd(int(B), int(L), int(N), int(nsteps), str(tau).encode(), str(sigma).encode(),
+                                 str(R).encode(), str(b).encode(), ctypes.cast(arr, ctypes.c_void_p),
+                                 int(h_digits), _ptr(J), ctypes.c_uint64(int(stream))))
+    return J
 
 
 def int_peak(variant: int, iters: int = 20000, threads: int = 1024):

@@ -113,7 +113,7 @@ def test_flow_jacobian_at_300_digits(mpt):
     ens = workloads.perturbed_ensemble(2, seed=19080931, fixed_digits=300)
     assert ens[0].L == L
     x0s = [t.x0 for t in ens]
-    _, J = grad.flow_jacobian(x0s, L=L, N=N, nsteps=steps, h=h, with_value=False)
+    _, J = grad.flow_jacobian(x0s, L=L, N=N, nsteps=steps, h=h, with_value=False, method="fd")
     par = ("10", "28", "8/3")
     jobs = []
     with cf.ThreadPoolExecutor(O.default_threads()) as ex:

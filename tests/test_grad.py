@@ -131,7 +131,7 @@ def test_library_jacobian_equals_oracle_central_differences(gpu):
     L, N, steps = 9, 10, 4
     h = Fraction(1, 10 ** 25)
     x0s = [O.X0, ("1.5", "-2.25", "20.125")]
-    F, J = gpu.flow_jacobian(x0s, tau="0.01", L=L, N=N, nsteps=steps, h=h)
+    F, J = gpu.flow_jacobian(x0s, tau="0.01", L=L, N=N, nsteps=steps, h=h, method="fd")
     tau = Fraction(1, 100)
     par = [O.parse_rational(v) for v in (O.SIGMA, O.R, O.B)]
     for b, x0 in enumerate(x0s):
@@ -152,17 +152,24 @@ def test_autograd_wrapper_passes_gradcheck(gpu):
 
 
 @pytest.mark.gpu
-def test_c_abi_backward_equals_the_python_differences(gpu):
+def test_reverse_sweep_agrees_with_central_differences(gpu):
+    """The reverse sweep's Jacobians and g^T J (mpt_backward) agree with the
+    central differences of bit-exact runs (mpt_jacobian_fd) to far below
+    float64 resolution; both approximate the derivative of the
+    exact-arithmetic order-N map."""
     from paper_1908_09301_gb300 import mpt
     L, N, steps = 9, 10, 4
     x0s = [O.X0, ("1.5", "-2.25", "20.125"), ("0.1", "-0.2", "0.3")]
     g = np.array([[1.0, -2.0, 0.5], [0.25, 0.0, 3.0], [-1.0, 1.0, 1.0]])
-    gx, gp, J = mpt.backward(x0s, g, L, N, steps, h_digits=25, with_jacobian=True)
-    _, Jp = gpu.flow_jacobian(x0s, L=L, N=N, nsteps=steps, h=Fraction(1, 10 ** 25), with_value=False)
-    assert np.array_equal(J, Jp)  # C++ and Python differences: both exact, rounded once
+    gx, gp, J = mpt.backward(x0s, g, L, N, steps, checkpoint_every=3, with_jacobian=True)
+    Jfd = mpt.jacobian_fd(x0s, L, N, steps, h_digits=25)
+    assert np.allclose(J, Jfd, rtol=1e-13, atol=1e-13 * np.abs(Jfd).max())
     want = np.einsum("bi,bij->bj", g, J)
     assert np.allclose(gx, want[:, :3], rtol=1e-15, atol=0)
     assert np.allclose(gp, want[:, 3:].sum(0), rtol=1e-14, atol=0)
+    gx1, gp1, _ = mpt.backward(x0s, g, L, N, steps, checkpoint_every=3)
+    assert np.allclose(gx1, gx, rtol=1e-13, atol=1e-13 * np.abs(gx).max())
+    assert np.allclose(gp1, gp, rtol=1e-13, atol=1e-13 * np.abs(gp).max())
 
 
 @pytest.mark.gpu
@@ -171,4 +178,8 @@ def test_c_abi_backward_rejects_bad_input(gpu):
     with pytest.raises(mpt.MPTError):
         mpt.backward([("1", "2", "x")], np.zeros((1, 3)), 5, 6, 1)
     with pytest.raises(mpt.MPTError):
-        mpt.backward([("1", "2", "3")], np.zeros((1, 3)), 5, 6, 1, h_digits=20000)
+        mpt.jacobian_fd([("1", "2", "3")], 5, 6, 1, h_digits=20000)
+    with pytest.raises(mpt.MPTError):
+        mpt.backward([("1", "2", "3")], np.zeros((1, 3)), 5, 6, 1, checkpoint_every=-1)
+    with pytest.raises(mpt.MPTError):
+        mpt.backward([("1", "2", "3")], np.array([[np.inf, 0.0, 0.0]]), 5, 6, 1)
