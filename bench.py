@@ -22,7 +22,7 @@ Other lines, each a JSON line of the same form:
 
   python bench.py --ensemble B        B trajectories of the perturbed ensemble in one batch
   python bench.py --system NAME       a general quadratic system (roessler, chen, lorenz)
-  python bench.py --grad B            3x6 flow Jacobians of B trajectories (central differences)
+  python bench.py --grad B            derivatives of B trajectories by the reverse sweep
 """
 from __future__ import annotations
 
@@ -408,70 +408,98 @@ def system_bench(args):
 
 
 def grad_bench(args):
-    """Jacobians of the n-step map with respect to (x0, sigma, R, b) for B
+    """Derivatives of the n-step map with respect to (x0, sigma, R, b) for B
     trajectories (300 digits, N = 150, 500 steps, tau = 0.01: Sec. 5's point
-    plus seeded 1e-20 perturbations), by multiple-precision central
-    differences: 13 bit-exact runs a trajectory, all in one batch launch."""
+    plus seeded 1e-20 perturbations, seed 19080931), by the reverse sweep
+    (mpt_backward, checkpoints every 50 steps): one adjoint vector per
+    trajectory (the gradient of a scalar of the final states), and the full
+    3 x 6 Jacobians (three sweeps a trajectory).  Its cost is compared with
+    one forward run of the same trajectories (mpt_integrate_batch), and its
+    gradients with central differences (h = 1e-100) of bit-exact runs on a
+    few of the trajectories."""
     import numpy as np
     import torch
 
-    from paper_1908_09301_gb300 import grad, mpt
+    from paper_1908_09301_gb300 import mpt
 
     torch.cuda.set_device(0)
-    B, K, N, steps = args.grad, 300, 150, args.grad_steps
+    B, K, N, steps, every = args.grad, 300, 150, args.grad_steps, 50
     L = mpt.limbs_for_digits(K)
-    ens = WL.perturbed_ensemble(B)
+    ens = WL.perturbed_ensemble(B, seed=19080931, fixed_digits=K)
     x0s = [t.x0 for t in ens]
-    grad.flow_jacobian(x0s[:2], L=L, N=N, nsteps=2)  # warm-up (module load, first launches)
+    rng = np.random.default_rng(19080931)
+    g = rng.standard_normal((B, 3))
+    states = [tuple(zip(*(mpt.parse_number(v, L) for v in x))) for x in x0s]
+    # warm-up (module load, first launches)
+    mpt.integrate_batch([L] * 2, [N] * 2, 2, states[:2])
+    mpt.backward(x0s[:2], g[:2], L, N, 2, checkpoint_every=every)
     torch.cuda.synchronize()
     sampler = ClockSampler(0)
     t0 = time.perf_counter()
-    F, J = grad.flow_jacobian(x0s, L=L, N=N, nsteps=steps)
+    mpt.integrate_batch([L] * B, [N] * B, steps, states)
     torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    t_fwd = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    gx, gp, _ = mpt.backward(x0s, g, L, N, steps, checkpoint_every=every)
+    torch.cuda.synchronize()
+    t_vjp = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    _, _, J = mpt.backward(x0s, g, L, N, steps, checkpoint_every=every, with_jacobian=True)
+    torch.cuda.synchronize()
+    t_jac = time.perf_counter() - t0
     clocks = sampler.stop()
-    runs = 13 * B
-    work = runs * steps * L * L * (N * (N + 1) + 7 * N)
+    # central differences of a few trajectories, as a check
+    nfd = min(B, args.grad_check)
+    Jfd = mpt.jacobian_fd(x0s[:nfd], L, N, steps, h_digits=100)
+    rel = float(np.max(np.abs(J[:nfd] - Jfd) / np.maximum(np.abs(Jfd), 1e-300)))
+    vjp_rel = float(np.max(np.abs(gx[:nfd] - np.einsum("bi,bij->bj", g[:nfd], Jfd)[:, :3])
+                           / np.maximum(np.abs(gx[:nfd]), 1e-300)))
+    work_fwd = B * steps * L * L * (N * (N + 1) + 7 * N)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = sms * IMAD_PER_SM_CLK / 2 * sm_max * 1e6
-    nbytes = runs * (12 + 12 * L)
+    # limb products of the sweep: the forward pass, the recomputation and the
+    # reverse sweep (twice the Cauchy products of a forward step, the powers
+    # of tau and the parameter sums)
+    work_vjp = 2 * work_fwd + B * steps * L * L * (2 * N * (N + 1) + 9 * N)
+    nbytes = B * (12 + 12 * L) + B * 3 * 8
     line = {
-        "metric": "3x6 Jacobians/sec of the n-step map w.r.t. (x0, sigma, R, b), float64 from "
-                  "multiple-precision central differences",
-        "value": B / dt, "unit": "Jacobians/s", "n_gpus": 1, "steps": steps, "warmup": 1,
-        "ms_per_step": dt / steps * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "metric": "gradients/sec of a scalar of the final states w.r.t. (x0, sigma, R, b), float64 from the "
+                  "multiple-precision reverse sweep",
+        "value": B / t_vjp, "unit": "gradients/s", "n_gpus": 1, "steps": steps, "warmup": 1,
+        "ms_per_step": t_vjp / steps * 1000.0, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32",
-        "data": "synthetic (Sec. 5 point plus seeded 1e-20 perturbations, exact rationals)",
-        "config": {"workload": f"jacobians_{B}_k{K}_n{N}_{steps}steps", "trajectories": B,
-                   "K_digits": K, "L_limbs": L, "N_order": N, "tau": "0.01", "h": "1e-100",
-                   "runs_per_trajectory": 13, "timing": "wall time of grad.flow_jacobian (one "
-                   "mpt_integrate_batch_params call, states from and to host memory, exact differences "
-                   "on the host)"},
-        "gpu_launches": 1,
-        "limb_macs": work,
-        "roofline": {"bound": "alu", "achieved": work / dt, "peak": peak, "unit": "limb-MAC/s",
-                     "frac": work / dt / peak, "traffic": None,
+        "data": "synthetic (Sec. 5 point plus seeded 1e-20 perturbations, exact rationals; seeded normal g)",
+        "config": {"workload": f"adjoint_{B}_k{K}_n{N}_{steps}steps", "trajectories": B, "K_digits": K,
+                   "L_limbs": L, "N_order": N, "tau": "0.01", "checkpoint_every": every,
+                   "timing": "wall time of one mpt_backward call (inputs from and outputs to host memory)"},
+        "forward_run_equivalents": t_vjp / t_fwd,
+        "forward_s": t_fwd, "vjp_s": t_vjp,
+        "jacobians": {"value": B / t_jac, "unit": "Jacobians/s", "seconds": t_jac,
+                      "forward_run_equivalents": t_jac / t_fwd, "sweeps_per_trajectory": 3},
+        "check_vs_central_differences": {"trajectories": nfd, "h": "1e-100",
+                                         "max_rel_diff_jacobian": rel, "max_rel_diff_gradient": vjp_rel},
+        "gpu_launches": int(2 * ((steps + every - 1) // every) + (steps + every - 1) // every),
+        "limb_macs": work_vjp,
+        "roofline": {"bound": "alu", "achieved": work_vjp / t_vjp, "peak": peak, "unit": "limb-MAC/s",
+                     "frac": work_vjp / t_vjp / peak, "traffic": None,
                      "peak_source": (f"derived: {sms} SMs x {IMAD_PER_SM_CLK} INT32 multiply-adds "
                                      f"per SM per clock / 2 per limb product x {sm_max:.0f} MHz")},
-        "e2e": {"value": B / dt, "unit": "Jacobians/s", "h2d_bytes_per_step": int(nbytes / steps),
-                "d2h_bytes_per_step": int(nbytes / steps)},
+        "e2e": {"value": B / t_vjp, "unit": "gradients/s", "h2d_bytes_per_step": int(nbytes / steps),
+                "d2h_bytes_per_step": int(B * 6 * 8 / steps)},
         "clocks": clocks,
-        "check": {"J_finite": bool(np.isfinite(J).all()), "J_abs_max": float(np.abs(J).max())},
     }
     if not args.no_cpu_baseline:
         from oracle import oracle as O
-        nth = O.default_threads()
         cs = args.cpu_steps_grad
-        p, st = O.params(L), O.state(L, x0s[0])
         t1 = time.perf_counter()
-        O.integrate(L, N, cs, p, st, nthreads=nth)
+        O.backward(L, N, cs, O.params(L), O.state(L, x0s[0]), O.MPArray.from_values(["1", "0", "0"], L))
         dc = time.perf_counter() - t1
-        line["cpu_baseline"] = {"value": 1.0 / (13 * steps * dc / cs), "unit": "Jacobians/s", "cores": nth,
+        line["cpu_baseline"] = {"value": 1.0 / (steps * dc / cs), "unit": "gradients/s", "cores": 1,
                                 "kind": "oracle",
-                                "sample": f"{cs} steps of one run (L = {L}, N = {N}, {dc:.1f} s), scaled "
-                                          f"to the 13 x {steps} steps of one Jacobian"}
+                                "sample": f"forward and reverse sweep of {cs} steps of one trajectory "
+                                          f"(L = {L}, N = {N}, {dc:.1f} s), scaled to {steps} steps"}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -494,7 +522,8 @@ def main():
     ap.add_argument("--sys-n", type=int, default=1000, help="order of --system")
     ap.add_argument("--sys-cpu-n", type=int, default=150, help="oracle indices for its cpu_baseline")
     ap.add_argument("--grad", type=int, default=0,
-                    help="instead of the headline: Jacobians of B trajectories (300 digits, N = 150)")
+                    help="instead of the headline: derivatives of B trajectories (300 digits, N = 150)")
+    ap.add_argument("--grad-check", type=int, default=4, help="trajectories checked by central differences")
     ap.add_argument("--grad-steps", type=int, default=500, help="steps of the map for --grad")
     ap.add_argument("--cpu-steps-grad", type=int, default=20, help="oracle steps for --grad's cpu_baseline")
     args = ap.parse_args()
