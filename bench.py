@@ -227,17 +227,21 @@ def config_of(wl):
 
 def ensemble_bench(args):
     """B trajectories of the perturbed ensemble (K in {200, 400, 800} digits,
-    N = 0.6 K, Sec. 5's point plus 1e-20 perturbations) through one
-    mpt_integrate_batch call of ``steps`` steps, states from and to host
-    memory; against the same trajectories solved one at a time (a timed sample
-    of each K, scaled to the batch)."""
+    N = 0.6 K, Sec. 5's point plus 1e-20 perturbations) through
+    mpt_integrate_batch_shape, ``--ens-steps`` steps in one launch, states from
+    and to host memory: with the library's default shape and with the shape
+    the autotuner picks for this workload (timed on a sample of it; the
+    tuning time is reported apart); against the same trajectories solved one
+    at a time (a timed sample of each K, scaled to the ensemble)."""
     import torch
 
+    from paper_1908_09301_gb300 import autotune as AT
     from paper_1908_09301_gb300 import mpt
 
     torch.cuda.set_device(0)
     ens = WL.perturbed_ensemble(args.ensemble)
     Ls, Ns = [t.L for t in ens], [t.N for t in ens]
+    steps = args.ens_steps
     states = []
     for t in ens:
         s, e, l = zip(*(mpt.parse_number(v, t.L) for v in t.x0))
@@ -245,13 +249,25 @@ def ensemble_bench(args):
     work = sum(t.L * t.L * (t.N * (t.N + 1) + 7 * t.N) for t in ens)  # limb products per step
     mpt.integrate_batch(Ls, Ns, 1, states)  # warm-up (module load, first launch)
     torch.cuda.synchronize()
-    sampler = ClockSampler(0)
     t0 = time.perf_counter()
-    mpt.integrate_batch(Ls, Ns, args.steps, states)
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    tuned = AT.tune_batch(Ls, Ns, states, steps=1, force=args.retune)
+    t_tune = time.perf_counter() - t0
+    shape = tuple(tuned["shape"])
+
+    def timed(sh):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        out = mpt.integrate_batch(Ls, Ns, steps, states, shape=sh)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t1, out
+
+    sampler = ClockSampler(0)
+    dt_default, out_default = timed((0, 0, 0))
+    dt, out = timed(shape)
     clocks = sampler.stop()
-    value = len(ens) * args.steps / dt
+    import numpy as np
+    same = all(np.array_equal(x, y) for a, b in zip(out, out_default) for x, y in zip(a, b))
+    value = len(ens) * steps / dt
     # the same trajectories one at a time: one trajectory of each K, timed
     single_ms = {}
     for K in sorted({t.K for t in ens}):
@@ -263,36 +279,43 @@ def ensemble_bench(args):
             t1 = time.perf_counter()
             c.integrate(2)
             single_ms[K] = (time.perf_counter() - t1) / 2 * 1000.0
-    one_at_a_time_s = sum(single_ms[t.K] for t in ens) * args.steps / 1000.0
+    one_at_a_time_s = sum(single_ms[t.K] for t in ens) * steps / 1000.0
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = sms * IMAD_PER_SM_CLK / 2 * sm_max * 1e6
-    achieved = work * args.steps / dt
+    achieved = work * steps / dt
     mix = {K: sum(1 for t in ens if t.K == K) for K in sorted({t.K for t in ens})}
+    state_bytes = int(sum(12 + 12 * t.L for t in ens))
     line = {
         "metric": "trajectory-steps/sec of a perturbed ensemble (bit-exact)", "value": value,
-        "unit": "trajectory-steps/s", "n_gpus": 1, "steps": args.steps, "warmup": 1,
-        "ms_per_step": dt / args.steps * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "unit": "trajectory-steps/s", "n_gpus": 1, "steps": steps, "warmup": 1,
+        "ms_per_step": dt / steps * 1000.0, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (Sec. 5 point plus seeded 1e-20 perturbations, exact rationals)",
         "config": {"workload": f"perturbed_ensemble_{len(ens)}", "trajectories": len(ens),
-                   "digits_mix": mix, "N": "0.6 K", "timing": "wall time of one mpt_integrate_batch "
-                   "call (states from and to host memory)"},
+                   "digits_mix": mix, "N": "0.6 K",
+                   "timing": f"wall time of one mpt_integrate_batch_shape call of {steps} steps (states "
+                             f"from and to host memory: {state_bytes} bytes each way)"},
+        "shape": {"chosen": {"variant": shape[0], "tb": shape[1], "nwin": shape[2]},
+                  "default_trajectory_steps_per_s": len(ens) * steps / dt_default,
+                  "same_bits_as_default": same, "tuning_s": t_tune,
+                  "tuned_on": f"{tuned['sample']} trajectories of the workload, 1 step per shape",
+                  "tried": tuned["tried"]},
         "gpu_launches": 1,
         "limb_macs_per_step": work,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "limb-MAC/s",
                      "frac": achieved / peak, "traffic": None,
                      "peak_source": (f"derived: {sms} SMs x {IMAD_PER_SM_CLK} INT32 multiply-adds "
                                      f"per SM per clock / 2 per limb product x {sm_max:.0f} MHz")},
-        "one_at_a_time": {"value": len(ens) * args.steps / one_at_a_time_s,
+        "one_at_a_time": {"value": len(ens) * steps / one_at_a_time_s,
                           "unit": "trajectory-steps/s",
                           "ms_per_step_by_digits": {str(k): round(v, 3) for k, v in single_ms.items()},
                           "sample": "one trajectory of each K through the context API, 2 steps, "
-                                    "scaled to the ensemble"},
+                                    "scaled to the ensemble (an extrapolation)"},
         "e2e": {"value": value, "unit": "trajectory-steps/s",
-                "h2d_bytes_per_step": int(sum(12 + 12 * t.L for t in ens) / args.steps),
-                "d2h_bytes_per_step": int(sum(12 + 12 * t.L for t in ens) / args.steps)},
+                "h2d_bytes_per_step": int(state_bytes / steps),
+                "d2h_bytes_per_step": int(state_bytes / steps)},
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
@@ -516,6 +539,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="instead of the headline: B trajectories of the perturbed ensemble")
+    ap.add_argument("--ens-steps", type=int, default=10, help="steps of the --ensemble launch")
+    ap.add_argument("--retune", action="store_true", help="--ensemble: tune again, ignoring the cache")
     ap.add_argument("--system", default="", choices=["", "lorenz", "roessler", "chen"],
                     help="instead of the headline: a general quadratic system")
     ap.add_argument("--sys-k", type=int, default=2000, help="digits of --system")

@@ -166,6 +166,13 @@ int mpt_set_launch(mpt_ctx *ctx, int ctas);
 int mpt_get_launch(const mpt_ctx *ctx, int *ctas);
 
 /*
+ * Terms a worker CTA of the pipelined kernel stages per batch (1 .. the
+ * largest that fits in shared memory; 0 = that largest, the default).
+ * Results do not depend on it; the autotuner searches it with the CTA count.
+ */
+int mpt_set_pipe_batch(mpt_ctx *ctx, int tb);
+
+/*
  * Kernel organisation (results are identical): 1 = lock-step (every CTA
  * takes a share of each index's products, grid barrier, every CTA closes the
  * brackets); 2 = pipelined (a CTA cluster closes the brackets and runs
@@ -266,6 +273,22 @@ int mpt_int_peak_run(int variant, int threads, int iters, double *mean_cycles, d
 int mpt_integrate_batch(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps,
                         const char *tau, const char *sigma, const char *R, const char *b,
                         int32_t *signs, int32_t *exps, uint32_t *limbs, uint64_t cuda_stream);
+
+/*
+ * The same batch with a launch shape of the caller's choosing (results are
+ * identical for every shape: the sums are exact).  shape[3] (host; null =
+ * the library's choice): the kernel variant (0: registers capped so that two
+ * trajectories share an SM; 1: not capped, one trajectory an SM), the terms
+ * staged per batch (0: as many as fit, up to 64; else 1..256), the copies of
+ * the accumulator windows the products add into (0: as many as fit, up to
+ * 8; else 1..8).  MPT_EINVAL for a value outside these ranges or a shape
+ * whose shared memory does not fit.  The project's autotuner picks shapes
+ * per workload with it (paper_1908_09301_gb300/autotune.py).
+ */
+int mpt_integrate_batch_shape(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps,
+                              const char *tau, const char *sigma, const char *R, const char *b,
+                              int32_t *signs, int32_t *exps, uint32_t *limbs, const int32_t *shape,
+                              uint64_t cuda_stream);
 
 /*
  * The same batch with parameters of each trajectory's own: sigma[j], R[j],

@@ -90,6 +90,7 @@ struct mpt_ctx {
     int pipe_C = 10;            // CTAs with fixed roles in the pipelined kernel (fixed by the kernel)
     int pipe_max_grid = 0;      // co-resident CTAs of the pipelined kernel
     int pipe_tb = 0;
+    int pipe_tb_fit = 0;        // the largest worker batch that fits (mpt_set_pipe_batch 0)
     size_t pipe_smem = 0;
     unsigned *pub = nullptr, *done = nullptr;
     long long *gin = nullptr;
@@ -347,6 +348,7 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
         while (ptb > 1 && mpt::pipe_smem_bytes(L, c->Lp, c->N, c->Wcap, ptb) > (size_t)smem_optin)
             ptb--;
         c->pipe_tb = ptb;
+        c->pipe_tb_fit = ptb;
         c->pipe_smem = mpt::pipe_smem_bytes(L, c->Lp, c->N, c->Wcap, ptb);
         c->pipe_C = mpt::pipe_fixed_ctas();
         c->pipe_max_grid = 0;
@@ -490,6 +492,27 @@ int mpt_set_launch(mpt_ctx *c, int ctas)
     if (ctas < 0 || ctas > c->sms)
         return fail(MPT_EINVAL, "ctas = %d outside 0..%d", ctas, c->sms);
     c->ctas_req = ctas;
+    return MPT_OK;
+}
+
+int mpt_set_pipe_batch(mpt_ctx *c, int tb)
+{
+    if (!c) return fail(MPT_EINVAL, "null context");
+    if (tb < 0 || tb > c->pipe_tb_fit)
+        return fail(MPT_EINVAL, "worker batch %d outside 0..%d", tb, c->pipe_tb_fit);
+    const int t = tb ? tb : c->pipe_tb_fit;
+    const size_t sm = mpt::pipe_smem_bytes(c->L, c->Lp, c->N, c->Wcap, t);
+    DeviceGuard g(c->dev);
+    if (c->pending) {
+        int rc = wait_steps(c);
+        if (rc) return rc;
+    }
+    const int grid = mpt::pipe_max_ctas(sm);
+    (void)cudaGetLastError();
+    if (grid < c->pipe_C + 1) return fail(MPT_EINVAL, "worker batch %d leaves too few co-resident CTAs", tb);
+    c->pipe_tb = t;
+    c->pipe_smem = sm;
+    c->pipe_max_grid = grid;
     return MPT_OK;
 }
 
@@ -862,10 +885,18 @@ namespace {
 
 // the batch, with the parameters (sigma, R, b) of trajectory j at sig[j * per],
 // Rr[j * per], bb[j * per] (per = 0: one set for all)
+// shape (nullable): {kernel variant (0: registers capped, two CTAs an SM; 1:
+// not), terms per staging batch (0: as many as fit, up to 64), window copies
+// (0: as many as fit, up to 8)}
 int batch_impl(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, const char *tau,
                const char *const *sig, const char *const *Rr, const char *const *bb, int per,
-               int32_t *signs, int32_t *exps, uint32_t *limbs, uint64_t cuda_stream)
+               int32_t *signs, int32_t *exps, uint32_t *limbs, uint64_t cuda_stream,
+               const int32_t *shape = nullptr)
 {
+    const int variant = shape ? shape[0] : 0, tb_req = shape ? shape[1] : 0, nwin_req = shape ? shape[2] : 0;
+    if (variant < 0 || variant > 1) return fail(MPT_EINVAL, "kernel variant %d is neither 0 nor 1", variant);
+    if (tb_req < 0 || tb_req > 256) return fail(MPT_EINVAL, "staging batch %d outside 0..256", tb_req);
+    if (nwin_req < 0 || nwin_req > 8) return fail(MPT_EINVAL, "window copies %d outside 0..8", nwin_req);
     if (B < 1) return fail(MPT_EINVAL, "batch size %d < 1", B);
     if (!Ls || !Ns || !signs || !exps || !limbs || !sig || !Rr || !bb)
         return fail(MPT_EINVAL, "null argument");
@@ -971,13 +1002,17 @@ int batch_impl(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, cons
     if (ce != cudaSuccess) return cuda_fail(ce, "device query");
     for (int j = 0; j < B; j++) {
         Traj &t = T[j];
-        int tb = 64;
-        while (tb > 8 && mpt::smem_bytes(t.L, t.Lp, t.N, t.Wcap, tb) > (size_t)smem_optin) tb /= 2;
+        int tb = tb_req ? tb_req : 64;
+        if (!tb_req)
+            while (tb > 8 && mpt::smem_bytes(t.L, t.Lp, t.N, t.Wcap, tb) > (size_t)smem_optin) tb /= 2;
         t.tb = tb;
-        // window copies (up to 8) while two CTAs still share an SM
+        // window copies (up to 8) while two CTAs still share an SM (the capped
+        // variant) or while one fits (the other)
         const size_t two = smem_sm > 2048 ? (size_t)smem_sm / 2 - 1024 : 0;
-        int nwin = 8;
-        while (nwin > 1 && mpt::smem_bytes(t.L, t.Lp, t.N, t.Wcap, tb, nwin) > two) nwin /= 2;
+        const size_t budget = variant == 1 ? (size_t)smem_optin : two;
+        int nwin = nwin_req ? nwin_req : 8;
+        if (!nwin_req)
+            while (nwin > 1 && mpt::smem_bytes(t.L, t.Lp, t.N, t.Wcap, tb, nwin) > budget) nwin /= 2;
         t.nwin = nwin;
         const size_t sm = mpt::smem_bytes(t.L, t.Lp, t.N, t.Wcap, tb, nwin);
         if (sm > (size_t)smem_optin)
@@ -1070,7 +1105,7 @@ int batch_impl(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, cons
     if (ce == cudaSuccess) ce = cudaMemsetAsync(bar, 0, sizeof(unsigned) * 2, st);
     if (ce == cudaSuccess)
         ce = cudaMemcpyAsync(dargs, hargs.data(), sizeof(mpt::KArgs) * B, cudaMemcpyHostToDevice, st);
-    if (ce == cudaSuccess) ce = mpt::launch_batch(dargs, B, smem, st);
+    if (ce == cudaSuccess) ce = mpt::launch_batch(dargs, B, smem, st, variant);
     int hstatus = 0;
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&hstatus, status, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(hstL.data(), stL, sizeof(uint32_t) * n_st, cudaMemcpyDeviceToHost, st);
@@ -1104,6 +1139,14 @@ int mpt_integrate_batch(int B, const int32_t *Ls, const int32_t *Ns, int64_t nst
                         int32_t *exps, uint32_t *limbs, uint64_t cuda_stream)
 {
     return batch_impl(B, Ls, Ns, nsteps, tau, &sigma, &R, &b, 0, signs, exps, limbs, cuda_stream);
+}
+
+int mpt_integrate_batch_shape(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps,
+                              const char *tau, const char *sigma, const char *R, const char *b,
+                              int32_t *signs, int32_t *exps, uint32_t *limbs, const int32_t *shape,
+                              uint64_t cuda_stream)
+{
+    return batch_impl(B, Ls, Ns, nsteps, tau, &sigma, &R, &b, 0, signs, exps, limbs, cuda_stream, shape);
 }
 
 int mpt_integrate_batch_params(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps,

@@ -144,7 +144,8 @@ cudaError_t launch_integrate(const KArgs &a, int grid, size_t smem, cudaStream_t
 // largest co-resident grid for this smem size (0 on error)
 int max_coresident_ctas(size_t smem);
 // independent trajectories: CTA j runs the lock-step kernel for args[j] (device
-// array of B argument blocks, each with vG = 1, vg = 0)
-cudaError_t launch_batch(const KArgs *args, int B, size_t smem, cudaStream_t st);
+// array of B argument blocks, each with vG = 1, vg = 0); variant 0 caps the
+// registers so that two CTAs share an SM, variant 1 does not (one CTA an SM)
+cudaError_t launch_batch(const KArgs *args, int B, size_t smem, cudaStream_t st, int variant = 0);
 
 }  // namespace mpt

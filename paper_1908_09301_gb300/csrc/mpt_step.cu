@@ -1441,8 +1441,19 @@ __global__ void __launch_bounds__(NT, 1) taylor_kernel(KArgs a)
     taylor_body<false>(a, smem_raw);
 }
 
-// one trajectory per CTA: its own argument block, a grid of one
+// one trajectory per CTA: its own argument block, a grid of one; registers
+// capped so that two CTAs share an SM
 __global__ void __launch_bounds__(NT, 2) taylor_batch_kernel(const KArgs *args)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ KArgs a;
+    if (threadIdx.x == 0) a = args[blockIdx.x];
+    __syncthreads();
+    taylor_body<true>(a, smem_raw);
+}
+
+// the same without the register cap (one CTA an SM, no spills)
+__global__ void __launch_bounds__(NT, 1) taylor_batch_kernel_wide(const KArgs *args)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ KArgs a;
@@ -1490,8 +1501,15 @@ int max_coresident_ctas(size_t smem)
     return per * sms;
 }
 
-cudaError_t launch_batch(const KArgs *args, int B, size_t smem, cudaStream_t st)
+cudaError_t launch_batch(const KArgs *args, int B, size_t smem, cudaStream_t st, int variant)
 {
+    if (variant == 1) {
+        cudaError_t e = cudaFuncSetAttribute(taylor_batch_kernel_wide,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        taylor_batch_kernel_wide<<<B, NT, smem, st>>>(args);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaFuncSetAttribute(taylor_batch_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

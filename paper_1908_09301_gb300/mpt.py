@@ -50,6 +50,10 @@ SIGNATURES = {
     "mpt_get_profile": (ctypes.c_int, [vp, vp, ctypes.c_int]),
     "mpt_wait": (ctypes.c_int, [vp]),
     "mpt_set_exact": (ctypes.c_int, [vp, ctypes.c_int]),
+    "mpt_set_pipe_batch": (ctypes.c_int, [vp, ctypes.c_int]),
+    "mpt_integrate_batch_shape": (ctypes.c_int, [ctypes.c_int, vp, vp, ctypes.c_int64, ctypes.c_char_p,
+                                                 ctypes.c_char_p, ctypes.c_char_p, ctypes.c_char_p, vp, vp,
+                                                 vp, vp, ctypes.c_uint64]),
     "mpt_get_counters": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "mpt_set_launch": (ctypes.c_int, [vp, ctypes.c_int]),
     "mpt_get_launch": (ctypes.c_int, [vp, ctypes.POINTER(ctypes.c_int)]),
@@ -260,6 +264,11 @@ class Context:
         """Every launch with all products in full (``mpt_set_exact``)."""
         _check(lib().mpt_set_exact(self._h, int(bool(on))))
 
+    def set_pipe_batch(self, tb: int):
+        """Worker terms per staged batch of the pipelined kernel (0 = the
+        largest that fits) (``mpt_set_pipe_batch``)."""
+        _check(lib().mpt_set_pipe_batch(self._h, int(tb)))
+
     def counters(self):
         """(full reruns so far, limb-product chunks of the last launch)
         (``mpt_get_counters``)."""
@@ -349,13 +358,15 @@ def integrate_noalloc(L: int, N: int, nsteps: int, params, state, stream: int | 
 
 
 def integrate_batch(Ls, Ns, nsteps: int, states, tau: str = "0.01", sigma="10",
-                    R="28", b="8/3", stream: int = 0):
+                    R="28", b="8/3", stream: int = 0, shape=None):
     """nsteps Taylor steps of B independent trajectories through
     ``mpt_integrate_batch``.  ``Ls``, ``Ns``: per-trajectory limbs and order;
     ``states``: per trajectory (signs[3], exps[3], limbs[3, L_j]) in the
     interchange layout (host).  ``sigma``, ``R``, ``b``: one string each, or a
-    list of B strings each (``mpt_integrate_batch_params``).  Returns the new
-    states in the same form."""
+    list of B strings each (``mpt_integrate_batch_params``).  ``shape``:
+    (kernel variant, terms per staging batch, window copies), see
+    ``mpt_integrate_batch_shape`` (one set of parameters only).  Returns the
+    new states in the same form."""
     B = len(Ls)
     if B != len(Ns) or B != len(states):
         raise ValueError("Ls, Ns and states must have the same length")
@@ -373,6 +384,12 @@ def integrate_batch(Ls, Ns, nsteps: int, states, tau: str = "0.01", sigma="10",
             int(B), _ptr(Lv), _ptr(Nv), int(nsteps), str(tau).encode(),
             *[ctypes.cast(a, ctypes.c_void_p) for a in arrs],
             _ptr(signs), _ptr(exps), _ptr(limbs), ctypes.c_uint64(int(stream))))
+    elif shape is not None:
+        sh = np.ascontiguousarray(np.asarray(shape, np.int32).reshape(3))
+        _check(lib().mpt_integrate_batch_shape(int(B), _ptr(Lv), _ptr(Nv), int(nsteps), str(tau).encode(),
+                                               str(sigma).encode(), str(R).encode(), str(b).encode(),
+                                               _ptr(signs), _ptr(exps), _ptr(limbs), _ptr(sh),
+                                               ctypes.c_uint64(int(stream))))
     else:
         _check(lib().mpt_integrate_batch(int(B), _ptr(Lv), _ptr(Nv), int(nsteps), str(tau).encode(),
                                          str(sigma).encode(), str(R).encode(), str(b).encode(),
