@@ -421,6 +421,59 @@ int from_double(double v, int L, int32_t *sign, int32_t *exp, uint32_t *limbs)
     return parse_number(str.c_str(), L, sign, exp, limbs);
 }
 
+// tau = trunc_L(p/q) with p/q in lowest terms, 0 < p < 2^32, 1 <= q < 2^16:
+// its limbs M = floor(p 2^k / q), k = 32 shift (shift = L - exp), so
+// M = (p 2^k - r) / q with r = p 2^k mod q.  Returns 0 with (p, q, r, shift,
+// neg), or -1 when tau is not such a ratio (or M differs, which cannot happen).
+int small_ratio(const char *str, int L, uint32_t *p, uint32_t *q, uint32_t *r, int *shift, int *neg)
+{
+    Rat t;
+    if (!parse_rational(str, t) || t.num.zero() || t.num.bits() > 64 || t.den.bits() > 64) return -1;
+    auto u64 = [](const BigU &a) {
+        uint64_t v = 0;
+        for (size_t i = a.w.size(); i-- > 0;) v = (v << 32) | a.w[i];
+        return v;
+    };
+    uint64_t a = u64(t.num), b = u64(t.den);
+    uint64_t x = a, y = b;
+    while (y) {
+        const uint64_t z = x % y;
+        x = y;
+        y = z;
+    }
+    a /= x;
+    b /= x;
+    if (a >= (1ull << 32) || b >= (1ull << 16)) return -1;
+    int32_t s = 0, e = 0;
+    std::vector<uint32_t> limbs((size_t)L);
+    if (parse_number(str, L, &s, &e, limbs.data())) return -1;
+    const long long sh = (long long)L - e;
+    if (sh < 0 || sh > (1LL << 20)) return -1;
+    uint64_t rem = a % b;
+    for (long long i = 0; i < sh; i++) rem = (rem << 32) % b;
+    // check M = (a 2^k - rem) / b limb for limb
+    BigU X;
+    X.w = {(uint32_t)a};
+    X.trim();
+    X.shl(32 * sh);
+    BigU R;
+    R.w = {(uint32_t)rem};
+    R.trim();
+    sub_inplace(X, R);
+    BigU D;
+    D.w = {(uint32_t)b};
+    const BigU M = divide(X, D);
+    if ((int)M.w.size() != L) return -1;
+    for (int j = 0; j < L; j++)
+        if (M.w[(size_t)j] != limbs[(size_t)j]) return -1;
+    *p = (uint32_t)a;
+    *q = (uint32_t)b;
+    *r = (uint32_t)rem;
+    *shift = (int)sh;
+    *neg = t.neg ? 1 : 0;
+    return 0;
+}
+
 // trunc_L of an exact decimal or rational string.  Returns 0, or -1 for a
 // malformed string, -3 for an exponent outside |exp| <= 2^30.
 int parse_number(const char *str, int L, int32_t *sign, int32_t *exp, uint32_t *limbs)

@@ -18,4 +18,8 @@ double diff_over_2h(int L, int32_t s1, int32_t e1, const uint32_t *l1, int32_t s
 double to_double(int L, int32_t s, int32_t e, const uint32_t *l);
 // trunc_L of the exact value of a finite double; 0, or -1 for inf / nan
 int from_double(double v, int L, int32_t *sign, int32_t *exp, uint32_t *limbs);
+// tau = trunc_L(p/q) with p/q in lowest terms, 0 < p < 2^32, 1 <= q < 2^16:
+// then its limbs are M = (p 2^k - r) / q, k = 32 shift, r = p 2^k mod q, and
+// tau h = (p h - r h 2^-k) / q exactly.  0 with (p, q, r, shift, neg), else -1.
+int small_ratio(const char *str, int L, uint32_t *p, uint32_t *q, uint32_t *r, int *shift, int *neg);
 }  // namespace mpt_host

@@ -108,6 +108,9 @@ struct mpt_ctx {
     bool last_exact = false;
     bool force_exact = false;      // mpt_set_exact: every launch in full
     long long exact_reruns = 0;
+    // tau as a small ratio p/q (tau_q = 0: not), for Horner steps without a limb product
+    uint32_t tau_p = 0, tau_q = 0, tau_r = 0;
+    int tau_shift = 0, tau_neg = 0;
     unsigned long long *chunks = nullptr;  // executed limb-product chunks of the last launch
 };
 
@@ -314,6 +317,8 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
                         strs[j]);
         }
     }
+    if (mpt_host::small_ratio(tau, L, &c->tau_p, &c->tau_q, &c->tau_r, &c->tau_shift, &c->tau_neg))
+        c->tau_q = 0;
     cudaError_t ce = cudaGetDevice(&c->dev);
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->dev);
     int smem_optin = 0;
@@ -677,6 +682,11 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
     a.ptau = c->sysT ? c->sys_npar : 3;
     a.exact = exact ? 1 : 0;
     a.chunks = c->chunks;
+    a.tau_p = c->tau_p;
+    a.tau_q = c->sysT ? 0 : c->tau_q;
+    a.tau_r = c->tau_r;
+    a.tau_shift = c->tau_shift;
+    a.tau_neg = c->tau_neg;
     if (c->prof) {
         ce = cudaMemsetAsync(c->prof, 0, sizeof(long long) * prof_len(c), c->st);
         if (ce != cudaSuccess) return cuda_fail(ce, "profile reset");
@@ -1060,6 +1070,21 @@ int batch_impl(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, cons
         return fail(ce == cudaErrorMemoryAllocation ? MPT_ENOMEM : MPT_ECUDA, "batch buffers: %s",
                     cudaGetErrorString(ce));
     }
+    // tau as a small ratio p/q at each L (Horner steps without a limb product)
+    struct TauRatio {
+        int L;
+        uint32_t p, q, r;
+        int shift, neg;
+    };
+    std::vector<TauRatio> ratios;
+    auto ratio_for = [&](int L) -> const TauRatio & {
+        for (const TauRatio &t : ratios)
+            if (t.L == L) return t;
+        TauRatio t{L, 0, 0, 0, 0, 0};
+        if (mpt_host::small_ratio(tau, L, &t.p, &t.q, &t.r, &t.shift, &t.neg)) t.q = 0;
+        ratios.push_back(t);
+        return ratios.back();
+    };
     // argument blocks, heaviest trajectories first (CTAs start in index order)
     std::vector<int> order(B);
     for (int j = 0; j < B; j++) order[j] = j;
@@ -1093,6 +1118,12 @@ int batch_impl(int B, const int32_t *Ls, const int32_t *Ns, int64_t nsteps, cons
         a.spin_limit = mpt::DEFAULT_SPIN_LIMIT;
         a.vG = 1;
         a.vg = 0;
+        const TauRatio tr = ratio_for(t.L);
+        a.tau_p = tr.p;
+        a.tau_q = tr.q;
+        a.tau_r = tr.r;
+        a.tau_shift = tr.shift;
+        a.tau_neg = tr.neg;
         hargs[i] = a;
     }
     ce = cudaMemcpyAsync(parL, hparL.data(), sizeof(uint32_t) * n_par, cudaMemcpyHostToDevice, st);

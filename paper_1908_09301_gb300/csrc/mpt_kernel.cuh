@@ -81,6 +81,11 @@ struct KArgs {
     const int32_t *fwdE, *fwdF;
     uint32_t *powL;
     int32_t *powE, *powF;
+    // tau = trunc_L(p/q) with small p, q (tau_q = 0: not): tau h =
+    // (p h - r h 2^(-32 shift)) / q exactly, so a Horner step of Eq. (2) is
+    // trunc_L((+-(p h - r h 2^(-32 shift)) + q c_i) / q) with no limb product
+    uint32_t tau_p, tau_q, tau_r;
+    int tau_shift, tau_neg;
     int exact;              // pipelined kernel: 1 = every product in full (no shortened sums)
     unsigned long long *chunks;  // pipelined kernel: executed 8 x 8 limb-product chunks of
                                  // the launch are added here (null: not counted)

@@ -1722,6 +1722,118 @@ __device__ bool horner_component(PSmem &S, const KArgs &a, const Geo &G, int c, 
 }
 
 
+// One Horner chain of Eq. (2) when tau = trunc_L(p/q) with small p, q: then
+// tau h = (p h - r h 2^(-32 shift)) / q exactly (r = p 2^(32 shift) mod q), so
+// h_i = trunc_L(tau h_{i+1} + c_i) = trunc_L(E / q) with the exact
+//   E = +-(p h_{i+1} - r h_{i+1} 2^(-32 shift)) + q c_i,
+// three one-limb multiples of numbers instead of an L x L product: the window
+// gets them column by column, then the close divides by q.  Same bits as
+// horner_component.
+__device__ bool horner_ratio(PSmem &S, const KArgs &a, const Geo &G, int c, long long step, Prof &pr)
+{
+    const int N1 = G.N1, Lp = G.Lp, L = G.L;
+    uint32_t *hp = S.raw + 2 * (size_t)Lp;  // h, plain limbs
+    uint32_t *ci = S.raw;                    // c_i, plain limbs
+    long long *win = S.win;
+    const uint32_t tp = a.tau_p, tq = a.tau_q, tr = a.tau_r;
+    const int sh = a.tau_shift;
+    const Divisor dq = make_divisor(tq);
+    int he = S.misc[MS_NEWE], hf = S.misc[MS_NEWE + 1];
+    constexpr int CR = MAX_L / PT;
+    uint32_t nxt[CR];
+    for (int x = threadIdx.x; x < Lp; x += PT) {
+        hp[x] = S.newc[x];
+        ci[x] = a.N >= 1 ? __ldcg(&a.coefL[((size_t)c * N1 + a.N - 1) * Lp + x]) : 0u;
+    }
+    __syncthreads();
+    bool ok = true;
+    for (int i = a.N - 1; i >= 0; i--) {
+#pragma unroll
+        for (int r = 0; r < CR; r++) {
+            const int x = threadIdx.x + r * PT;
+            nxt[r] = (i > 0 && x < Lp) ? __ldcg(&a.coefL[((size_t)c * N1 + i - 1) * Lp + x]) : 0u;
+        }
+        const int ce = S.expT[c * N1 + i], cf = S.flgT[c * N1 + i];
+        const bool prod = (hf & F_NZ) != 0;
+        const bool lone = (cf & F_NZ) != 0;
+        const long long lph = (long long)he - L, lpr = lph - sh, lpc = (long long)ce - L;
+        long long lo = LLONG_MAX, hi = LLONG_MIN;
+        if (prod) {
+            lo = min(lo, tr ? lpr : lph);
+            hi = max(hi, lph + Lp + 2);
+        }
+        if (lone) {
+            lo = min(lo, lpc);
+            hi = max(hi, lpc + Lp + 2);
+        }
+        int width = 0;
+        if (hi > lo) {
+            if (hi - lo > a.Wcap) {
+                if (threadIdx.x == 0) atomicCAS(a.status, 0, DEV_ERANGE);
+                ok = false;
+                break;  // uniform
+            }
+            width = (int)(hi - lo);
+        }
+        const bool hneg = ((hf & F_NEG) != 0) != (a.tau_neg != 0), cneg = (cf & F_NEG) != 0;
+        const int oh = (int)(lph - lo), orr = (int)(lpr - lo), oc = (int)(lpc - lo);
+        // column cc of v X placed at offset o: low half of v x_y plus high half of v x_{y-1}
+        auto scaled = [&](const uint32_t *X, uint32_t v, int y) -> long long {
+            long long t = 0;
+            if (y >= 0 && y < Lp) t += (uint32_t)((uint64_t)v * X[y]);
+            if (y >= 1 && y <= Lp) t += (long long)(((uint64_t)v * X[y - 1]) >> 32);
+            return t;
+        };
+        for (int cc = threadIdx.x; cc < width; cc += PT) {
+            long long s = 0;
+            if (prod) {
+                const long long th = scaled(hp, tp, cc - oh) - (tr ? scaled(hp, tr, cc - orr) : 0);
+                s += hneg ? -th : th;
+            }
+            if (lone) {
+                const long long tc = scaled(ci, tq, cc - oc);
+                s += cneg ? -tc : tc;
+            }
+            if (s) win[cc] += s;
+        }
+        __syncthreads();
+        pr.mark(PR_HMAC);
+        int e, f;
+        if (!close_bracket(S, a, G, win, width, lo, dq, hp, e, f)) {
+            ok = false;
+            break;
+        }
+        he = e;
+        hf = f;
+        // c_{i-1} for the next step (every thread is past the column loop)
+#pragma unroll
+        for (int r = 0; r < CR; r++) {
+            const int x = threadIdx.x + r * PT;
+            if (x < Lp) ci[x] = nxt[r];
+        }
+        __syncthreads();
+        pr.mark(PR_HCLOSE);
+    }
+    if (!ok) return false;
+    const long long rec = (a.record_every > 0 && ((step + 1) % a.record_every) == 0)
+                              ? (step + 1) / a.record_every - 1 : -1;
+    for (int x = threadIdx.x; x < Lp; x += PT) {
+        const uint32_t v = x < L ? hp[x] : 0u;
+        a.stL[(size_t)c * Lp + x] = v;
+        if (rec >= 0 && x < L) a.recL[((size_t)rec * 3 + c) * L + x] = v;
+    }
+    if (threadIdx.x == 0) {
+        a.stE[c] = he;
+        a.stF[c] = hf;
+        if (rec >= 0) {
+            a.recS[rec * 3 + c] = (hf & F_NEG) ? 1 : 0;
+            a.recE[rec * 3 + c] = he;
+        }
+    }
+    __threadfence();
+    return true;
+}
+
 // Bracket CTA c: coefficient component c of every index, then Horner.
 __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &G)
 {
@@ -1882,7 +1994,8 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
         }
         // Horner (Eq. (2)) for this CTA's component
         Prof ph(a, prof_on, S.misc);
-        if (!horner_component(S, a, G, c, step, ph)) return;
+        if (!(a.tau_q ? horner_ratio(S, a, G, c, step, ph) : horner_component(S, a, G, c, step, ph)))
+            return;
         __syncthreads();
         ph.mark(PR_HORNER);
     }

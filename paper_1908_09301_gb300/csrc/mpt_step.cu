@@ -1138,7 +1138,33 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
                 }
         }
         // window placement and term info
-        if (threadIdx.x < nc) {
+        if (a.tau_q && threadIdx.x < nc) {
+            // tau = trunc_L(p/q): h_i = trunc_L(E / q), E = +-(p h - r h 2^(-32 shift)) + q c_i
+            const int j = threadIdx.x, comp = c_first + j;
+            const int ce = S.expT[comp * N1 + i], cf = S.flgT[comp * N1 + i];
+            const bool prod = (hF[j] & F_NZ) != 0, lone = (cf & F_NZ) != 0;
+            const long long lph = (long long)hE[j] - a.L, lpr = lph - a.tau_shift, lpc = (long long)ce - a.L;
+            long long lo = LLONG_MAX, hi = LLONG_MIN;
+            if (prod) {
+                lo = min(lo, a.tau_r ? lpr : lph);
+                hi = max(hi, lph + Lp + 2);
+            }
+            if (lone) {
+                lo = min(lo, lpc);
+                hi = max(hi, lpc + Lp + 2);
+            }
+            int width = 0;
+            if (hi > lo) {
+                if (hi - lo > a.Wcap) set_status(a.status, DEV_ERANGE);
+                else width = (int)(hi - lo);
+            }
+            S.tinfo[2 * (2 * j)] = prod ? (int)(lph - lo) : 0;
+            S.tinfo[2 * (2 * j) + 1] = (prod ? 1 : 0) | ((((hF[j] & F_NEG) != 0) != (a.tau_neg != 0)) ? 2 : 0);
+            S.tinfo[2 * (2 * j + 1)] = lone ? (int)(lpc - lo) : 0;
+            S.tinfo[2 * (2 * j + 1) + 1] = (lone ? 1 : 0) | ((cf & F_NEG) ? 2 : 0);
+            ((long long *)(S.misc + MS_BASE))[j] = lo;
+            S.misc[MS_WIDTH + j] = width;
+        } else if (!a.tau_q && threadIdx.x < nc) {
             const int j = threadIdx.x, comp = c_first + j;
             const int ce = S.expT[comp * N1 + i], cf = S.flgT[comp * N1 + i];
             long long lo = LLONG_MAX, hi = LLONG_MIN;
@@ -1171,10 +1197,41 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
             S.misc[MS_WIDTH + j] = width;
         }
         if (!cta_ok(S, a)) return;
-        const int units = 2 * nc * a.P;
-        for (int u = threadIdx.x; u < units; u += NT) {
-            const int slot = u / a.P;
-            run_unit(S, a, slot, u - slot * a.P, 0);
+        if (a.tau_q) {
+            // the window of E column by column: low half of v x_y plus high half of v x_{y-1}
+            for (int j = 0; j < nc; j++) {
+                const int wd = S.misc[MS_WIDTH + j];
+                const int oh = S.tinfo[2 * (2 * j)], fh = S.tinfo[2 * (2 * j) + 1];
+                const int oc = S.tinfo[2 * (2 * j + 1)], fc = S.tinfo[2 * (2 * j + 1) + 1];
+                const uint32_t *hp = S.newc + (size_t)(c_first + j) * Lp;
+                const uint32_t *cs = S.slots + (size_t)(2 * j + 1) * SL;  // c_i, A layout
+                for (int cc = threadIdx.x; cc < wd; cc += NT) {
+                    long long sum = 0;
+                    if (fh & 1) {
+                        const int y = cc - oh, yr = y + a.tau_shift;
+                        long long t = 0;
+                        if (y >= 0 && y < Lp) t += (uint32_t)((uint64_t)a.tau_p * hp[y]);
+                        if (y >= 1 && y <= Lp) t += (long long)(((uint64_t)a.tau_p * hp[y - 1]) >> 32);
+                        if (yr >= 0 && yr < Lp) t -= (uint32_t)((uint64_t)a.tau_r * hp[yr]);
+                        if (yr >= 1 && yr <= Lp) t -= (long long)(((uint64_t)a.tau_r * hp[yr - 1]) >> 32);
+                        sum += (fh & 2) ? -t : t;
+                    }
+                    if (fc & 1) {
+                        const int y = cc - oc;
+                        long long t = 0;
+                        if (y >= 0 && y < Lp) t += (uint32_t)((uint64_t)a.tau_q * cs[phys(y)]);
+                        if (y >= 1 && y <= Lp) t += (long long)(((uint64_t)a.tau_q * cs[phys(y - 1)]) >> 32);
+                        sum += (fc & 2) ? -t : t;
+                    }
+                    if (sum) S.win[(size_t)j * a.Wcap + cc] += sum;
+                }
+            }
+        } else {
+            const int units = 2 * nc * a.P;
+            for (int u = threadIdx.x; u < units; u += NT) {
+                const int slot = u / a.P;
+                run_unit(S, a, slot, u - slot * a.P, 0);
+            }
         }
         __syncthreads();
         pr.mark(PR_HMAC);
@@ -1190,7 +1247,7 @@ __device__ void horner_phase(const Smem &S, const KArgs &a, int step)
                 Norm nr = warp_normalize(S.win + (size_t)j * a.Wcap, false, dig, wd, a.status);
                 for (int c = lane; c < wd; c += 32) S.win[j * a.Wcap + c] = 0;
                 if (nr.top >= 0) {
-                    long long eq = warp_divide(dig, nr.top, win_base(S, j), 1u, a.L, hp);
+                    long long eq = warp_divide(dig, nr.top, win_base(S, j), a.tau_q ? a.tau_q : 1u, a.L, hp);
                     if (eq > (1LL << 30) || eq < -(1LL << 30)) {
                         if (lane == 0) set_status(a.status, DEV_ERANGE);
                         eq = 0;
