@@ -236,17 +236,28 @@ def ensemble_bench(args):
     import torch
 
     from paper_1908_09301_gb300 import autotune as AT
-    from paper_1908_09301_gb300 import mpt
+    from paper_1908_09301_gb300 import mpt, shard
 
-    torch.cuda.set_device(0)
-    ens = WL.perturbed_ensemble(args.ensemble)
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    full = WL.perturbed_ensemble(args.ensemble)
+    # this rank's share of the trajectories, balanced by the work of a step
+    # (no exchange while they step; the ensemble is fixed: strong scaling)
+    mine = shard.partition([shard.step_work(t.L, t.N) for t in full], world)[rank]
+    ens = [full[j] for j in mine]
     Ls, Ns = [t.L for t in ens], [t.N for t in ens]
     steps = args.ens_steps
     states = []
     for t in ens:
         s, e, l = zip(*(mpt.parse_number(v, t.L) for v in t.x0))
         states.append((s, e, l))
-    work = sum(t.L * t.L * (t.N * (t.N + 1) + 7 * t.N) for t in ens)  # limb products per step
+    work = sum(t.L * t.L * (t.N * (t.N + 1) + 7 * t.N) for t in full)  # limb products per step, all ranks
     mpt.integrate_batch(Ls, Ns, 1, states)  # warm-up (module load, first launch)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -261,13 +272,22 @@ def ensemble_bench(args):
         torch.cuda.synchronize()
         return time.perf_counter() - t1, out
 
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
     dt_default, out_default = timed((0, 0, 0))
+    if dist is not None:
+        dist.barrier()
     dt, out = timed(shape)
     clocks = sampler.stop()
+    dt_default = max_over_ranks(dt_default, dist)
+    dt = max_over_ranks(dt, dist)
     import numpy as np
     same = all(np.array_equal(x, y) for a, b in zip(out, out_default) for x, y in zip(a, b))
-    value = len(ens) * steps / dt
+    value = len(full) * steps / dt
+    if rank != 0:
+        dist.destroy_process_group()
+        return 0
     # the same trajectories one at a time: one trajectory of each K, timed
     single_ms = {}
     for K in sorted({t.K for t in ens}):
@@ -279,26 +299,29 @@ def ensemble_bench(args):
             t1 = time.perf_counter()
             c.integrate(2)
             single_ms[K] = (time.perf_counter() - t1) / 2 * 1000.0
-    one_at_a_time_s = sum(single_ms[t.K] for t in ens) * steps / 1000.0
+    one_at_a_time_s = sum(single_ms[t.K] for t in full) * steps / 1000.0
     sms = torch.cuda.get_device_properties(0).multi_processor_count
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = sms * IMAD_PER_SM_CLK / 2 * sm_max * 1e6
     achieved = work * steps / dt
-    mix = {K: sum(1 for t in ens if t.K == K) for K in sorted({t.K for t in ens})}
-    state_bytes = int(sum(12 + 12 * t.L for t in ens))
+    mix = {K: sum(1 for t in full if t.K == K) for K in sorted({t.K for t in full})}
+    state_bytes = int(sum(12 + 12 * t.L for t in full))
     line = {
         "metric": "trajectory-steps/sec of a perturbed ensemble (bit-exact)", "value": value,
-        "unit": "trajectory-steps/s", "n_gpus": 1, "steps": steps, "warmup": 1,
-        "ms_per_step": dt / steps * 1000.0, "higher_is_better": True, "scaling": "weak",
+        "unit": "trajectory-steps/s", "n_gpus": world, "steps": steps, "warmup": 1,
+        "ms_per_step": dt / steps * 1000.0, "higher_is_better": True,
+        "scaling": "strong" if world > 1 else "weak",
         "vs_baseline": None, "dtype": "u32",
         "data": "synthetic (Sec. 5 point plus seeded 1e-20 perturbations, exact rationals)",
-        "config": {"workload": f"perturbed_ensemble_{len(ens)}", "trajectories": len(ens),
+        "config": {"workload": f"perturbed_ensemble_{len(full)}", "trajectories": len(full),
                    "digits_mix": mix, "N": "0.6 K",
+                   "parallelism": f"trajectories split over {world} rank(s) by step work, no collective "
+                                  "while stepping",
                    "timing": f"wall time of one mpt_integrate_batch_shape call of {steps} steps (states "
                              f"from and to host memory: {state_bytes} bytes each way)"},
         "shape": {"chosen": {"variant": shape[0], "tb": shape[1], "nwin": shape[2]},
-                  "default_trajectory_steps_per_s": len(ens) * steps / dt_default,
+                  "default_trajectory_steps_per_s": len(full) * steps / dt_default,
                   "same_bits_as_default": same, "tuning_s": t_tune,
                   "tuned_on": f"{tuned['sample']} trajectories of the workload, 1 step per shape",
                   "tried": tuned["tried"]},
@@ -319,6 +342,8 @@ def ensemble_bench(args):
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
     return 0
 
 

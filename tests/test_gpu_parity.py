@@ -138,14 +138,18 @@ def test_edge_cases(mpt, name, L, N, par, x0, kind):
 # limb, then one), one with a period too long for the pattern product
 # (0.001: 25 limbs) and a negative one: the Horner chain of Eq. (2) must be
 # bit-exact whichever way the kernel forms tau h
-TAUS = ["1/3", "2/7", "0.1", "1.01", "1/48", "0.001", "-0.01"]
+# the rest are ratios p/q with p < 2^32, q < 2^16, whose Horner steps need no
+# limb product (tau h = (p h - r h 2^(-32 shift))/q); 1/65537 and a long
+# decimal are not, and take the general product
+TAUS = ["1/3", "2/7", "0.1", "1.01", "1/48", "0.001", "-0.01", "1/65537", "0.0031415926535897932"]
 
 
+@pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("tau", TAUS)
-def test_horner_step_sizes(mpt, tau):
+def test_horner_step_sizes(mpt, tau, kind):
     L, N = 40, 30
     par = (O.SIGMA, O.R, O.B, tau)
-    c = gpu_ctx(mpt, L, N, par, kind=2)
+    c = gpu_ctx(mpt, L, N, par, kind=kind)
     c.integrate(2)
     fin, _ = oracle_run(L, N, par, nsteps=2)
     assert same(c.get_state(), fin), first_mismatch(c.get_state(), fin)
