@@ -621,6 +621,7 @@ def main():
         ctx.launch_async(1)
         ctx.wait()
 
+    reruns0, _ = ctx.counters()
     # device-timed region: one launch per Taylor step, L2 flushed in between
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -639,6 +640,9 @@ def main():
     if dist is not None:
         dist.barrier()
     ms_steps = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    # limb products the last timed launch executed (shortened sums leave out
+    # the columns below each sum's kept limbs), and full reruns in the region
+    reruns1, chunks = ctx.counters()
     ms_per_step = sum(ms_steps) / len(ms_steps)
     ms_per_step = max_over_ranks(ms_per_step, dist)
     value = job_rate(world, ms_per_step / 1000.0)
@@ -677,6 +681,10 @@ def main():
         "gpu_launches": args.steps,
         "limb_macs_per_step": work,
         "limb_macs_per_s": achieved * world,
+        "executed_limb_macs_per_step": 64 * chunks,
+        "executed_frac": 64 * chunks / (ms_per_step / 1000.0) / (sms * IMAD_PER_SM_CLK / 2 * float(
+            measured_peaks().get("sm_max_mhz", 2070.0)) * 1e6),
+        "exact_reruns_in_timed_region": reruns1 - reruns0,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                      "unit": "limb-MAC/s", "frac": achieved / peak,
                      "traffic": profiled_traffic(),
