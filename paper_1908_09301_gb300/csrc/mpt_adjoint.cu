@@ -105,14 +105,18 @@ int status_error(int st)
     return failf(MPT_ECUDA, "device status %d in the reverse sweep", st);
 }
 
-}  // namespace
+// tau as a small ratio p/q (q = 0: not known to be one), for the forward
+// recomputation's Horner steps without a limb product
+struct TauRatio {
+    uint32_t p = 0, q = 0, r = 0;
+    int shift = 0, neg = 0;
+};
 
-extern "C" int mpt_backward_raw(int B, int G, int L, int N, int64_t nsteps, int checkpoint_every,
-                                const int32_t *par_signs, const int32_t *par_exps,
-                                const uint32_t *par_limbs, const int32_t *st_signs,
-                                const int32_t *st_exps, const uint32_t *st_limbs, int32_t *g_signs,
-                                int32_t *g_exps, uint32_t *g_limbs, int32_t *th_signs,
-                                int32_t *th_exps, uint32_t *th_limbs, uint64_t cuda_stream)
+int backward_impl(int B, int G, int L, int N, int64_t nsteps, int checkpoint_every,
+                  const int32_t *par_signs, const int32_t *par_exps, const uint32_t *par_limbs,
+                  const int32_t *st_signs, const int32_t *st_exps, const uint32_t *st_limbs,
+                  int32_t *g_signs, int32_t *g_exps, uint32_t *g_limbs, int32_t *th_signs,
+                  int32_t *th_exps, uint32_t *th_limbs, uint64_t cuda_stream, const TauRatio &tr)
 {
     if (B < 1 || G < 1) return failf(MPT_EINVAL, "B = %d and G = %d must be >= 1", B, G);
     if ((long long)B * G > (1LL << 24)) return failf(MPT_EINVAL, "B * G = %lld is too large", (long long)B * G);
@@ -269,6 +273,11 @@ extern "C" int mpt_backward_raw(int B, int G, int L, int N, int64_t nsteps, int 
             a.vg = 0;
             a.npar = 4;
             a.ptau = 3;
+            a.tau_p = tr.p;
+            a.tau_q = tr.q;
+            a.tau_r = tr.r;
+            a.tau_shift = tr.shift;
+            a.tau_neg = tr.neg;
             if (hist) {
                 a.histL = histL + (size_t)b * every * nc * Lp;
                 a.histE = histE + (size_t)b * every * nc;
@@ -386,6 +395,20 @@ extern "C" int mpt_backward_raw(int B, int G, int L, int N, int64_t nsteps, int 
     return MPT_OK;
 }
 
+}  // namespace
+
+extern "C" int mpt_backward_raw(int B, int G, int L, int N, int64_t nsteps, int checkpoint_every,
+                                const int32_t *par_signs, const int32_t *par_exps,
+                                const uint32_t *par_limbs, const int32_t *st_signs,
+                                const int32_t *st_exps, const uint32_t *st_limbs, int32_t *g_signs,
+                                int32_t *g_exps, uint32_t *g_limbs, int32_t *th_signs,
+                                int32_t *th_exps, uint32_t *th_limbs, uint64_t cuda_stream)
+{
+    return backward_impl(B, G, L, N, nsteps, checkpoint_every, par_signs, par_exps, par_limbs, st_signs,
+                         st_exps, st_limbs, g_signs, g_exps, g_limbs, th_signs, th_exps, th_limbs,
+                         cuda_stream, TauRatio{});
+}
+
 extern "C" int mpt_backward(int B, int L, int N, int64_t nsteps, const char *tau, const char *sigma,
                             const char *R, const char *b, const char *const *x0, const double *g,
                             int checkpoint_every, double *g_x0, double *g_params, double *jac,
@@ -418,9 +441,11 @@ extern "C" int mpt_backward(int B, int L, int N, int64_t nsteps, const char *tau
             if (mpt_host::from_double(v, L, &gS[3 * it + k], &gE[3 * it + k], &gLm[((size_t)3 * it + k) * L]))
                 return failf(MPT_EINVAL, "g[%d] is not finite", 3 * it + k);
         }
-    const int rc = mpt_backward_raw(B, G, L, N, nsteps, checkpoint_every, pS.data(), pE.data(), pLm.data(),
-                                    sS.data(), sE.data(), sLm.data(), gS.data(), gE.data(), gLm.data(),
-                                    tS.data(), tE.data(), tLm.data(), cuda_stream);
+    TauRatio tr;
+    if (mpt_host::small_ratio(tau, L, &tr.p, &tr.q, &tr.r, &tr.shift, &tr.neg)) tr = TauRatio{};
+    const int rc = backward_impl(B, G, L, N, nsteps, checkpoint_every, pS.data(), pE.data(), pLm.data(),
+                                 sS.data(), sE.data(), sLm.data(), gS.data(), gE.data(), gLm.data(), tS.data(),
+                                 tE.data(), tLm.data(), cuda_stream, tr);
     if (rc) return rc;
     auto dbl = [&](const std::vector<int32_t> &s, const std::vector<int32_t> &e, const std::vector<uint32_t> &l,
                    size_t k) { return mpt_host::to_double(L, s[k], e[k], &l[k * L]); };
