@@ -488,6 +488,177 @@ __device__ long long block_divide(const uint32_t *dig, int t, long long base, co
     return eq;
 }
 
+// block_normalize for Wn <= PT (one column a thread), with two barriers
+// (three when the value is negative) instead of four: with one column a
+// thread, the carry a thread's column hands on before any adjustment is the
+// column's own high part, so thread t reads the column below its own to form
+// its carry map and needs no exchange for it; and every warp composes the
+// warps' maps itself (a scan over the lanes, lane w holding warp w's map)
+// instead of waiting for one warp to do it.  Same result and contract as
+// block_normalize; `red` holds RED_LL long longs (ints [64, 148) used).
+__device__ Norm block_normalize_1(long long *col, uint32_t *dig, int Wn, long long *red, int *status)
+{
+    Norm r;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int *ri = (int *)red;
+    int *mapw = ri + 64;                    // [NWARPS] the warps' maps
+    long long *fin0 = red + 48;             // ints 96, 97: the top column's own carry
+    int *zt = ri + 100;                     // [3][NWARPS] lowest non-zero, top non-zero, top non-all-ones
+    const bool own = tid < Wn;
+    const long long v = own ? col[tid] : 0;
+    const long long lprev = (own && tid > 0) ? (col[tid - 1] >> 32) : 0;
+    const uint32_t d = (uint32_t)v;
+    int f = CMAP_ID;
+    if (own) {
+        f = 0;
+#pragma unroll
+        for (int x = -1; x <= 1; x++) f |= ((int)(((long long)d + lprev + x) >> 32) + 1) << (2 * (x + 1));
+        if (tid == Wn - 1) *fin0 = v >> 32;
+    }
+    int F = f;  // inclusive scan of maps, lowest thread first
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int G = __shfl_up_sync(FULL, F, o);
+        if (lane >= o) F = cmap_compose(F, G);
+    }
+    if (lane == 31) mapw[warp] = F;
+    __syncthreads();
+    int Gw = lane < NWARPS ? mapw[lane] : CMAP_ID;
+#pragma unroll
+    for (int o = 1; o < NWARPS; o <<= 1) {
+        const int H = __shfl_up_sync(FULL, Gw, o);
+        if (lane >= o) Gw = cmap_compose(Gw, H);
+    }
+    int pre = __shfl_sync(FULL, Gw, (warp + 31) & 31);  // the warps below this one
+    if (warp == 0) pre = CMAP_ID;
+    const int total = __shfl_sync(FULL, Gw, NWARPS - 1);
+    const long long topc = *fin0 + cmap_apply(total, 0);
+    int ex = __shfl_up_sync(FULL, F, 1);
+    if (lane == 0) ex = CMAP_ID;
+    const int din = cmap_apply(cmap_compose(ex, pre), 0);
+    uint32_t dd = 0u;
+    int z = INT_MAX, t0 = -1, t1 = -1;
+    if (own) {
+        dd = (uint32_t)((long long)d + lprev + din);
+        dig[tid] = dd;
+        col[tid] = 0;  // every read of it was before the barrier
+        if (dd) {
+            z = tid;
+            t0 = tid;
+        }
+        if (dd != 0xffffffffu) t1 = tid;
+    }
+    z = warp_min_i(z);
+    t0 = warp_max_i(t0);
+    t1 = warp_max_i(t1);
+    if (lane == 0) {
+        zt[warp] = z;
+        zt[NWARPS + warp] = t0;
+        zt[2 * NWARPS + warp] = t1;
+    }
+    __syncthreads();
+    {
+        int zz = INT_MAX, a0 = -1, a1 = -1;
+        if (lane < NWARPS) {
+            zz = zt[lane];
+            a0 = zt[NWARPS + lane];
+            a1 = zt[2 * NWARPS + lane];
+        }
+        z = warp_min_i(zz);
+        t0 = warp_max_i(a0);
+        t1 = warp_max_i(a1);
+    }
+    if (topc != 0 && topc != -1 && tid == 0) atomicCAS(status, 0, DEV_INTERNAL);
+    r.neg = topc < 0;
+    r.top = r.neg ? (z == INT_MAX ? -1 : max(t1, z)) : t0;
+    if (r.neg) {
+        if (own) {
+            if (tid > z) dig[tid] = ~dd;
+            else if (tid == z) dig[tid] = 0u - dd;
+        }
+        __syncthreads();
+    }
+    return r;
+}
+
+// block_divide when the quotient has at most PT digits (one digit a thread,
+// thread 0 the top one), with two barriers: every warp composes the warps'
+// remainder maps itself.  Same result and contract as block_divide; `red`
+// holds >= 2 NWARPS ints (ints [0, 32) used).
+__device__ long long block_divide_1(const uint32_t *dig, int t, long long base, const Divisor &dv, int L,
+                                    uint32_t *out, int *red, uint32_t *out2 = nullptr)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long T = base + t + 1;
+    const uint32_t d = dv.d;
+    const long long eq = (dig[t] >= d) ? T : T - 1;
+    const long long s = eq - L;
+    const int nX = (int)(T - s);  // L or L+1 digits j = 0 .. nX-1, bottom up
+    const int j = nX - 1 - tid;   // this thread's digit (j < 0: none)
+    uint32_t X = 0u;
+    if (j >= 0) {
+        const long long idx = s + j - base;
+        X = idx >= 0 ? dig[idx] : 0u;
+    }
+    if (d == 1u) {
+        if (j >= 0 && j < L) {
+            out[j] = X;
+            if (out2) out2[gpos(j)] = X;
+        }
+        __syncthreads();
+        return eq;
+    }
+    uint32_t t32 = 1;
+    (void)divstep(t32, 0u, dv);  // 2^32 mod d
+    // this digit's map r -> (2^32 r + X) mod d, identity without a digit
+    uint32_t Pm = 1u, V = 0u;
+    if (j >= 0) {
+        Pm = t32;
+        (void)divstep(V, X, dv);
+    }
+    // inclusive scan: (P2, V2) after (P1, V1) = (P2 P1, P2 V1 + V2) mod d
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t Po = __shfl_up_sync(FULL, Pm, o);
+        const uint32_t Vo = __shfl_up_sync(FULL, V, o);
+        if (lane >= o) {
+            V = mod_inv(Pm * Vo + V, dv);
+            Pm = mod_inv(Pm * Po, dv);
+        }
+    }
+    int *wP = red, *wV = red + NWARPS;
+    if (lane == 31) {
+        wP[warp] = (int)Pm;
+        wV[warp] = (int)V;
+    }
+    __syncthreads();
+    uint32_t GP = lane < NWARPS ? (uint32_t)wP[lane] : 1u;
+    uint32_t GV = lane < NWARPS ? (uint32_t)wV[lane] : 0u;
+#pragma unroll
+    for (int o = 1; o < NWARPS; o <<= 1) {
+        const uint32_t Po = __shfl_up_sync(FULL, GP, o);
+        const uint32_t Vo = __shfl_up_sync(FULL, GV, o);
+        if (lane >= o) {
+            GV = mod_inv(GP * Vo + GV, dv);
+            GP = mod_inv(GP * Po, dv);
+        }
+    }
+    uint32_t rin = __shfl_sync(FULL, GV, (warp + 31) & 31);  // the remainder leaving the warps above
+    if (warp == 0) rin = 0u;
+    uint32_t Pe = __shfl_up_sync(FULL, Pm, 1), Ve = __shfl_up_sync(FULL, V, 1);
+    if (lane == 0) {
+        Pe = 1u;
+        Ve = 0u;
+    }
+    uint32_t rr = mod_inv(Pe * rin + Ve, dv);
+    if (j >= 0) {
+        const uint32_t qd = divstep(rr, X, dv);
+        if (j < L) out[j] = qd;
+    }
+    __syncthreads();
+    return eq;
+}
+
 // ------------------------------------------------------------------ async copies
 
 __device__ __forceinline__ void cp_async4(uint32_t *dst_smem, const uint32_t *src_gmem)

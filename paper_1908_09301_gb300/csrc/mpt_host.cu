@@ -116,8 +116,13 @@ struct mpt_ctx {
 
 namespace {
 
-// profile counters: the first and the last CTA, then one row per SM
-size_t prof_len(const mpt_ctx *c) { return (size_t)(2 + c->sms) * mpt::PROF_SLOTS; }
+// profile counters: the first and the last CTA, then one row per SM, then the
+// pipelined kernel's per-index timeline
+size_t prof_rows_len(const mpt_ctx *c) { return (size_t)(2 + c->sms) * mpt::PROF_SLOTS; }
+size_t prof_len(const mpt_ctx *c)
+{
+    return prof_rows_len(c) + (size_t)mpt::TL_ROWS * (mpt::MAX_N + 1);
+}
 
 // which kernel runs a launch: the pipelined one for large L x N, when the
 // device fits its fixed-role CTAs and at least one worker
@@ -674,6 +679,7 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
     a.nsteps = nsteps;
     a.record_every = nrec > 0 ? record_every : 0;
     a.prof = c->prof;
+    a.timeline = c->prof ? c->prof + prof_rows_len(c) : nullptr;
     a.spin_limit = c->spin_limit;
     a.sysT = c->sysT;
     a.sysNF = c->sysNF;

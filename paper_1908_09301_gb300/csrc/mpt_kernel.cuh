@@ -56,6 +56,8 @@ struct KArgs {
     long long nsteps;
     long long record_every;
     long long *prof;        // [2][PROF_SLOTS] per-phase SM cycles of CTAs 0 and G-1, or null
+    long long *timeline;    // pipelined kernel, profiling: [TL_ROWS][MAX_N + 1] global-timer
+                            // stamps of each index of the launch's last step (or null)
     long long spin_limit;   // polls before a device-side wait gives up
     int vG, vg;             // lock-step kernel: grid size and CTA index it runs as
                             // (vG = 0: the launch's own grid); a batch runs each
@@ -99,6 +101,14 @@ constexpr int SYS_MAX_FIXED = 32;  // fixed terms (linear and constant)
 constexpr int SYS_MAX_QUAD = 16;   // Cauchy products
 
 constexpr long long DEFAULT_SPIN_LIMIT = 20LL * 1000 * 1000;
+
+// rows of the per-index timeline (global timer, ns) of the pipelined kernel:
+// the beta' bracket at the start of index m, after its wait for the other
+// CTAs' sums, after publishing; the last edge CTA and the last worker (or
+// outer-pair CTA) to count index m done; the gamma' bracket after publishing;
+// the last edge CTA to see coefficient m, to start its products, to end them
+enum { TL_B_START = 0, TL_B_WAITED = 1, TL_B_PUB = 2, TL_EDGE = 3, TL_WORK = 4, TL_G_PUB = 5,
+       TL_E_SEEN = 6, TL_E_MAC = 7, TL_E_MACD = 8, TL_ROWS = 9 };
 
 // phases of the per-phase cycle profile
 enum ProfSlot {

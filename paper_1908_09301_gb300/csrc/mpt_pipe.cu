@@ -94,7 +94,8 @@ enum {
     MS_PARX = 272,  // [4][2] exponent and flags of sigma, R, b, tau (ints 272..279)
     MS_PROF = 336,  // [PROF_SLOTS] long long (ints 336..367)
     MS_CHUNKS = 368,  // long long: limb-product chunks this CTA executed
-    MISC_INTS = 372
+    MS_KDONE = 372,   // workers: batches the compute group is through (written by its thread 0)
+    MISC_INTS = 376
 };
 
 // bracket setup (ints at MS_BK): lo (long long), width, simple parts, terms, the workers' sums
@@ -242,28 +243,57 @@ struct Prof {
     }
 };
 
+// Per-index timeline (profiling only): global-timer stamp of index m of the
+// launch's last step, set (tl_put) or raised to the latest of several CTAs
+// (tl_max).
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void tl_put(const KArgs &a, int row, int m, long long step)
+{
+    if (a.timeline && step == a.nsteps - 1) a.timeline[(size_t)row * (MAX_N + 1) + m] = (long long)global_ns();
+}
+__device__ __forceinline__ void tl_max(const KArgs &a, int row, int m, long long step)
+{
+    if (a.timeline && step == a.nsteps - 1)
+        atomicMax((unsigned long long *)&a.timeline[(size_t)row * (MAX_N + 1) + m], global_ns());
+}
+
+// One poll of a flag: the status word and the flag, both loads in flight
+// together (the status load is issued first: an acquire load holds back only
+// the memory operations that follow it).
+__device__ __forceinline__ unsigned poll_flag(const unsigned *flag, const int *status, int &st, bool acquire)
+{
+    st = ld_relaxed_int(status);
+    return acquire ? ld_acquire_u32(flag) : ld_relaxed_u32(flag);
+}
+
+// bounded wait (thread 0) until *flag >= target, the status word read with
+// every poll; returns the status (0: go on).  Acquire on the flag.
+__device__ __forceinline__ int poll_geq(const KArgs &a, const unsigned *flag, unsigned target)
+{
+    long long it = 0;
+    for (;;) {
+        int st;
+        const unsigned v = poll_flag(flag, a.status, st, true);
+        if (st) return st;
+        if ((int)(v - target) >= 0) return 0;
+        if (++it > a.spin_limit) {
+            atomicCAS(a.status, 0, DEV_TIMEOUT);
+            return DEV_TIMEOUT;
+        }
+        __nanosleep(20);
+    }
+}
+
 // bounded wait until *flag >= target (thread 0), the status word checked on
 // the way.  Returns false (CTA-uniform) when the launch must stop.
 __device__ bool wait_geq(PSmem &S, const KArgs &a, const unsigned *flag, unsigned target)
 {
-    if (threadIdx.x == 0) {
-        int st = 0;
-        long long it = 0;
-        while ((int)(ld_acquire_u32(flag) - target) < 0) {
-            if (++it > a.spin_limit) {
-                atomicCAS(a.status, 0, DEV_TIMEOUT);
-                st = DEV_TIMEOUT;
-                break;
-            }
-            if ((it & 63) == 0) {
-                st = ld_relaxed_int(a.status);
-                if (st) break;
-            }
-            __nanosleep(20);
-        }
-        if (!st) st = ld_relaxed_int(a.status);
-        S.misc[MS_STATUS] = st;
-    }
+    if (threadIdx.x == 0) S.misc[MS_STATUS] = poll_geq(a, flag, target);
     __syncthreads();
     return S.misc[MS_STATUS] == 0;
 }
@@ -916,32 +946,43 @@ __device__ void ctl_prepare(PSmem &S, const Geo &G, int TB, int buf, int role, i
 }
 
 // bounded wait of the control group until *flag >= target (its first thread
-// polls); false (group-uniform) when the launch must stop.  The compute
-// warps keep running meanwhile, so the poll is a relaxed load (an acquire
-// load may invalidate the SM's L1 on every poll) with one acquire at the end.
-__device__ bool ctl_wait_geq(PSmem &S, const KArgs &a, const unsigned *flag, unsigned target, int ct)
+// polls); returns 0 when the flag is reached, -1 (group-uniform) when the
+// launch must stop, and 1 as soon as the compute group is through batch
+// `flush_at` - 1 (flush_at >= 0), so that the window of those batches can be
+// flushed before the wait goes on.  The compute warps keep running
+// meanwhile, so the poll is a relaxed load (an acquire load may invalidate
+// the SM's L1 on every poll), made an acquire at the end by a fence.
+__device__ int ctl_wait_geq(PSmem &S, const KArgs &a, const unsigned *flag, unsigned target, int ct,
+                            long long flush_at = -1)
 {
     if (ct == 0) {
-        int st = 0;
+        int st = 0, r = 0;
         long long it = 0;
-        while ((int)(ld_relaxed_u32(flag) - target) < 0) {
+        for (;;) {
+            if ((int)(ld_relaxed_u32(flag) - target) >= 0) break;
+            if ((it & 63) == 63) {  // the status word now and then (many CTAs poll here)
+                st = ld_relaxed_int(a.status);
+                if (st) break;
+            }
+            if (flush_at >= 0 && *(volatile int *)&S.misc[MS_KDONE] >= flush_at) {
+                r = 1;
+                break;
+            }
             if (++it > a.spin_limit) {
                 atomicCAS(a.status, 0, DEV_TIMEOUT);
                 st = DEV_TIMEOUT;
                 break;
             }
-            if ((it & 63) == 0) {
-                st = ld_relaxed_int(a.status);
-                if (st) break;
-            }
             __nanosleep(64);
         }
-        (void)ld_acquire_u32(flag);  // pairs with the publisher's release
-        if (!st) st = ld_relaxed_int(a.status);
-        S.misc[MS_STATUS] = st;
+        // with the relaxed loads above, an acquire pattern (the flag; and the
+        // compute group's count, published with a CTA fence)
+        asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        if (!st && !r) st = ld_relaxed_int(a.status);
+        S.misc[MS_STATUS] = st ? -1 : r;
     }
     named_sync(BAR_CT, CT);
-    return S.misc[MS_STATUS] == 0;
+    return S.misc[MS_STATUS];
 }
 
 // The control group of a worker or outer-pair CTA (roles 0 and 1 + target):
@@ -1010,6 +1051,7 @@ __device__ void worker_control(PSmem &S, const KArgs &a, const PArgs &pa, const 
     auto flush_pending = [&]() {
         consumed(pend_last + 1);
         flush(pend_set, pend_par);
+        if (ct == 0) tl_max(a, TL_WORK, (int)(pend_g % a.N), pend_g / a.N);
         pend = false;
         pr.mark(PR_CLOSE);
     };
@@ -1027,8 +1069,14 @@ __device__ void worker_control(PSmem &S, const KArgs &a, const PArgs &pa, const 
             // that one: a pending one among them is flushed first
             if (pend && pend_g <= g - lag - 1) flush_pending();
             // every index waits for its coefficient, so that no CTA runs more
-            // than a few indices ahead of the brackets (the sets are reused)
-            if (!ctl_wait_geq(S, a, pa.pub, (unsigned)(3 * (step * N1 + m + 1 - lag)), ct)) {
+            // than a few indices ahead of the brackets (the sets are reused);
+            // a pending window is flushed meanwhile as soon as the compute
+            // group is through it
+            int wr;
+            while ((wr = ctl_wait_geq(S, a, pa.pub, (unsigned)(3 * (step * N1 + m + 1 - lag)), ct,
+                                      pend ? pend_last + 1 : -1)) == 1)
+                flush_pending();
+            if (wr < 0) {
                 ok = false;
                 break;
             }
@@ -1148,6 +1196,12 @@ __device__ void worker_compute(PSmem &S, const Geo &G, const PArgs &pa, const KA
                      ti[3] * W, cw == NO_CUT ? 0 : cw - ti[3] * W, chunks);
         }
         named_arrive(BAR_EMPTY + b, PT);
+        if (threadIdx.x == 0) {
+            // every compute thread's window sums are in (the products end
+            // with a barrier of the group): tell the control group
+            __threadfence_block();
+            *(volatile int *)&S.misc[MS_KDONE] = (int)(k + 1);
+        }
         pr.mark(PR_MAC);
     }
 }
@@ -1254,7 +1308,9 @@ __device__ void edge_window(const PSmem &S, const KArgs &a, const Geo &G, int c,
 {
     lo = LLONG_MAX;
     hi = LLONG_MIN;
+#pragma unroll
     for (int e = 0; e < NEDGE; e++)
+#pragma unroll
         for (int k = 0; k < 2; k++) {
             const EdgeTerm T = EDGE_T[e][k];
             long long lp;
@@ -1283,100 +1339,95 @@ __device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &
             Prof pr(a, true, S.misc);
             const long long g = step * a.N + m;
             const int set = (int)(g % PIPE_SETS);
-            // thread 0 waits for coefficient m, takes its exponents and
-            // places this CTA's terms; one barrier for all of it
-            if (threadIdx.x == 0) {
-                int st = 0;
-                long long it = 0;
-                const unsigned target = (unsigned)(3 * (step * N1 + m + 1));
-                while ((int)(ld_acquire_u32(pa.pub) - target) < 0) {
-                    if (++it > a.spin_limit) {
-                        atomicCAS(a.status, 0, DEV_TIMEOUT);
-                        st = DEV_TIMEOUT;
-                        break;
-                    }
-                    if ((it & 63) == 0) {
-                        st = ld_relaxed_int(a.status);
-                        if (st) break;
-                    }
-                    __nanosleep(20);
+            // thread 0 waits for coefficient m; then, in one round trip, its
+            // exponents and the limbs of this CTA's components of it
+            if (threadIdx.x == 0) S.misc[MS_STATUS] = poll_geq(a, pa.pub, (unsigned)(3 * (step * N1 + m + 1)));
+            __syncthreads();
+            if (S.misc[MS_STATUS]) return;
+            pr.mark(PR_BARRIER);
+            if (threadIdx.x == 0) tl_max(a, TL_E_SEEN, m, step);
+            if (threadIdx.x >= 32) {
+                // warps 1..: the limbs of this CTA's components of coefficient m
+                for (int x = threadIdx.x - 32; x < 2 * Lp; x += PT - 32) {
+                    const int k = x >= Lp ? 1 : 0, y = x - k * Lp;
+                    const EdgeTerm T = EDGE_T[e][k];
+                    if (T.tgt >= 0) S.raw[x] = __ldcg(&a.coefL[((size_t)T.comp * N1 + m) * Lp + y]);
                 }
-                if (!st) st = ld_relaxed_int(a.status);
-                S.misc[MS_STATUS] = st;
-                pr.mark(PR_BARRIER);
-                if (!st) {
-                    int ev[3], fv[3];
-#pragma unroll
-                    for (int k = 0; k < 3; k++) {
-                        ev[k] = __ldcg(&a.coefE[k * N1 + m]);
-                        fv[k] = __ldcg(&a.coefF[k * N1 + m]);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 3; k++) {
-                        S.expT[k * N1 + m] = ev[k];
-                        S.flgT[k * N1 + m] = fv[k];
-                    }
-                    for (int k = 0; k < 2; k++) {
+                if (m == 0) {
+                    // the fixed factors of this CTA's terms: coefficient 0 or a parameter
+                    for (int x = threadIdx.x - 32; x < 2 * Lp; x += PT - 32) {
+                        const int k = x >= Lp ? 1 : 0, y = x - k * Lp;
                         const EdgeTerm T = EDGE_T[e][k];
-                        long long lp, lo, hi;
-                        int neg = 0, on = 0, d = 0, width = 0, cut = NO_CUT;
-                        if (T.tgt >= 0 && edge_term(S, a, G, T, m, lp, neg)) {
-                            edge_window(S, a, G, T.tgt, m, lo, hi);
-                            if (hi - lo > a.Wcap) {
-                                atomicCAS(a.status, 0, DEV_ERANGE);
-                            } else {
-                                on = 1;
-                                d = (int)(lp - lo);
-                                width = (int)(hi - lo);
-                                cut = part_cut(a, G, lo, hi);
-                            }
-                        }
-                        int *ti = S.tinfo + k * TI;
-                        ti[0] = on;
-                        ti[1] = neg;
-                        ti[2] = d & 7;
-                        ti[3] = d >> 3;
-                        ti[4] = width;
-                        // product column of the cut (0: in full)
-                        ti[5] = cut == NO_CUT ? 0 : cut - (d >> 3) * W;
+                        if (T.tgt < 0) continue;
+                        const uint32_t *src = T.fix < 3 ? a.coefL + (size_t)T.fix * N1 * Lp
+                                                        : a.parL + (size_t)(T.fix - 3) * Lp;
+                        S.vC[(size_t)k * G.VW + gpos(y)] = __ldcg(&src[y]);
                     }
+                }
+            } else if (threadIdx.x == 0) {
+                // thread 0: the exponents of coefficient m (one round trip, in
+                // step with the limbs), then the placement of the terms
+                int ev[3], fv[3];
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    ev[k] = __ldcg(&a.coefE[k * N1 + m]);
+                    fv[k] = __ldcg(&a.coefF[k * N1 + m]);
+                }
+#pragma unroll
+                for (int k = 0; k < 3; k++) {
+                    S.expT[k * N1 + m] = ev[k];
+                    S.flgT[k * N1 + m] = fv[k];
+                }
+#pragma unroll
+                for (int k = 0; k < 2; k++) {
+                    const EdgeTerm T = EDGE_T[e][k];
+                    long long lp, lo, hi;
+                    int neg = 0, on = 0, d = 0, width = 0, cut = NO_CUT;
+                    if (T.tgt >= 0 && edge_term(S, a, G, T, m, lp, neg)) {
+                        edge_window(S, a, G, T.tgt, m, lo, hi);
+                        if (hi - lo > a.Wcap) {
+                            atomicCAS(a.status, 0, DEV_ERANGE);
+                        } else {
+                            on = 1;
+                            d = (int)(lp - lo);
+                            width = (int)(hi - lo);
+                            cut = part_cut(a, G, lo, hi);
+                        }
+                    }
+                    int *ti = S.tinfo + k * TI;
+                    ti[0] = on;
+                    ti[1] = neg;
+                    ti[2] = d & 7;
+                    ti[3] = d >> 3;
+                    ti[4] = width;
+                    // product column of the cut (0: in full)
+                    ti[5] = cut == NO_CUT ? 0 : cut - (d >> 3) * W;
                 }
             }
             __syncthreads();
-            if (S.misc[MS_STATUS]) return;
-            if (m == 0) {
-                // the fixed factors of this CTA's terms: coefficient 0 or a parameter
-                for (int k = 0; k < 2; k++) {
-                    const EdgeTerm T = EDGE_T[e][k];
-                    if (T.tgt < 0) continue;
-                    const uint32_t *src = T.fix < 3 ? a.coefL + (size_t)T.fix * N1 * Lp
-                                                    : a.parL + (size_t)(T.fix - 3) * Lp;
-                    for (int x = threadIdx.x; x < Lp; x += PT)
-                        S.vC[(size_t)k * G.VW + gpos(x)] = __ldcg(&src[x]);
-                }
-            }
             pr.mark(PR_PLACE);
             // first factors: the component shifted by d_lo, complemented when negative
             for (int k = 0; k < 2; k++) {
                 const int *ti = S.tinfo + k * TI;
                 if (!ti[0]) continue;
-                const EdgeTerm T = EDGE_T[e][k];
-                const uint32_t *src = a.coefL + ((size_t)T.comp * N1 + m) * Lp;
+                const uint32_t *src = S.raw + (size_t)k * Lp;
                 const uint32_t inv = ti[1] ? 0xffffffffu : 0u;
                 const int dl = ti[2];
                 uint32_t *dst = S.vA + (size_t)k * G.VW;
                 for (int x = threadIdx.x; x < G.M; x += PT) {
                     const int y = x - dl;
-                    dst[gpos(x)] = (y >= 0 && y < Lp) ? (__ldcg(&src[y]) ^ inv) : 0u;
+                    dst[gpos(x)] = (y >= 0 && y < Lp) ? (src[y] ^ inv) : 0u;
                 }
             }
             pr.mark(PR_STAGE);
+            if (threadIdx.x == 0) tl_max(a, TL_E_MAC, m, step);
             for (int k = 0; k < 2; k++) {
                 const int *ti = S.tinfo + k * TI;
                 if (!ti[0]) continue;
                 products(G, G.RS, whole_cta(), S.vA, S.vC, k, 1, S.tinfo, false, S.bstage, S.bcstage,
                          S.win + (size_t)k * G.WW, ti[3] * W, ti[5], chunks);
             }
+            if (threadIdx.x == 0) tl_max(a, TL_E_MACD, m, step);
             pr.mark(PR_MAC);
             for (int k = 0; k < 2; k++) {
                 const int *ti = S.tinfo + k * TI;
@@ -1396,6 +1447,7 @@ __device__ void edge_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo &
             if (threadIdx.x == 0) {
                 __threadfence();
                 atomicAdd(&pa.done[set], 1u);
+                tl_max(a, TL_EDGE, m, step);
             }
             pr.mark(PR_FLUSH);
         }
@@ -1565,7 +1617,9 @@ __device__ bool close_bracket(PSmem &S, const KArgs &a, const Geo &G, long long 
     int top = -1, neg = 0;
     if (threadIdx.x == 0) S.misc[MS_NRUN] = 0;  // the buffer-digit flags (ordered by the barriers below)
     if (width > 0) {
-        const Norm nr = block_normalize(win, S.dig, width, (long long *)(S.misc + MS_RED), a.status);
+        long long *red = (long long *)(S.misc + MS_RED);
+        const Norm nr = width <= PT ? block_normalize_1(win, S.dig, width, red, a.status)
+                                    : block_normalize(win, S.dig, width, red, a.status);
         top = nr.top;
         neg = nr.neg;
     }
@@ -1584,7 +1638,8 @@ __device__ bool close_bracket(PSmem &S, const KArgs &a, const Geo &G, long long 
         if (bits) atomicOr(&S.misc[MS_NRUN], bits);
     }
     if (top >= 0) {
-        const long long eq = block_divide(S.dig, top, lo, dv, G.L, out, S.misc + MS_RED, out2);
+        const long long eq = G.L < PT ? block_divide_1(S.dig, top, lo, dv, G.L, out, S.misc + MS_RED, out2)
+                                      : block_divide(S.dig, top, lo, dv, G.L, out, S.misc + MS_RED, out2);
         if (eq > (1LL << 30) || eq < -(1LL << 30)) {
             if (threadIdx.x == 0) atomicCAS(a.status, 0, DEV_ERANGE);
             ok = false;
@@ -1876,6 +1931,7 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             const long long g = step * a.N + m;
             const int set = (int)(g % PIPE_SETS);
             const Divisor dvm = S.divT[m];
+            if (c == 1 && threadIdx.x == 0) tl_put(a, TL_B_START, m, step);
             if (threadIdx.x == 0) S.misc[MS_STATUS] = bracket_setup(S, a, pa, G, c, m, set) ? 0 : 1;
             __syncthreads();
             pr.mark(PR_X1);
@@ -1890,6 +1946,7 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 // every other CTA has added its sums of index m
                 const unsigned target = (unsigned)((g / PIPE_SETS + 1) * (long long)(gridDim.x - NCL));
                 if (!wait_geq(S, a, pa.done + set, target)) return;
+                if (c == 1 && threadIdx.x == 0) tl_put(a, TL_B_WAITED, m, step);
                 pr.mark(PR_BARRIER);
                 // the three parts of this bracket (middle pairs, outer pairs,
                 // edge terms); a thread owns window columns cc = threadIdx.x mod PT
@@ -1969,6 +2026,8 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
                 a.coefE[c * N1 + m + 1] = e;
                 a.coefF[c * N1 + m + 1] = f;
                 red_release_add_u32(pa.pub, 1u);
+                if (c == 1) tl_put(a, TL_B_PUB, m, step);
+                if (c == 2) tl_put(a, TL_G_PUB, m, step);
             }
             pr.mark(PR_X3);
             // coefficient m+1: all three components
@@ -2011,6 +2070,7 @@ __global__ void __launch_bounds__(PT, 1) pipe_kernel(KArgs a, PArgs pa)
     if (threadIdx.x < PROF_SLOTS) ((long long *)(S.misc + MS_PROF))[threadIdx.x] = 0;
     if (threadIdx.x == 0) {
         S.misc[MS_STATUS] = 0;
+        S.misc[MS_KDONE] = 0;
         ll_at(S.misc, MS_CHUNKS) = 0;
     }
     __syncthreads();

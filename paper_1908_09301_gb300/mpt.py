@@ -299,6 +299,20 @@ class Context:
         out["ctas"] = buf[32:].reshape(-1, 16)
         return out
 
+    TIMELINE_ROWS = ("beta_start", "beta_waited", "beta_published", "last_edge_done", "last_worker_done",
+                     "gamma_published", "last_edge_seen", "last_edge_mac_start", "last_edge_mac_end")
+    MAX_N = 4096
+
+    def timeline(self, sms: int):
+        """Per-index global-timer stamps (ns) of the last step of the last
+        launch (pipelined kernel, profiling on): {row: int64 array [N]},
+        rows as TIMELINE_ROWS; ``sms`` is the device's SM count."""
+        n = (2 + int(sms)) * 16 + len(self.TIMELINE_ROWS) * (self.MAX_N + 1)
+        buf = np.zeros(n, np.int64)
+        _check(lib().mpt_get_profile(self._h, _ptr(buf), int(buf.size)))
+        tl = buf[(2 + int(sms)) * 16:].reshape(len(self.TIMELINE_ROWS), self.MAX_N + 1)
+        return {name: tl[k, :self.N].copy() for k, name in enumerate(self.TIMELINE_ROWS)}
+
     def set_launch(self, ctas: int):
         _check(lib().mpt_set_launch(self._h, int(ctas)))
 
