@@ -581,6 +581,114 @@ __device__ Norm block_normalize_1(long long *col, uint32_t *dig, int Wn, long lo
     return r;
 }
 
+// Carries into each bit of a binary carry chain over 32 positions: generate
+// mask g, propagate mask p (disjoint), carry cin into bit 0; bit 32 of the
+// result is the carry out of bit 31.  The carries are those of the integer
+// sum (g | p) + g + cin: a generating bit is 1 in both addends, a propagating
+// bit in one, a killing bit in neither.
+__device__ __forceinline__ unsigned long long chain_carries(unsigned g, unsigned p, unsigned cin)
+{
+    const unsigned long long A = (unsigned long long)(g | p), B = g;
+    return (A + B + cin) ^ A ^ B;
+}
+
+// block_normalize for Wn <= PT (one column a thread) with carry lookahead
+// instead of a scan of carry maps.  With v_t = d_t + 2^32 h_t (0 <= d_t <
+// 2^32), the value is sum (d_t + h_{t-1}) 2^(32 t) + h_top 2^(32 Wn); split
+// each h_{t-1} into its positive part p_t and negative part n_t (both below
+// 2^31): first S = sum (d_t + p_t) 2^(32 t), a binary carry chain (a column
+// generates a carry when d_t + p_t >= 2^32 and propagates one when it is
+// 2^32 - 1), then S - sum n_t 2^(32 t), a binary borrow chain (a column
+// generates a borrow when its digit of S is below n_t and propagates one when
+// equal).  Each chain's carries come from one addition of ballot masks per
+// warp, and across the warps from one more on the warps' summaries.  Same
+// result and contract as block_normalize; `red` holds RED_LL long longs (ints
+// [96, 182) used).
+__device__ Norm block_normalize_2(long long *col, uint32_t *dig, int Wn, long long *red, int *status)
+{
+    Norm r;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int *ri = (int *)red;
+    int *sw1 = ri + 150, *sw2 = ri + 166;  // [NWARPS] the warps' summaries of each chain
+    long long *ftop = red + 48;            // ints 96, 97: what lies beyond the top column
+    int *zt = ri + 100;                    // [3][NWARPS] lowest non-zero, top non-zero, top non-all-ones
+    const bool own = tid < Wn;
+    const long long v = own ? col[tid] : 0;
+    const long long hp = (own && tid > 0) ? (col[tid - 1] >> 32) : 0;
+    const uint32_t pp = hp > 0 ? (uint32_t)hp : 0u, np = hp < 0 ? (uint32_t)(-hp) : 0u;
+    const unsigned long long u = (unsigned long long)(uint32_t)v + pp;  // below 2^32 + 2^31
+    const uint32_t e = (uint32_t)u;
+    // the carry chain of S
+    const unsigned g1 = __ballot_sync(FULL, own && (u >> 32) != 0);
+    const unsigned p1 = __ballot_sync(FULL, own && (u >> 32) == 0 && e == 0xffffffffu);
+    if (lane == 0) {
+        const int o0 = (int)(chain_carries(g1, p1, 0) >> 32), o1 = (int)(chain_carries(g1, p1, 1) >> 32);
+        sw1[warp] = o0 | ((o1 & ~o0) << 1);
+    }
+    __syncthreads();
+    int s = lane < NWARPS ? sw1[lane] : 0;
+    unsigned x = (unsigned)(chain_carries(__ballot_sync(FULL, s & 1), __ballot_sync(FULL, s & 2), 0) >> warp) & 1u;
+    const unsigned cin = (unsigned)(chain_carries(g1, p1, x) >> lane) & 1u;
+    const uint32_t sd = e + cin;  // this column's digit of S
+    // the borrow chain of S minus the negative parts
+    const unsigned g2 = __ballot_sync(FULL, own && sd < np), p2 = __ballot_sync(FULL, own && sd == np);
+    if (lane == 0) {
+        const int o0 = (int)(chain_carries(g2, p2, 0) >> 32), o1 = (int)(chain_carries(g2, p2, 1) >> 32);
+        sw2[warp] = o0 | ((o1 & ~o0) << 1);
+    }
+    __syncthreads();
+    s = lane < NWARPS ? sw2[lane] : 0;
+    x = (unsigned)(chain_carries(__ballot_sync(FULL, s & 1), __ballot_sync(FULL, s & 2), 0) >> warp) & 1u;
+    const unsigned bin = (unsigned)(chain_carries(g2, p2, x) >> lane) & 1u;
+    uint32_t dd = 0u;
+    int z = INT_MAX, t0 = -1, t1 = -1;
+    if (own) {
+        const long long w = (long long)sd - np - bin;
+        dd = (uint32_t)w;
+        dig[tid] = dd;
+        col[tid] = 0;  // every read of it was before the first barrier
+        if (dd) {
+            z = tid;
+            t0 = tid;
+        }
+        if (dd != 0xffffffffu) t1 = tid;
+        // the top column's own high part, the carry out of S, the borrow out
+        if (tid == Wn - 1) *ftop = (v >> 32) + (long long)((u + cin) >> 32) - (w < 0 ? 1 : 0);
+    }
+    z = warp_min_i(z);
+    t0 = warp_max_i(t0);
+    t1 = warp_max_i(t1);
+    if (lane == 0) {
+        zt[warp] = z;
+        zt[NWARPS + warp] = t0;
+        zt[2 * NWARPS + warp] = t1;
+    }
+    __syncthreads();
+    {
+        int zz = INT_MAX, a0 = -1, a1 = -1;
+        if (lane < NWARPS) {
+            zz = zt[lane];
+            a0 = zt[NWARPS + lane];
+            a1 = zt[2 * NWARPS + lane];
+        }
+        z = warp_min_i(zz);
+        t0 = warp_max_i(a0);
+        t1 = warp_max_i(a1);
+    }
+    const long long topc = *ftop;
+    if (topc != 0 && topc != -1 && tid == 0) atomicCAS(status, 0, DEV_INTERNAL);
+    r.neg = topc < 0;
+    r.top = r.neg ? (z == INT_MAX ? -1 : max(t1, z)) : t0;
+    if (r.neg) {
+        if (own) {
+            if (tid > z) dig[tid] = ~dd;
+            else if (tid == z) dig[tid] = 0u - dd;
+        }
+        __syncthreads();
+    }
+    return r;
+}
+
 // block_divide when the quotient has at most PT digits (one digit a thread,
 // thread 0 the top one), with two barriers: every warp composes the warps'
 // remainder maps itself.  Same result and contract as block_divide; `red`

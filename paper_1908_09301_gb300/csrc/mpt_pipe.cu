@@ -1618,7 +1618,7 @@ __device__ bool close_bracket(PSmem &S, const KArgs &a, const Geo &G, long long 
     if (threadIdx.x == 0) S.misc[MS_NRUN] = 0;  // the buffer-digit flags (ordered by the barriers below)
     if (width > 0) {
         long long *red = (long long *)(S.misc + MS_RED);
-        const Norm nr = width <= PT ? block_normalize_1(win, S.dig, width, red, a.status)
+        const Norm nr = width <= PT ? block_normalize_2(win, S.dig, width, red, a.status)
                                     : block_normalize(win, S.dig, width, red, a.status);
         top = nr.top;
         neg = nr.neg;

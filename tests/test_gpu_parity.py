@@ -156,6 +156,28 @@ def test_horner_step_sizes(mpt, tau, kind):
     c.close()
 
 
+# b in the pipelined kernel: one-limb values enter as a scaled part of the
+# gamma' bracket, the rest (ratios, long decimals, negative values) as a limb
+# product on an edge CTA
+BS = ["8/3", "7/5", "-2/3", "1/7", "22/7", "255/254", "3", "2.75", "1/300", "2.6666666666666666666666667"]
+
+
+@pytest.mark.parametrize("b", BS)
+def test_b_forms(mpt, b):
+    """Every coefficient of one step and the state after 3 steps, bit for bit."""
+    L, N = 40, 30
+    par = (O.SIGMA, O.R, b, O.TAU)
+    c = gpu_ctx(mpt, L, N, par, kind=2)
+    c.step()
+    want = oracle_coefficients(L, N, par)
+    got = c.coefficients()
+    assert same(got, want), first_mismatch(got, want)
+    c.integrate(2)
+    fin, _ = oracle_run(L, N, par, nsteps=3)
+    assert same(c.get_state(), fin), first_mismatch(c.get_state(), fin)
+    c.close()
+
+
 def test_symmetry_bit_exact(mpt):
     """(x, y, z) -> (-x, -y, z) maps GPU runs onto each other exactly."""
     L, N = 11, 60
