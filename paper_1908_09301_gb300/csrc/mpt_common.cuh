@@ -767,6 +767,55 @@ __device__ long long block_divide_1(const uint32_t *dig, int t, long long base, 
     return eq;
 }
 
+// block_divide when the quotient has at most PT digits and d = d' 2^a > 1
+// (d' odd), without a scan of remainder maps: with Y = floor(E / 2^a) (so
+// floor(E / d) = floor(Y / d')), the remainder mod d' entering quotient digit
+// j from the digits above it is W_{i-1} (sum over the higher digits i' < i of
+// (Y_{i'} mod d') U_{i'}) mod d', where i counts digits from the top (thread
+// i holds the digit with index i from the top), W_i = 2^(32 i) mod d' and U_i
+// = 2^(-32 i) mod d' (2 is invertible mod an odd d').  The sum is a prefix
+// sum of integers below 2^16, then every thread divides its digit.  ent is
+// this thread's U_i | W_{i-1} << 16; dvo divides by d'.  Same result and
+// contract as block_divide (d > 1); `red` holds >= NWARPS ints (ints [0, 16)).
+__device__ long long block_divide_2(const uint32_t *dig, int t, long long base, uint32_t d, int a,
+                                    const Divisor &dvo, int L, uint32_t *out, int *red, uint32_t ent)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long T = base + t + 1;
+    const long long eq = (dig[t] >= d) ? T : T - 1;
+    const long long s = eq - L;
+    const int nX = (int)(T - s);  // L or L+1 digits j = 0 .. nX-1, bottom up
+    const int j = nX - 1 - tid;   // this thread's digit (j < 0: none)
+    uint32_t Y = 0u, term = 0u;
+    if (j >= 0) {
+        const long long idx = s + j - base;
+        const uint32_t x0 = idx >= 0 ? dig[idx] : 0u;
+        const uint32_t x1 = (j + 1 < nX && idx + 1 >= 0) ? dig[idx + 1] : 0u;
+        Y = a ? ((x0 >> a) | (x1 << (32 - a))) : x0;
+        term = mod_inv(mod_inv(Y, dvo) * (ent & 0xffffu), dvo);
+    }
+    uint32_t P = term;  // inclusive prefix sum from the top digit
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t q = __shfl_up_sync(FULL, P, o);
+        if (lane >= o) P += q;
+    }
+    if (lane == 31) red[warp] = (int)P;
+    __syncthreads();
+    uint32_t above = 0u;
+#pragma unroll
+    for (int w = 0; w < NWARPS; w++)
+        if (w < warp) above += (uint32_t)red[w];
+    const uint32_t E = P - term + above;  // the higher digits' sum
+    uint32_t r = tid == 0 ? 0u : mod_inv(mod_inv(E, dvo) * (ent >> 16), dvo);
+    if (j >= 0) {
+        const uint32_t qd = divstep(r, Y, dvo);
+        if (j < L) out[j] = qd;
+    }
+    __syncthreads();
+    return eq;
+}
+
 // ------------------------------------------------------------------ async copies
 
 __device__ __forceinline__ void cp_async4(uint32_t *dst_smem, const uint32_t *src_gmem)

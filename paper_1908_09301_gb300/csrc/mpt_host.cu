@@ -112,6 +112,8 @@ struct mpt_ctx {
     uint32_t tau_p = 0, tau_q = 0, tau_r = 0;
     int tau_shift = 0, tau_neg = 0;
     unsigned long long *chunks = nullptr;  // executed limb-product chunks of the last launch
+    uint32_t *divtab = nullptr;            // pipelined kernel: powers of 2^32 modulo the divisors
+    int divtab_rl = 0;
 };
 
 namespace {
@@ -230,7 +232,7 @@ void free_all(mpt_ctx *c)
     c->sysT = nullptr;
     void *ptrs[] = {c->coefL, c->coefE, c->coefF, c->parL, c->parE, c->parF, c->stL, c->stBackL,
                     c->stE, c->stF, c->stBackEF, c->gwin, c->bar, c->status, c->recS, c->recE,
-                    c->recL, c->prof, c->pub, c->done, c->gin, c->imid, c->chunks};
+                    c->recL, c->prof, c->pub, c->done, c->gin, c->imid, c->chunks, c->divtab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
 }
@@ -282,6 +284,39 @@ int mpt_parse_number(const char *str, int L, int32_t *sign, int32_t *exp, uint32
     if (rc) return fail(MPT_EINVAL, "malformed number \"%s\"", str);
     return MPT_OK;
 }
+
+// The division table of the pipelined kernel's closes (KArgs::divtab): row
+// d (row 0 for q0) holds, for the odd part d' of d and i < rl,
+// 2^(-32 i) mod d' in the low half and 2^(32 (i-1)) mod d' in the high half.
+static std::vector<uint32_t> division_table(int N, int rl, uint32_t q0)
+{
+    std::vector<uint32_t> t((size_t)(N + 1) * rl, 0u);
+    for (int row = 0; row <= N; row++) {
+        uint32_t d = row == 0 ? (q0 ? q0 : 1u) : (uint32_t)row;
+        while (d % 2 == 0) d /= 2;
+        if (d == 1) continue;  // every power is 0 mod 1
+        const uint64_t w1 = (1ull << 32) % d;
+        // inverse of w1 mod d (d odd, so it exists): extended Euclid
+        int64_t r0 = d, r1 = (int64_t)w1, s0 = 0, s1 = 1;
+        while (r1) {
+            const int64_t qq = r0 / r1, r2 = r0 - qq * r1, s2 = s0 - qq * s1;
+            r0 = r1;
+            r1 = r2;
+            s0 = s1;
+            s1 = s2;
+        }
+        const uint64_t u1 = (uint64_t)((s0 % (int64_t)d + d) % d);
+        uint64_t W = 1 % d, U = 1 % d, Wprev = 0;
+        for (int i = 0; i < rl; i++) {
+            t[(size_t)row * rl + i] = (uint32_t)U | ((uint32_t)Wprev << 16);
+            Wprev = W;
+            W = W * w1 % d;
+            U = U * u1 % d;
+        }
+    }
+    return t;
+}
+
 
 int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *tau,
              const char *sigma, const char *R, const char *b, uint64_t cuda_stream)
@@ -387,6 +422,14 @@ int mpt_init(mpt_ctx **out, int K_digits, int N_order, int L_limbs, const char *
     if (ce == cudaSuccess) ce = dalloc(&c->gin, (size_t)mpt::PIPE_SETS * 9 * c->Wcap);
     if (ce == cudaSuccess) ce = dalloc(&c->imid, (size_t)mpt::PIPE_SETS * 4);
     if (ce == cudaSuccess) ce = dalloc(&c->chunks, 1);
+    if (ce == cudaSuccess && L + 1 < mpt::PT) {
+        c->divtab_rl = L + 2;
+        ce = dalloc(&c->divtab, (size_t)(N_order + 1) * c->divtab_rl);
+        if (ce == cudaSuccess) {
+            const std::vector<uint32_t> t = division_table(N_order, c->divtab_rl, c->tau_q);
+            ce = cudaMemcpy(c->divtab, t.data(), sizeof(uint32_t) * t.size(), cudaMemcpyHostToDevice);
+        }
+    }
     if (ce != cudaSuccess) {
         free_all(c);
         delete c;
@@ -688,6 +731,8 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
     a.ptau = c->sysT ? c->sys_npar : 3;
     a.exact = exact ? 1 : 0;
     a.chunks = c->chunks;
+    a.divtab = c->divtab;
+    a.divtab_rl = c->divtab_rl;
     a.tau_p = c->tau_p;
     a.tau_q = c->sysT ? 0 : c->tau_q;
     a.tau_r = c->tau_r;

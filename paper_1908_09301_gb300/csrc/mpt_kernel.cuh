@@ -91,6 +91,11 @@ struct KArgs {
     int exact;              // pipelined kernel: 1 = every product in full (no shortened sums)
     unsigned long long *chunks;  // pipelined kernel: executed 8 x 8 limb-product chunks of
                                  // the launch are added here (null: not counted)
+    // pipelined kernel, L < PT: for each divisor d (row d = 1..N: the brackets'
+    // m + 1; row 0: tau's q, or 1) and i < L + 2, with d' the odd part of d,
+    // 2^(-32 i) mod d' | (2^(32 (i-1)) mod d') << 16 (null: not used)
+    const uint32_t *divtab;
+    int divtab_rl;  // entries a row (L + 2)
 };
 
 // limits of a general system

@@ -1607,9 +1607,32 @@ __device__ void add_simple_parts(const PSmem &S, const Geo &G, long long *win, i
 // from cut + 2 up to the quotient's lowest kept limb must then be neither all
 // zero nor all ones, or the sum may differ from the exact one in what the
 // truncated quotient keeps, and the launch ends with DEV_INEXACT.
+// Divisor d with its division-table entry for this thread (DivT::ent, the
+// table row of d) and the odd part of d (dvo, shift a), when the table is used.
+struct DivT {
+    uint32_t ent;
+    int a;
+    Divisor dvo;
+    bool on;
+};
+// divT: divisors of 1, 2, 3, ... (entry k: k + 1) covering d, or null
+__device__ __forceinline__ DivT div_entry(const KArgs &a, int row, uint32_t d, const Divisor *divT = nullptr)
+{
+    DivT r;
+    r.on = a.divtab != nullptr && d > 1u;
+    r.ent = 0u;
+    r.a = 0;
+    if (r.on) {
+        r.a = __ffs(d) - 1;
+        r.dvo = divT ? divT[(d >> r.a) - 1] : make_divisor(d >> r.a);
+        if ((int)threadIdx.x < a.divtab_rl) r.ent = __ldg(&a.divtab[(size_t)row * a.divtab_rl + threadIdx.x]);
+    }
+    return r;
+}
+
 __device__ bool close_bracket(PSmem &S, const KArgs &a, const Geo &G, long long *win, int width,
                               long long lo, const Divisor &dv, uint32_t *out, int &e, int &f,
-                              uint32_t *out2 = nullptr, long long cut = LLONG_MIN)
+                              uint32_t *out2 = nullptr, long long cut = LLONG_MIN, const DivT *dt = nullptr)
 {
     e = 0;
     f = 0;
@@ -1638,8 +1661,10 @@ __device__ bool close_bracket(PSmem &S, const KArgs &a, const Geo &G, long long 
         if (bits) atomicOr(&S.misc[MS_NRUN], bits);
     }
     if (top >= 0) {
-        const long long eq = G.L < PT ? block_divide_1(S.dig, top, lo, dv, G.L, out, S.misc + MS_RED, out2)
-                                      : block_divide(S.dig, top, lo, dv, G.L, out, S.misc + MS_RED, out2);
+        const long long eq =
+            (dt && dt->on && G.L < PT) ? block_divide_2(S.dig, top, lo, dv.d, dt->a, dt->dvo, G.L, out, S.misc + MS_RED, dt->ent)
+            : G.L < PT                 ? block_divide_1(S.dig, top, lo, dv, G.L, out, S.misc + MS_RED, out2)
+                                       : block_divide(S.dig, top, lo, dv, G.L, out, S.misc + MS_RED, out2);
         if (eq > (1LL << 30) || eq < -(1LL << 30)) {
             if (threadIdx.x == 0) atomicCAS(a.status, 0, DEV_ERANGE);
             ok = false;
@@ -1793,6 +1818,7 @@ __device__ bool horner_ratio(PSmem &S, const KArgs &a, const Geo &G, int c, long
     const uint32_t tp = a.tau_p, tq = a.tau_q, tr = a.tau_r;
     const int sh = a.tau_shift;
     const Divisor dq = make_divisor(tq);
+    const DivT dth = div_entry(a, 0, tq);  // row 0: tau's q
     int he = S.misc[MS_NEWE], hf = S.misc[MS_NEWE + 1];
     constexpr int CR = MAX_L / PT;
     uint32_t nxt[CR];
@@ -1854,7 +1880,7 @@ __device__ bool horner_ratio(PSmem &S, const KArgs &a, const Geo &G, int c, long
         __syncthreads();
         pr.mark(PR_HMAC);
         int e, f;
-        if (!close_bracket(S, a, G, win, width, lo, dq, hp, e, f)) {
+        if (!close_bracket(S, a, G, win, width, lo, dq, hp, e, f, nullptr, LLONG_MIN, &dth)) {
             ok = false;
             break;
         }
@@ -1931,6 +1957,7 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             const long long g = step * a.N + m;
             const int set = (int)(g % PIPE_SETS);
             const Divisor dvm = S.divT[m];
+            const DivT dtm = div_entry(a, m + 1, (uint32_t)(m + 1), S.divT);  // read now, used at the close
             if (c == 1 && threadIdx.x == 0) tl_put(a, TL_B_START, m, step);
             if (threadIdx.x == 0) S.misc[MS_STATUS] = bracket_setup(S, a, pa, G, c, m, set) ? 0 : 1;
             __syncthreads();
@@ -1987,7 +2014,7 @@ __device__ void closer_loop(PSmem &S, const KArgs &a, const PArgs &pa, const Geo
             __syncthreads();
             int e, f;
             const bool ok = close_bracket(S, a, G, win, width, lo, dvm, S.newc, e, f, nullptr,
-                                          ((const long long *)(bk + BK_CUT))[0]);
+                                          ((const long long *)(bk + BK_CUT))[0], &dtm);
             pr.mark(PR_CLOSE);
             if (!ok) return;
             if (threadIdx.x == 0) {
