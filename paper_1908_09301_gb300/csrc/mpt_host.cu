@@ -734,7 +734,7 @@ int launch_steps(mpt_ctx *c, int64_t nsteps, long long nrec, int64_t record_ever
     a.divtab = c->divtab;
     a.divtab_rl = c->divtab_rl;
     a.tau_p = c->tau_p;
-    a.tau_q = c->sysT ? 0 : c->tau_q;
+    a.tau_q = c->tau_q;
     a.tau_r = c->tau_r;
     a.tau_shift = c->tau_shift;
     a.tau_neg = c->tau_neg;

@@ -1042,18 +1042,26 @@ __device__ void close_phase(const Smem &S, const KArgs &a, int m, int set)
     const int G = vgrid(a);
     const int N1 = a.N + 1;
     Prof pr(a);
+    if (G > 1) {
+        // the three windows of the global set into shared memory, every thread
+        // taking a share (one round trip, not one per column a lane)
+        for (int tg = 0; tg < 3; tg++) {
+            const int wd = S.misc[MS_WIDTH + tg];
+            const long long *src = a.gwin + ((size_t)set * 3 + tg) * a.Wcap;
+            for (int c = threadIdx.x; c < wd; c += NT) S.win[(size_t)tg * a.Wcap + c] = __ldcg(&src[c]);
+        }
+        __syncthreads();
+    }
     if (warp < 3) {
         const int tg = warp;  // 0 alpha, 1 beta, 2 gamma
         const int wd = S.misc[MS_WIDTH + tg];
         uint32_t *out = S.newc + tg * a.Lp;
         int e = 0, f = 0;
         if (wd > 0) {
-            const long long *src = (G > 1) ? a.gwin + ((size_t)set * 3 + tg) * a.Wcap
-                                            : S.win + (size_t)tg * a.Wcap;
+            const long long *src = S.win + (size_t)tg * a.Wcap;
             uint32_t *dig = S.dig + (size_t)tg * a.Wcap;
-            Norm nr = warp_normalize(src, G > 1, dig, wd, a.status);
-            if (G == 1)
-                for (int c = lane; c < wd; c += 32) S.win[tg * a.Wcap + c] = 0;
+            Norm nr = warp_normalize(src, false, dig, wd, a.status);
+            for (int c = lane; c < wd; c += 32) S.win[tg * a.Wcap + c] = 0;
             if (nr.top >= 0) {
                 long long eq = warp_divide(dig, nr.top, win_base(S, tg), (uint32_t)(m + 1), a.L, out);
                 if (eq > (1LL << 30) || eq < -(1LL << 30)) {
