@@ -53,6 +53,7 @@ IMAD_PER_SM_CLK = 64
 PROFILE = os.path.join(ROOT, "profiles", "pipe_kernel_k2000_n1000.md")
 KERNEL_SOURCES = ["paper_1908_09301_gb300/csrc/mpt_pipe.cu",
                   "paper_1908_09301_gb300/csrc/mpt_common.cuh",
+                  "paper_1908_09301_gb300/csrc/mpt_divisor.cuh",
                   "paper_1908_09301_gb300/csrc/mpt_kernel.cuh"]
 
 

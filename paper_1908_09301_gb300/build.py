@@ -21,7 +21,7 @@ LIB = os.path.join(HERE, "libmpt.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["mpt_step.cu", "mpt_pipe.cu", "mpt_host.cu", "mpt_static.cu", "mpt_adjoint.cu", "int_peak.cu"]
 CPP_SOURCES = ["host_parse.cpp"]
-HEADERS = ["mpt_kernel.cuh", "mpt_common.cuh", "host_parse.h"]
+HEADERS = ["mpt_kernel.cuh", "mpt_common.cuh", "mpt_divisor.cuh", "host_parse.h"]
 
 
 def nvcc() -> str:

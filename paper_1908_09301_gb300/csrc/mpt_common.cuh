@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mpt_divisor.cuh"
 #include "mpt_kernel.cuh"
 
 namespace mpt {
@@ -35,62 +36,6 @@ __device__ __forceinline__ void mac_cc(uint32_t a, uint32_t b, uint32_t &c0, uin
         "addc.u32 %2, %2, 0;"
         : "+r"(c0), "+r"(c1), "+r"(c2)
         : "r"(a), "r"(b));
-}
-
-// ------------------------------------------------------------------ division by an invariant
-
-// Division of a 32-bit n by d (1 <= d < 2^31) with a multiplier and shifts:
-// the method of Granlund and Montgomery, "Division by invariant integers
-// using multiplication" (PLDI 1994), Sec. 4: with l = ceil(log2 d),
-// m = floor(2^32 (2^l - d) / d) + 1, t = mulhi(m, n),
-// q = (t + ((n - t) >> min(l, 1))) >> max(l - 1, 0).
-struct Divisor {
-    uint32_t d, m;
-    int s1, s2;
-};
-
-__host__ __device__ inline Divisor make_divisor(uint32_t d)
-{
-    Divisor v;
-    v.d = d;
-    int l = 0;
-    while (l < 32 && (1ull << l) < d) l++;
-    v.m = (uint32_t)((((1ull << l) - d) << 32) / d + 1);
-    v.s1 = l < 1 ? l : 1;
-    v.s2 = l - 1 > 0 ? l - 1 : 0;
-    return v;
-}
-
-__host__ __device__ __forceinline__ uint32_t mulhi32(uint32_t a, uint32_t b)
-{
-#ifdef __CUDA_ARCH__
-    return __umulhi(a, b);
-#else
-    return (uint32_t)(((uint64_t)a * b) >> 32);
-#endif
-}
-
-__host__ __device__ __forceinline__ uint32_t div_inv(uint32_t n, const Divisor &v)
-{
-    uint32_t t = mulhi32(v.m, n);
-    return (t + ((n - t) >> v.s1)) >> v.s2;
-}
-
-// (r * 2^32 + x) div d with r < d < 2^16 on entry; r becomes the remainder
-__host__ __device__ __forceinline__ uint32_t divstep(uint32_t &r, uint32_t x, const Divisor &v)
-{
-    uint32_t n1 = (r << 16) | (x >> 16);
-    uint32_t q1 = div_inv(n1, v);
-    uint32_t r1 = n1 - q1 * v.d;
-    uint32_t n0 = (r1 << 16) | (x & 0xffffu);
-    uint32_t q0 = div_inv(n0, v);
-    r = n0 - q0 * v.d;
-    return (q1 << 16) | q0;
-}
-
-__host__ __device__ __forceinline__ uint32_t mod_inv(uint32_t n, const Divisor &v)
-{
-    return n - div_inv(n, v) * v.d;
 }
 
 #ifdef __CUDACC__

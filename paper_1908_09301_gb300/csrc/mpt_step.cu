@@ -31,6 +31,7 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "mpt_divisor.cuh"
 #include "mpt_kernel.cuh"
 
 namespace mpt {
@@ -651,18 +652,6 @@ __device__ Norm warp_normalize(const long long *col, bool from_global, uint32_t 
     return r;
 }
 
-// (hi * 2^32 + lo) div/mod d for r = hi < d < 2^16, in two 16-bit halves
-__device__ __forceinline__ uint32_t divstep(uint32_t &r, uint32_t x, uint32_t d)
-{
-    uint32_t n1 = (r << 16) | (x >> 16);
-    uint32_t q1 = n1 / d;
-    uint32_t r1 = n1 - q1 * d;
-    uint32_t n0 = (r1 << 16) | (x & 0xffffu);
-    uint32_t q0 = n0 / d;
-    r = n0 - q0 * d;
-    return (q1 << 16) | q0;
-}
-
 // trunc_L(|E| / d) for |E| = sum_c dig[c] 2^(32(base+c)) with top digit t:
 // writes L limbs to out (lanes write their own chunks) and returns the exponent.
 // Only limbs of |E| at or above the quotient's lowest kept position matter
@@ -689,30 +678,28 @@ __device__ long long warp_divide(const uint32_t *dig, int t, long long base, uin
         __syncwarp();
         return eq;
     }
-    // this lane's chunk as an affine map r -> (Pm r + V) mod d
+    // this lane's chunk as an affine map r -> (Pm r + V) mod d; the divisions
+    // by d with a multiplier (invariant-divisor method)
+    const Divisor dv = make_divisor16(d);
     uint32_t V = 0, Pm = 1;
-    uint32_t t32 = 0;
-    {
-        uint32_t rr = 1;  // 2^32 mod d
-        (void)divstep(rr, 0u, d);
-        t32 = rr;
-    }
+    uint32_t t32 = 1;
+    (void)divstep(t32, 0u, dv);  // 2^32 mod d
     for (int j = jhi - 1; j >= jlo; j--) {
-        (void)divstep(V, X(j), d);
-        Pm = (Pm * t32) % d;
+        (void)divstep(V, X(j), dv);
+        Pm = mod_inv(Pm * t32, dv);
     }
     for (int o = 1; o < 32; o <<= 1) {
         uint32_t Po = __shfl_up_sync(FULL, Pm, o);
         uint32_t Vo = __shfl_up_sync(FULL, V, o);
         if (lane >= o) {
-            V = (Pm * Vo + V) % d;
-            Pm = (Pm * Po) % d;
+            V = mod_inv(Pm * Vo + V, dv);
+            Pm = mod_inv(Pm * Po, dv);
         }
     }
     uint32_t r = __shfl_up_sync(FULL, V, 1);
     if (lane == 0) r = 0;
     for (int j = jhi - 1; j >= jlo; j--) {
-        uint32_t qd = divstep(r, X(j), d);
+        uint32_t qd = divstep(r, X(j), dv);
         if (j < L) out[j] = qd;
     }
     __syncwarp();

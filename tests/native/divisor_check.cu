@@ -1,6 +1,7 @@
 // Host-side check of the invariant-divisor division used by the device code:
 // for every d in [1, 2^16) and a set of numerators, div_inv and divstep must
-// agree with the plain integer quotient and remainder.
+// agree with the plain integer quotient and remainder, and make_divisor16 must
+// give make_divisor's multiplier and shifts.
 #include <cstdio>
 #include <cstdint>
 #include "../../paper_1908_09301_gb300/csrc/mpt_common.cuh"
@@ -17,6 +18,11 @@ int main()
     long long checks = 0;
     for (uint32_t d = 1; d < 65536u; d++) {
         mpt::Divisor v = mpt::make_divisor(d);
+        const mpt::Divisor w = mpt::make_divisor16(d);
+        if (w.d != v.d || w.m != v.m || w.s1 != v.s1 || w.s2 != v.s2) {
+            printf("FAIL make_divisor16 d=%u\n", d);
+            return 1;
+        }
         uint32_t ns[12] = {0u, 1u, d - 1u, d, d + 1u, 0xffffffffu, 0xfffffffeu, 0x80000000u,
                            0x7fffffffu, (uint32_t)(d * 65535u), next(), next()};
         for (uint32_t n : ns) {
