@@ -514,4 +514,36 @@ int parse_number(const char *str, int L, int32_t *sign, int32_t *exp, uint32_t *
     return 0;
 }
 
+// The division table of the pipelined kernel's closes (KArgs::divtab): row
+// d (row 0 for q0) holds, for the odd part d' of d and i < rl,
+// 2^(-32 i) mod d' in the low half and 2^(32 (i-1)) mod d' in the high half.
+std::vector<uint32_t> division_table(int N, int rl, uint32_t q0)
+{
+    std::vector<uint32_t> t((size_t)(N + 1) * rl, 0u);
+    for (int row = 0; row <= N; row++) {
+        uint32_t d = row == 0 ? (q0 ? q0 : 1u) : (uint32_t)row;
+        while (d % 2 == 0) d /= 2;
+        if (d == 1) continue;  // every power is 0 mod 1
+        const uint64_t w1 = (1ull << 32) % d;
+        // inverse of w1 mod d (d odd, so it exists): extended Euclid
+        int64_t r0 = d, r1 = (int64_t)w1, s0 = 0, s1 = 1;
+        while (r1) {
+            const int64_t qq = r0 / r1, r2 = r0 - qq * r1, s2 = s0 - qq * s1;
+            r0 = r1;
+            r1 = r2;
+            s0 = s1;
+            s1 = s2;
+        }
+        const uint64_t u1 = (uint64_t)((s0 % (int64_t)d + d) % d);
+        uint64_t W = 1 % d, U = 1 % d, Wprev = 0;
+        for (int i = 0; i < rl; i++) {
+            t[(size_t)row * rl + i] = (uint32_t)U | ((uint32_t)Wprev << 16);
+            Wprev = W;
+            W = W * w1 % d;
+            U = U * u1 % d;
+        }
+    }
+    return t;
+}
+
 }  // namespace mpt_host

@@ -2,6 +2,7 @@
 #pragma once
 #include <cstdint>
 #include <string>
+#include <vector>
 
 namespace mpt_host {
 // trunc_L of the exact value of `str` (decimal such as "-15.8", "1e-20", or a
@@ -22,4 +23,9 @@ int from_double(double v, int L, int32_t *sign, int32_t *exp, uint32_t *limbs);
 // then its limbs are M = (p 2^k - r) / q, k = 32 shift, r = p 2^k mod q, and
 // tau h = (p h - r h 2^-k) / q exactly.  0 with (p, q, r, shift, neg), else -1.
 int small_ratio(const char *str, int L, uint32_t *p, uint32_t *q, uint32_t *r, int *shift, int *neg);
+// The division table of the pipelined kernel's closes: rows d = 0..N (row 0
+// for q0, or 1 when q0 = 0), rl entries a row; with d' the odd part of d,
+// entry i holds 2^(-32 i) mod d' in its low 16 bits and 2^(32 (i-1)) mod d'
+// (0 for i = 0) in its high 16 bits.  Every entry is 0 where d' = 1.
+std::vector<uint32_t> division_table(int N, int rl, uint32_t q0);
 }  // namespace mpt_host

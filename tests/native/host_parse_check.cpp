@@ -2,6 +2,7 @@
 // and rounded differences, one case per input line.
 //   P x h sgn                      -> the string x + sgn 10^-h
 //   D L h s1 e1 l1.. s2 e2 l2..    -> (v1 - v2) / (2 10^-h) as %.17g
+//   T N rl q0                      -> the division table, (N+1) rl entries
 #include <cstdio>
 #include <iostream>
 #include <string>
@@ -34,6 +35,12 @@ int main()
             char buf[64];
             std::snprintf(buf, sizeof buf, "%.17g", d);
             std::cout << buf << "\n";
+        } else if (op == "T") {
+            int N, rl;
+            uint32_t q0;
+            std::cin >> N >> rl >> q0;
+            const std::vector<uint32_t> t = mpt_host::division_table(N, rl, q0);
+            for (size_t i = 0; i < t.size(); i++) std::cout << t[i] << (i + 1 < t.size() ? " " : "\n");
         }
     }
     return 0;

@@ -68,3 +68,27 @@ def test_differences_are_rounded_once(exe):
     for (L, h, v1, v2), line in zip(cases, out):
         want = float((v1 - v2) / (2 * Fraction(1, 10 ** h)))
         assert float(line) == want, (L, h, v1, v2)
+
+
+def test_division_table_against_modular_powers(exe):
+    """The pipelined kernel's division table (the closes divide by d = d' 2^a,
+    d' odd, through prefix sums of (digit mod d') 2^(-32 i)): entry i of row d
+    is 2^(-32 i) mod d' and 2^(32 (i-1)) mod d', from Python's modular powers;
+    row 0 is tau's q; odd parts 1 give zeros.  The two factors are inverses."""
+    N, rl, q0 = 300, 40, 100
+    vals = [int(v) for v in run(exe, [f"T {N} {rl} {q0}"])[0].split()]
+    assert len(vals) == (N + 1) * rl
+    for row in range(N + 1):
+        d = q0 if row == 0 else row
+        while d % 2 == 0:
+            d //= 2
+        for i in range(rl):
+            v = vals[row * rl + i]
+            if d == 1:
+                assert v == 0, (row, i)
+                continue
+            U = pow(2, -32 * i, d)
+            Wm = pow(2, 32 * (i - 1), d) if i > 0 else 0
+            assert v & 0xFFFF == U and v >> 16 == Wm, (row, i, v, U, Wm)
+            if i > 0:
+                assert (Wm * pow(2, 32, d) * U) % d == 1
