@@ -433,99 +433,6 @@ __device__ long long block_divide(const uint32_t *dig, int t, long long base, co
     return eq;
 }
 
-// block_normalize for Wn <= PT (one column a thread), with two barriers
-// (three when the value is negative) instead of four: with one column a
-// thread, the carry a thread's column hands on before any adjustment is the
-// column's own high part, so thread t reads the column below its own to form
-// its carry map and needs no exchange for it; and every warp composes the
-// warps' maps itself (a scan over the lanes, lane w holding warp w's map)
-// instead of waiting for one warp to do it.  Same result and contract as
-// block_normalize; `red` holds RED_LL long longs (ints [64, 148) used).
-__device__ Norm block_normalize_1(long long *col, uint32_t *dig, int Wn, long long *red, int *status)
-{
-    Norm r;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int *ri = (int *)red;
-    int *mapw = ri + 64;                    // [NWARPS] the warps' maps
-    long long *fin0 = red + 48;             // ints 96, 97: the top column's own carry
-    int *zt = ri + 100;                     // [3][NWARPS] lowest non-zero, top non-zero, top non-all-ones
-    const bool own = tid < Wn;
-    const long long v = own ? col[tid] : 0;
-    const long long lprev = (own && tid > 0) ? (col[tid - 1] >> 32) : 0;
-    const uint32_t d = (uint32_t)v;
-    int f = CMAP_ID;
-    if (own) {
-        f = 0;
-#pragma unroll
-        for (int x = -1; x <= 1; x++) f |= ((int)(((long long)d + lprev + x) >> 32) + 1) << (2 * (x + 1));
-        if (tid == Wn - 1) *fin0 = v >> 32;
-    }
-    int F = f;  // inclusive scan of maps, lowest thread first
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int G = __shfl_up_sync(FULL, F, o);
-        if (lane >= o) F = cmap_compose(F, G);
-    }
-    if (lane == 31) mapw[warp] = F;
-    __syncthreads();
-    int Gw = lane < NWARPS ? mapw[lane] : CMAP_ID;
-#pragma unroll
-    for (int o = 1; o < NWARPS; o <<= 1) {
-        const int H = __shfl_up_sync(FULL, Gw, o);
-        if (lane >= o) Gw = cmap_compose(Gw, H);
-    }
-    int pre = __shfl_sync(FULL, Gw, (warp + 31) & 31);  // the warps below this one
-    if (warp == 0) pre = CMAP_ID;
-    const int total = __shfl_sync(FULL, Gw, NWARPS - 1);
-    const long long topc = *fin0 + cmap_apply(total, 0);
-    int ex = __shfl_up_sync(FULL, F, 1);
-    if (lane == 0) ex = CMAP_ID;
-    const int din = cmap_apply(cmap_compose(ex, pre), 0);
-    uint32_t dd = 0u;
-    int z = INT_MAX, t0 = -1, t1 = -1;
-    if (own) {
-        dd = (uint32_t)((long long)d + lprev + din);
-        dig[tid] = dd;
-        col[tid] = 0;  // every read of it was before the barrier
-        if (dd) {
-            z = tid;
-            t0 = tid;
-        }
-        if (dd != 0xffffffffu) t1 = tid;
-    }
-    z = warp_min_i(z);
-    t0 = warp_max_i(t0);
-    t1 = warp_max_i(t1);
-    if (lane == 0) {
-        zt[warp] = z;
-        zt[NWARPS + warp] = t0;
-        zt[2 * NWARPS + warp] = t1;
-    }
-    __syncthreads();
-    {
-        int zz = INT_MAX, a0 = -1, a1 = -1;
-        if (lane < NWARPS) {
-            zz = zt[lane];
-            a0 = zt[NWARPS + lane];
-            a1 = zt[2 * NWARPS + lane];
-        }
-        z = warp_min_i(zz);
-        t0 = warp_max_i(a0);
-        t1 = warp_max_i(a1);
-    }
-    if (topc != 0 && topc != -1 && tid == 0) atomicCAS(status, 0, DEV_INTERNAL);
-    r.neg = topc < 0;
-    r.top = r.neg ? (z == INT_MAX ? -1 : max(t1, z)) : t0;
-    if (r.neg) {
-        if (own) {
-            if (tid > z) dig[tid] = ~dd;
-            else if (tid == z) dig[tid] = 0u - dd;
-        }
-        __syncthreads();
-    }
-    return r;
-}
-
 // Carries into each bit of a binary carry chain over 32 positions: generate
 // mask g, propagate mask p (disjoint), carry cin into bit 0; bit 32 of the
 // result is the carry out of bit 31.  The carries are those of the integer
