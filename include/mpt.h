@@ -226,7 +226,13 @@ int mpt_set_wait_limit(mpt_ctx *ctx, int64_t polls);
  * marks of the pipelined kernel).  Row 0 is the first CTA (the pipelined
  * kernel: its beta' bracket CTA), row 1 the last CTA; the pipelined kernel
  * adds one row per CTA of the launch (row 2 + CTA index), up to 2 + the
- * device's SM count rows in all.  Off by default.
+ * device's SM count rows in all.  After those rows (at (2 + SM count) * 16)
+ * the pipelined kernel writes a per-index timeline of the launch's last step:
+ * 9 rows of 4097 global-timer stamps in ns (row r, index m at r * 4097 + m):
+ * the beta' bracket at the start of index m, after its wait for the other
+ * CTAs' sums, after publishing; the last edge CTA and the last worker to
+ * finish index m; the gamma' bracket after publishing; the last edge CTA to
+ * see coefficient m, to start its products, to end them.  Off by default.
  */
 int mpt_set_profiling(mpt_ctx *ctx, int on);
 int mpt_get_profile(mpt_ctx *ctx, int64_t *cycles, int n);
