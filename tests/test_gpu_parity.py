@@ -70,9 +70,14 @@ def test_parameters_match_oracle(mpt):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("L,N", [(1, 5), (2, 7), (3, 20), (11, 60), (13, 25), (21, 40), (53, 30),
-                                 (8, 9), (9, 64), (130, 12), (250, 9), (600, 8), (1024, 6)])
+                                 (8, 9), (9, 64), (130, 12), (250, 9), (510, 4), (511, 4), (600, 8),
+                                 (1024, 6)])
 def test_one_step_coefficients(mpt, L, N, kind):
-    """Eq. (3) coefficients alpha_0..alpha_N etc. and the Horner state, bit for bit."""
+    """Eq. (3) coefficients alpha_0..alpha_N etc. and the Horner state, bit for bit.
+    The sizes cross the pipelined closes' limits: windows of at most 512
+    columns (carry chains) or more (a scan of carry maps); quotients of L + 1
+    digits with the division table (L <= 510), one digit a thread without it
+    (L = 511), or several digits a thread (L >= 512)."""
     c = gpu_ctx(mpt, L, N, kind=kind)
     c.step()
     want = oracle_coefficients(L, N)
