@@ -243,7 +243,8 @@ int mpt_get_profile(mpt_ctx *ctx, int64_t *cycles, int n);
  * 2 mad.wide.u32, 3 limb product with mad.lo.cc/madc.hi.cc/addc, 4 two
  * mad.wide.u32 on 16-bit halves, 5 mad.wide.u32 plus a wide carry word,
  * 6 mad.lo.cc+addc and mad.hi.cc+addc, 7 mad.lo+mad.hi, 8 mul.wide plus
- * add.cc chains) on one CTA of `threads` threads (multiple of 32, <= 1024)
+ * add.cc chains, 9 a row of 8 limb products with the carries along the row:
+ * one madc.lo.cc chain, one madc.hi.cc chain, two addc) on one CTA of `threads` threads (multiple of 32, <= 1024)
  * per SM, 8 independent chains per thread, `iters` rounds.  Outputs: mean
  * loop cycles of a CTA, kernel time in ms, number of distinct SMs used, grid
  * size.  Allocates its own scratch buffers.  Returns 0 or a cudaError_t

@@ -17,6 +17,11 @@
 //   6  limb product, lo/hi separately:     mad.lo.cc+addc, mad.hi.cc+addc
 //   7  mad.lo.u32 + mad.hi.u32 pair, no carries (two 32-bit column sums)
 //   8  limb product, wide + carry adds:    mul.wide, add.cc/addc.cc/addc
+//   9  limb products of a row, carries along the row: one limb a times 8
+//      limbs b_j into columns 0..8, low halves in one mad.lo.cc/madc.lo.cc
+//      chain over columns 0..7 and high halves in one mad.hi.cc/madc.hi.cc
+//      chain over columns 1..8, each chain's carry out into a counter word
+//      (8 products, 16 multiply-adds, 2 addc)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -81,6 +86,36 @@ __device__ __forceinline__ void mac_lohi(uint32_t a, uint32_t b, uint32_t &l0, u
         : "r"(a), "r"(b));
 }
 
+// a times the row b[0..7] added into the columns acc[0..8] with carries along
+// the row; the low chain's carry out goes to k[0], the high chain's to k[1]
+__device__ __forceinline__ void mac_row(uint32_t a, const uint32_t (&b)[W], uint32_t (&acc)[W + 1],
+                                        uint32_t (&k)[2])
+{
+    asm volatile(
+        "mad.lo.cc.u32  %0, %11, %12, %0;\n\t"
+        "madc.lo.cc.u32 %1, %11, %13, %1;\n\t"
+        "madc.lo.cc.u32 %2, %11, %14, %2;\n\t"
+        "madc.lo.cc.u32 %3, %11, %15, %3;\n\t"
+        "madc.lo.cc.u32 %4, %11, %16, %4;\n\t"
+        "madc.lo.cc.u32 %5, %11, %17, %5;\n\t"
+        "madc.lo.cc.u32 %6, %11, %18, %6;\n\t"
+        "madc.lo.cc.u32 %7, %11, %19, %7;\n\t"
+        "addc.u32       %9, %9, 0;\n\t"
+        "mad.hi.cc.u32  %1, %11, %12, %1;\n\t"
+        "madc.hi.cc.u32 %2, %11, %13, %2;\n\t"
+        "madc.hi.cc.u32 %3, %11, %14, %3;\n\t"
+        "madc.hi.cc.u32 %4, %11, %15, %4;\n\t"
+        "madc.hi.cc.u32 %5, %11, %16, %5;\n\t"
+        "madc.hi.cc.u32 %6, %11, %17, %6;\n\t"
+        "madc.hi.cc.u32 %7, %11, %18, %7;\n\t"
+        "madc.hi.cc.u32 %8, %11, %19, %8;\n\t"
+        "addc.u32       %10, %10, 0;"
+        : "+r"(acc[0]), "+r"(acc[1]), "+r"(acc[2]), "+r"(acc[3]), "+r"(acc[4]), "+r"(acc[5]),
+          "+r"(acc[6]), "+r"(acc[7]), "+r"(acc[8]), "+r"(k[0]), "+r"(k[1])
+        : "r"(a), "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]),
+          "r"(b[7]));
+}
+
 template <int V>
 __global__ void __launch_bounds__(1024) peak_kernel(int iters, uint32_t seed, uint64_t *sink,
                                                        long long *cycles, int *smid)
@@ -96,9 +131,13 @@ __global__ void __launch_bounds__(1024) peak_kernel(int iters, uint32_t seed, ui
         c0[k] = c1[k] = c2[k] = 0;
         w0[k] = w1[k] = 0;
     }
+    uint32_t acc[W + 1], kc[2] = {0u, 0u};
+#pragma unroll
+    for (int k = 0; k <= W; k++) acc[k] = 0;
     __syncthreads();
     long long t0 = clock64();
     for (int it = 0; it < iters; it++) {
+        if (V == 9) mac_row(a, b, acc, kc);  // W limb products a round, as the chains below
 #pragma unroll
         for (int k = 0; k < W; k++) {
             if (V == 0) c0[k] = mad_lo(c0[k], b[k], a);
@@ -127,7 +166,8 @@ __global__ void __launch_bounds__(1024) peak_kernel(int iters, uint32_t seed, ui
     long long t1 = clock64();
     uint64_t s = 0;
 #pragma unroll
-    for (int k = 0; k < W; k++) s += c0[k] + c1[k] + c2[k] + w0[k] + w1[k] + b[k];
+    for (int k = 0; k < W; k++) s += c0[k] + c1[k] + c2[k] + w0[k] + w1[k] + b[k] + acc[k];
+    s += acc[W] + kc[0] + kc[1];
     sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
     if (threadIdx.x == 0) {
         cycles[blockIdx.x] = t1 - t0;
@@ -185,6 +225,7 @@ extern "C" int mpt_int_peak_run(int variant, int threads, int iters, double *mea
             case 6: launch<6>(grid, iters, sink, cycles, smid, 0); break;
             case 7: launch<7>(grid, iters, sink, cycles, smid, 0); break;
             case 8: launch<8>(grid, iters, sink, cycles, smid, 0); break;
+            case 9: launch<9>(grid, iters, sink, cycles, smid, 0); break;
             default: e = cudaErrorInvalidValue;
         }
         cudaEventRecord(b, 0);
